@@ -1,0 +1,125 @@
+/*
+ * ov.h -- C ABI of the GB300 two-sided Lanczos sgn(H) b library and its
+ * gauge-force vector-Jacobian product.
+ *
+ * Method: M. Puhr, P. Buividovich, "A numerical method to compute derivatives
+ * of functions of large complex matrices and its application to the overlap
+ * Dirac operator at finite chemical potential", arXiv:1604.08057.
+ *
+ *   H(mu) = gamma5 D_w(mu)                                   (Sec. 1, Eq. overlap)
+ *   D_w(mu) = 1 - kappa sum_{i<=3}(G_i^+ + G_i^-)
+ *                - kappa (e^{mu} G_4^+ + e^{-mu} G_4^-)       (App. A, Eq. WD_op)
+ *   (G_nu^+)_{x,y} = (1 + gamma_nu) U_nu(x) delta_{x+nu,y}
+ *   (G_nu^-)_{x,y} = (1 - gamma_nu) U_nu(x-nu)^dagger delta_{x-nu,y}   (Eq. WD_G)
+ *   kappa = 1 / (2 m_w + 8)
+ *
+ * Conventions shared by every entry point:
+ *   - Lattice dims[4] = {Nx, Ny, Nz, Nt}; site index ((t*Nz + z)*Ny + y)*Nx + x;
+ *     periodic boundary conditions in all four directions.
+ *   - gamma matrices: Euclidean chiral basis, gamma_k = [[0,-i s_k],[i s_k,0]],
+ *     gamma_4 = [[0,1],[1,0]], gamma5 = diag(1,1,-1,-1).
+ *   - All array arguments are DEVICE pointers to interleaved complex128
+ *     (re, im doubles), caller-owned, 16-byte aligned:
+ *       links  U[V][4][3][3]  (direction order x, y, z, t; U[..][a][b] row a col b)
+ *       spinor psi[V][4][3]   (spin, colour)
+ *       n sources are stored back to back: psi[nsrc][V][4][3].
+ *   - Every call is ordered on the context's CUDA stream and returns only
+ *     after the stream has finished the call's work; the return value is 0
+ *     on success or a negative OV_ERR_* code.  No exception crosses the ABI.
+ *   - The context owns all device workspace; it grows on demand and is
+ *     released by ov_context_destroy.  A context is used by one host thread
+ *     at a time.
+ */
+#ifndef OV_H
+#define OV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define OV_OK                  0
+#define OV_ERR_INVALID_ARG    -1  /* a null pointer, a non-positive size, k out of range */
+#define OV_ERR_OOM            -2  /* device workspace could not be allocated */
+#define OV_ERR_BREAKDOWN      -3  /* Lanczos breakdown: |omega| <= 1e-14 ||r|| ||s|| */
+#define OV_ERR_SIGN_ILLPOSED  -4  /* k x k Newton sign did not converge or hit a singular iterate */
+#define OV_ERR_CUDA           -5  /* a CUDA runtime call failed */
+#define OV_ERR_NONFINITE      -6  /* a NaN or Inf appeared in a recurrence coefficient */
+
+/* Precision of lattice vectors, links and stencil arithmetic.
+ * OV_FP64 : everything in FP64.
+ * OV_MIXED: links, basis vectors and stencils in FP32; dot products accumulated
+ *           with compensated (Dot2) FP32 arithmetic per thread and FP64 across
+ *           threads; recurrence coefficients, re-biorthogonalisation
+ *           coefficients, the k x k sign and its Frechet adjoint in FP64. */
+#define OV_FP64  0
+#define OV_MIXED 1
+
+typedef struct {
+  int32_t precision;   /* OV_FP64 or OV_MIXED */
+  int32_t rebiorth;    /* 0: none; 1: every step; P > 1: at the two steps j = 0, 1 (mod P) */
+  int32_t passes;      /* classical Gram-Schmidt passes per re-biorthogonalisation (1 or 2) */
+  int32_t reserved[5];
+} ov_options;
+
+typedef struct {
+  int32_t k_reached;        /* Lanczos steps completed */
+  int32_t newton_iters;     /* Newton iterations of the k x k sign (forward) */
+  int32_t newton_iters_adj; /* Newton iterations of the Frechet adjoint (VJP only) */
+  int32_t reserved;
+  double  min_abs_re_ritz;  /* unused (0) unless computed by the caller */
+  double  t_ms[8];          /* phase times: 0 forward Krylov, 1 k x k sign, 2 combine,
+                               3 Frechet adjoint, 4 reverse sweep, 5 force/dmu, 6-7 unused */
+} ov_tsl_info;
+
+typedef struct ov_context ov_context;
+
+/* Create a context bound to `stream` (a cudaStream_t; NULL = legacy default
+ * stream) on the current CUDA device.  `opt` may be NULL (FP64, rebiorth 1,
+ * 2 passes).  *ctx receives the handle. */
+int ov_context_create(ov_context **ctx, const ov_options *opt, void *stream);
+int ov_context_destroy(ov_context *ctx);
+int ov_context_set_options(ov_context *ctx, const ov_options *opt);
+
+/* out = H(mu) in (dagger = 0) or H(mu)^dagger in (dagger != 0) for nsrc
+ * sources; H^dagger = gamma5 D_w(-mu) (gamma5-hermiticity of Eq. WD_op).
+ * in and out must not overlap.  Arithmetic in the context's precision. */
+int ov_apply_H(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+               int32_t nsrc, const void *in, void *out, int32_t dagger);
+
+/* x ~ sgn(H(mu)) b by k steps of two-sided Lanczos (Sec. 1 and 2, the TSL of
+ * Bloch et al.), one independent Krylov recurrence per source:
+ *   v_1 = w_1 = b/||b||; T_k tridiagonal; x = ||b|| V_k sgn(T_k) e_1.
+ * 2 <= k <= 4096.  info may be NULL. */
+int ov_tsl_sign(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                int32_t nsrc, const void *b, int32_t k, void *x, ov_tsl_info *info);
+
+/* Vector-Jacobian product of the k-step TSL map: with L = sum_src Re <xbar, x>,
+ *   dU[V][4][3][3] (device, complex128) = dL/dRe U + i dL/dIm U   (all 9 entries
+ *                                          independent, no SU(3) projection)
+ *   *dmu (host double)                   = dL/dmu.
+ * The forward pass is recomputed; the reverse sweep differentiates every step
+ * of it, including the re-biorthogonalisation, and the k x k sign through its
+ * Frechet adjoint, taken from the Theorem-1 block matrix by Newton iteration.
+ * x (device, may be NULL) receives the forward result.  info may be NULL. */
+int ov_tsl_sign_vjp(ov_context *ctx, const int32_t dims[4], const void *U, double mu,
+                    double m_w, int32_t nsrc, const void *b, int32_t k, const void *xbar,
+                    void *x, void *dU, double *dmu, ov_tsl_info *info);
+
+/* Recurrence coefficients of source `src` from the last ov_tsl_sign or
+ * ov_tsl_sign_vjp call on this context (k must equal that call's k), copied
+ * to HOST arrays: alpha[2k] and beta[2k] interleaved complex, delta[k].
+ * alpha_j = T[j][j], beta_j = T[j-1][j], delta_j = T[j][j-1] (0-based j,
+ * beta_0 = delta_0 = 0). */
+int ov_tsl_coefficients(ov_context *ctx, int32_t src, int32_t k, double *alpha, double *beta,
+                        double *delta);
+
+/* Human-readable text for a status code (static storage). */
+const char *ov_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OV_H */

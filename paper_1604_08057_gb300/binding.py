@@ -1,0 +1,187 @@
+"""Thin Python binding of the C ABI in ``include/ov.h`` (argument marshalling only).
+
+Every numerical step runs in the CUDA library; this module checks shapes and
+dtypes of torch tensors, passes their device pointers and the current CUDA
+stream, and turns status codes into exceptions.  There is no CPU path: if the
+library has not been built, ``load()`` raises.
+
+Tensor conventions (complex128, contiguous, on a CUDA device):
+    U    (Nt, Nz, Ny, Nx, 4, 3, 3)    links, direction order x, y, z, t
+    psi  (nsrc, Nt, Nz, Ny, Nx, 4, 3) or (Nt, Nz, Ny, Nx, 4, 3) for one source
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libov.so")
+
+OV_FP64, OV_MIXED = 0, 1
+_PREC = {"fp64": OV_FP64, "mixed": OV_MIXED}
+
+_lib = None
+_contexts = {}
+
+
+class OVError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {_lib.ov_strerror(status).decode()} (status {status})")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
+                ("passes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("k_reached", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
+                ("newton_iters_adj", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("min_abs_re_ritz", ctypes.c_double), ("t_ms", ctypes.c_double * 8)]
+
+    def as_dict(self) -> dict:
+        return {"k_reached": self.k_reached, "newton_iters": self.newton_iters,
+                "newton_iters_adj": self.newton_iters_adj, "t_ms": list(self.t_ms)}
+
+
+EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
+           "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_strerror"]
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    dims_t = ctypes.POINTER(ctypes.c_int32)
+    lib.ov_context_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Options), P]
+    lib.ov_context_destroy.argtypes = [P]
+    lib.ov_context_set_options.argtypes = [P, ctypes.POINTER(Options)]
+    lib.ov_apply_H.argtypes = [P, dims_t, P, D, D, I32, P, P, I32]
+    lib.ov_tsl_sign.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, ctypes.POINTER(Info)]
+    lib.ov_tsl_sign_vjp.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, P, P,
+                                    ctypes.POINTER(D), ctypes.POINTER(Info)]
+    lib.ov_tsl_coefficients.argtypes = [P, I32, I32, P, P, P]
+    lib.ov_strerror.argtypes = [ctypes.c_int]
+    lib.ov_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+    lib.ov_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise OVError(status, what)
+
+
+def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=None):
+    """A cached library context for (device, current stream, options)."""
+    lib = load()
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    key = (dev.index, stream, precision, rebiorth, passes)
+    if key not in _contexts:
+        opt = Options(_PREC[precision], rebiorth, passes)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            _check(lib.ov_context_create(ctypes.byref(h), ctypes.byref(opt), ctypes.c_void_p(stream)),
+                   "ov_context_create")
+        _contexts[key] = h
+    return _contexts[key]
+
+
+def _dims(u: torch.Tensor):
+    if u.dtype != torch.complex128 or not u.is_cuda or u.dim() != 7 or tuple(u.shape[4:]) != (4, 3, 3):
+        raise ValueError("U must be complex128 CUDA (Nt, Nz, Ny, Nx, 4, 3, 3)")
+    nt, nz, ny, nx = u.shape[:4]
+    return (ctypes.c_int32 * 4)(nx, ny, nz, nt)
+
+
+def _spinors(psi: torch.Tensor, u: torch.Tensor):
+    if psi.dtype != torch.complex128 or not psi.is_cuda:
+        raise ValueError("spinor fields must be complex128 CUDA tensors")
+    lat = tuple(u.shape[:4]) + (4, 3)
+    if tuple(psi.shape) == lat:
+        return psi.contiguous().unsqueeze(0), True
+    if psi.dim() == 7 and tuple(psi.shape[1:]) == lat:
+        return psi.contiguous(), False
+    raise ValueError(f"spinor shape {tuple(psi.shape)} does not match the lattice {lat}")
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def apply_H(u, mu, m_w, psi, dagger=False, precision="fp64"):
+    """H(mu) psi or H(mu)^dagger psi."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    p, single = _spinors(psi, u)
+    out = torch.empty_like(p)
+    ctx = context(precision)
+    _check(lib.ov_apply_H(ctx, dims, _ptr(u), float(mu), float(m_w), p.shape[0], _ptr(p), _ptr(out),
+                          int(bool(dagger))), "ov_apply_H")
+    return out[0] if single else out
+
+
+def tsl_sign(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2, return_info=False):
+    """x ~ sgn(H(mu)) b by k-step two-sided Lanczos (per source)."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    x = torch.empty_like(bb)
+    info = Info()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_tsl_sign(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
+                           _ptr(x), ctypes.byref(info)), "ov_tsl_sign")
+    x = x[0] if single else x
+    return (x, info.as_dict()) if return_info else x
+
+
+def tsl_sign_vjp(u, mu, m_w, b, k, xbar, precision="fp64", rebiorth=1, passes=2, want_x=True,
+                 return_info=False):
+    """(dU, dmu, x) for L = sum_src Re <xbar, x>."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    xb, _ = _spinors(xbar, u)
+    if xb.shape != bb.shape:
+        raise ValueError("xbar must have the shape of b")
+    x = torch.empty_like(bb) if want_x else None
+    du = torch.empty_like(u)
+    dmu = ctypes.c_double(0.0)
+    info = Info()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_tsl_sign_vjp(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
+                               _ptr(xb), _ptr(x) if x is not None else None, _ptr(du),
+                               ctypes.byref(dmu), ctypes.byref(info)), "ov_tsl_sign_vjp")
+    if x is not None and single:
+        x = x[0]
+    out = (du, dmu.value, x)
+    return out + (info.as_dict(),) if return_info else out
+
+
+def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2):
+    """(alpha, beta, delta) of the last TSL call on the matching context (host numpy)."""
+    import numpy as np
+    lib = load()
+    ctx = context(precision, rebiorth, passes)
+    a = np.zeros(k, dtype=np.complex128)
+    b = np.zeros(k, dtype=np.complex128)
+    d = np.zeros(k, dtype=np.float64)
+    _check(lib.ov_tsl_coefficients(ctx, int(src), int(k), a.ctypes.data_as(ctypes.c_void_p),
+                                   b.ctypes.data_as(ctypes.c_void_p), d.ctypes.data_as(ctypes.c_void_p)),
+           "ov_tsl_coefficients")
+    return a, b, d

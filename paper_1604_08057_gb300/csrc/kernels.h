@@ -1,0 +1,117 @@
+// Host-visible declarations of the kernel launchers and the device-side
+// per-source state shared by the forward recurrence and the reverse sweep.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace ov {
+
+// error bits written by kernels into SrcScal::err
+enum : int { ERRB_BREAKDOWN = 1, ERRB_NONFINITE = 2, ERRB_SINGULAR = 4 };
+
+// Per-source scalars kept in device memory for the whole call.
+struct SrcScal {
+  double beta0;          // ||b||
+  zd sv, sw;             // v_j = sv * r_{j-1},  w_j = sw * s_{j-1}
+  int err;               // ERRB_* bits
+  int err_step;          // first step that set an error bit
+  // reverse sweep
+  zd g_alpha;            // gradient of alpha_j of the current step
+  zd carry_beta;         // gradient of beta_{j} carried from step j (for step j-1)
+  double carry_delta;
+  zd cr1, cr2, cs1, cs2; // g_r = cr1 Gv_{j+1} + cr2 w_{j+1};  g_s = cs1 Gw_{j+1} + cs2 v_{j+1}
+};
+
+// Everything a lattice kernel needs, passed by value.
+template <typename R>
+struct Lat {
+  Geom g;
+  R kappa, ef, efinv;        // kappa, e^{mu}, e^{-mu}
+  const R* u;                // internal links (72 V reals)
+  int nsrc, k;
+  int64_t vs;                // reals per lattice vector (padded)
+  R* bv;                     // basis V: [src][k][vs]
+  R* bw;                     // basis W: [src][k][vs]
+  R* p; R* q; R* r; R* s;    // per-source scratch vectors [src][vs]
+  SrcScal* sc;               // [src]
+  zd* alpha;                 // [src][k]
+  zd* beta;                  // [src][k]  (index j couples j-1 and j)
+  double* delta;             // [src][k]
+  zd* part;                  // reduction partials
+  unsigned* cnt;             // last-block counters [src][16]
+  int64_t part_stride;       // zd per source in `part`
+  OV_HD R* basis_v(int src, int j) const { return bv + ((int64_t)src * k + j) * vs; }
+  OV_HD R* basis_w(int src, int j) const { return bw + ((int64_t)src * k + j) * vs; }
+};
+
+// reverse-sweep buffers
+template <typename R>
+struct Rev {
+  R* gv; R* gw;              // complete gradients of v_{j+1}, w_{j+1}: [src][vs]
+  R* gv_new; R* gw_new;      // gradients being formed for v_j, w_j
+  R* gr_ring; R* gs_ring; R* gp_ring;   // [m][src][vs]
+  int m;                     // ring length
+  const R* xbar;             // [src][vs]
+  const zd* y;               // [src][k]
+  const zd* gaT; const zd* gbT; const double* gdT;   // [src][k] gradients of T entries
+  zd* ev; zd* ew;            // lazy projection-adjoint coefficients [src][nreb_max][k]
+  int* reb_steps;            // [nreb_max] step of each recorded projection (host-ordered)
+  int nreb_max;
+  double* force;             // FP64 accumulator, 36 complex * V  (zd, layout e*V + x)
+  double* dmu;               // single accumulator
+  zd* dmu_part;              // partials for dmu
+  unsigned* dmu_cnt;
+  int nsrc;
+  int64_t vs;
+  OV_HD R* ring(R* base, int slot, int src) const { return base + ((int64_t)slot * nsrc + src) * vs; }
+};
+
+// ---- lattice launchers (precision R = double or float) ----
+template <typename R> void pack_spinors(const double* src_aos, R* dst, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
+template <typename R> void unpack_spinors(const R* src, double* dst_aos, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
+template <typename R> void pack_links(const double* src_aos, R* dst, int64_t V, cudaStream_t st);
+template <typename R> void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st);
+
+template <typename R> void tsl_init(const Lat<R>& L, cudaStream_t st);
+template <typename R> void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st);
+template <typename R> void tsl_update(const Lat<R>& L, int j, bool finalize, cudaStream_t st);
+// projection of (r, s) against bases (A: dots with `a` vector, B: dots with `b` vector).
+// mode 0 (forward):  c = W^dag r, d = V^dag s;  r -= V c, s -= W d
+// mode 1 (adjoint):  e_r = V^dag g_r, e_s = W^dag g_s;  g_r -= W e_r, g_s -= V e_s
+template <typename R> void tsl_project(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_src_stride,
+                                       zd* coef, zd* cpart, bool finalize_omega, cudaStream_t st);
+template <typename R> void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_src_stride, zd* out,
+                                      zd* cpart, cudaStream_t st);
+template <typename R> void combine(const Lat<R>& L, int nvec, const zd* y, double* out_aos, cudaStream_t st);
+
+// reverse sweep
+template <typename R> void rev_init(const Lat<R>& L, const Rev<R>& B, cudaStream_t st);
+template <typename R> void rev_dots(const Lat<R>& L, const Rev<R>& B, int j, cudaStream_t st);
+template <typename R> void rev_form(const Lat<R>& L, const Rev<R>& B, int j, int slot, bool with_dots, cudaStream_t st);
+template <typename R> void rev_proj_record(const Lat<R>& L, const Rev<R>& B, int j, int m_index, const zd* coef, cudaStream_t st);
+template <typename R> void rev_alpha_dots(const Lat<R>& L, const Rev<R>& B, int j, int slot, cudaStream_t st);
+template <typename R> void rev_stencil(const Lat<R>& L, const Rev<R>& B, int j, int slot, int prev_slot,
+                                       int nrec, cudaStream_t st);
+template <typename R> void force_flush(const Lat<R>& L, const Rev<R>& B, const int* steps_dev, int nterms,
+                                       int first_slot, cudaStream_t st);
+void unpack_force(const double* force, double* du_aos, int64_t V, cudaStream_t st);
+
+// ---- dense FP64 k x k (row-major, complex) ----
+void dense_build_t(const zd* alpha, const zd* beta, const double* delta, int k, zd* T, cudaStream_t st);
+void dense_adjoint(const zd* A, zd* B, int k, cudaStream_t st);
+void dense_copy(const zd* A, zd* B, int64_t n, cudaStream_t st);
+void dense_zero(zd* A, int64_t n, cudaStream_t st);
+// in-place inverse by Gauss-Jordan with partial pivoting; logdet[0] += sum log|pivot|
+void dense_inverse(zd* X, int k, int* ipiv, zd* prow, zd* col, double* logdet, int* err, cudaStream_t st);
+void dense_gemm(const zd* A, const zd* B, zd* C, int k, cudaStream_t st);   // C = A B
+// Xn = 0.5 (g X + s Xi / g) with g = |det|^(-1/k) from *logdet when scaling, else 1;
+// stats[0] += w |Xn - X|^2, stats[1] += w |Xn|^2 (deterministic order)
+void dense_newton_combine(const zd* X, const zd* Xi, zd* Xn, int k, const double* logdet, int scaling,
+                          double s, double w, double* stats, zd* part, unsigned* cnt, cudaStream_t st);
+void dense_set_column0(zd* E, const zd* gy, int64_t gy_stride, double beta0, int k, cudaStream_t st);
+void dense_extract_y(const zd* F, double beta0, int k, zd* y, cudaStream_t st);
+void dense_extract_tri(const zd* E, int k, zd* ga, zd* gb, double* gd, cudaStream_t st);
+
+}  // namespace ov

@@ -1,0 +1,931 @@
+// Lattice-vector kernels: layout conversion, H / H^dagger application, the
+// two-sided Lanczos step (stencil pair + biorthogonality dots, three-term
+// update), classical Gram-Schmidt re-biorthogonalisation, basis combination,
+// and the reverse sweep with the gauge-force contraction.
+//
+// Thread mapping: one thread per lattice site (blockIdx.y = source) unless a
+// kernel says otherwise.  All reductions are deterministic: per-block partials
+// are summed in block order by the last block to finish.
+#include "dslash.cuh"
+#include "kernels.h"
+
+namespace ov {
+
+constexpr int BS = 128;   // threads per block for site kernels
+constexpr int NB = 8;     // basis vectors per block in the projection dots
+
+static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ---------------------------------------------------------------------------
+// layout conversion
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_pack_spinors(const double* __restrict__ aos, R* __restrict__ dst, int64_t V, int64_t vs) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  if (x >= V) return;
+  const double2* in = reinterpret_cast<const double2*>(aos) + ((int64_t)src * V + x) * 12;
+  Spinor<R> o;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) { double2 t = in[c]; o.c[c] = mk<R>((R)t.x, (R)t.y); }
+  store_spinor(dst + src * vs, V, x, o);
+}
+
+template <typename R>
+__global__ void k_unpack_spinors(const R* __restrict__ f, double* __restrict__ aos, int64_t V, int64_t vs) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  if (x >= V) return;
+  Spinor<R> o;
+  load_spinor(f + src * vs, V, x, o);
+  double2* out = reinterpret_cast<double2*>(aos) + ((int64_t)src * V + x) * 12;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) out[c] = make_double2((double)o.c[c].re, (double)o.c[c].im);
+}
+
+template <typename R>
+__global__ void k_pack_links(const double* __restrict__ aos, R* __restrict__ u, int64_t V) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (x >= V) return;
+  const double2* in = reinterpret_cast<const double2*>(aos) + x * 36;
+  for (int e = 0; e < 36; ++e) {
+    double2 t = in[e];
+    u[2 * (e * V + x)] = (R)t.x;
+    u[2 * (e * V + x) + 1] = (R)t.y;
+  }
+}
+
+__global__ void k_unpack_force(const double* __restrict__ f, double* __restrict__ du, int64_t V) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (x >= V) return;
+  double2* out = reinterpret_cast<double2*>(du) + x * 36;
+  const double2* in = reinterpret_cast<const double2*>(f);
+  for (int e = 0; e < 36; ++e) out[e] = in[e * V + x];
+}
+
+template <typename R>
+void pack_spinors(const double* aos, R* dst, int nsrc, int64_t V, int64_t vs, cudaStream_t st) {
+  k_pack_spinors<R><<<dim3(nblocks(V, BS), nsrc), BS, 0, st>>>(aos, dst, V, vs);
+}
+template <typename R>
+void unpack_spinors(const R* f, double* aos, int nsrc, int64_t V, int64_t vs, cudaStream_t st) {
+  k_unpack_spinors<R><<<dim3(nblocks(V, BS), nsrc), BS, 0, st>>>(f, aos, V, vs);
+}
+template <typename R>
+void pack_links(const double* aos, R* u, int64_t V, cudaStream_t st) {
+  k_pack_links<R><<<nblocks(V, BS), BS, 0, st>>>(aos, u, V);
+}
+void unpack_force(const double* f, double* du, int64_t V, cudaStream_t st) {
+  k_unpack_force<<<nblocks(V, BS), BS, 0, st>>>(f, du, V);
+}
+
+// ---------------------------------------------------------------------------
+// H and H^dagger
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(BS) k_apply_h(Lat<R> L, const R* __restrict__ in, R* __restrict__ out,
+                                                int dagger) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  if (x >= L.g.V) return;
+  Spinor<R> o;
+  const R ft = dagger ? L.efinv : L.ef, fti = dagger ? L.ef : L.efinv;
+  h_site(in + src * L.vs, L.u, L.g, x, L.kappa, ft, fti, o);
+  store_spinor(out + src * L.vs, L.g.V, x, o);
+}
+template <typename R>
+void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st) {
+  k_apply_h<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, in, out, dagger);
+}
+
+// ---------------------------------------------------------------------------
+// helpers for the recurrence scalars
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool finite_z(zd a) { return isfinite(a.re) && isfinite(a.im); }
+
+__device__ __forceinline__ void flag_error(SrcScal& sc, int bit, int step) {
+  if (sc.err == 0) sc.err_step = step;
+  sc.err |= bit;
+}
+
+// Sum NV partial slots of this source (fixed block order); thread 0 gets the result.
+template <int NV>
+__device__ __forceinline__ void sum_partials(const zd* part, int nblk, zd (&out)[NV], zd* scratch) {
+  zd v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = mk(0.0, 0.0);
+  // each thread takes a contiguous range of blocks, so the order is fixed
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = v[i] + ld_cg(part + i * nblk + b);
+  }
+  block_sum<NV>(v, scratch);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = v[i];
+}
+
+// omega = s^dag r, rr = r^dag r, ss = s^dag s  ->  delta_{j+1}, beta_{j+1} and the next scales
+template <typename R>
+__device__ void omega_finalize(const Lat<R>& L, int src, int j, zd om, double rr, double ss) {
+  SrcScal& sc = L.sc[src];
+  const double aom = sqrt(om.re * om.re + om.im * om.im);
+  if (!finite_z(om) || !isfinite(rr) || !isfinite(ss)) {
+    flag_error(sc, ERRB_NONFINITE, j + 1);
+    return;
+  }
+  if (aom <= 1e-14 * sqrt(rr * ss)) {
+    flag_error(sc, ERRB_BREAKDOWN, j + 1);
+    return;
+  }
+  const double d = sqrt(aom);
+  const zd bt = mk(om.re / d, om.im / d);
+  L.beta[(int64_t)src * L.k + j + 1] = bt;
+  L.delta[(int64_t)src * L.k + j + 1] = d;
+  sc.sv = mk(1.0 / d, 0.0);
+  sc.sw = zdiv(mk(1.0, 0.0), conj(bt));
+}
+
+// ---------------------------------------------------------------------------
+// TSL forward: initialisation (beta_0 = ||b||)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(BS) k_tsl_init(Lat<R> L) {
+  __shared__ zd scratch[32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  zd v[1] = {mk(0.0, 0.0)};
+  if (x < L.g.V) {
+    Spinor<R> b;
+    load_spinor(L.r + src * L.vs, L.g.V, x, b);
+    v[0] = spinor_dot(b, b);
+  }
+  block_sum<1>(v, scratch);
+  zd* part = L.part + src * L.part_stride;
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (arrive_last(L.cnt + src * 16 + 0, gridDim.x)) {
+    zd s[1];
+    sum_partials<1>(part, gridDim.x, s, scratch);
+    if (threadIdx.x == 0) {
+      SrcScal& sc = L.sc[src];
+      sc.err = 0;
+      sc.err_step = -1;
+      const double b0 = sqrt(s[0].re);
+      sc.beta0 = b0;
+      if (!(b0 > 0.0) || !isfinite(b0)) flag_error(sc, ERRB_NONFINITE, 0);
+      sc.sv = mk(1.0 / b0, 0.0);
+      sc.sw = mk(1.0 / b0, 0.0);
+      L.beta[(int64_t)src * L.k] = mk(0.0, 0.0);
+      L.delta[(int64_t)src * L.k] = 0.0;
+    }
+  }
+}
+template <typename R>
+void tsl_init(const Lat<R>& L, cudaStream_t st) {
+  k_tsl_init<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L);
+}
+
+// ---------------------------------------------------------------------------
+// TSL step j: v_j = sv r_{j-1}, w_j = sw s_{j-1} stored in the bases;
+// p = H v_j, q = H^dag w_j; alpha_j = w_j^dag p.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(BS) k_tsl_stencil(Lat<R> L, int j, int need_q) {
+  __shared__ zd scratch[32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  const R* rp = L.r + src * L.vs;
+  const R* sp = L.s + src * L.vs;
+  zd v[1] = {mk(0.0, 0.0)};
+  if (x < V && L.sc[src].err == 0) {
+    const cplx<R> sv = cast<R>(L.sc[src].sv), sw = cast<R>(L.sc[src].sw);
+    Spinor<R> a, w, o;
+    load_spinor(rp, V, x, a);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) a.c[c] = sv * a.c[c];
+    store_spinor(L.basis_v(src, j), V, x, a);
+    load_spinor(sp, V, x, w);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) w.c[c] = sw * w.c[c];
+    store_spinor(L.basis_w(src, j), V, x, w);
+    h_site(rp, L.u, L.g, x, L.kappa, L.ef, L.efinv, o);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) o.c[c] = sv * o.c[c];
+    store_spinor(L.p + src * L.vs, V, x, o);
+    v[0] = spinor_dot(w, o);
+    if (need_q) {
+      h_site(sp, L.u, L.g, x, L.kappa, L.efinv, L.ef, o);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) o.c[c] = sw * o.c[c];
+      store_spinor(L.q + src * L.vs, V, x, o);
+    }
+  }
+  block_sum<1>(v, scratch);
+  zd* part = L.part + src * L.part_stride;
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (arrive_last(L.cnt + src * 16 + 1, gridDim.x)) {
+    zd s[1];
+    sum_partials<1>(part, gridDim.x, s, scratch);
+    if (threadIdx.x == 0) {
+      SrcScal& sc = L.sc[src];
+      if (!finite_z(s[0])) flag_error(sc, ERRB_NONFINITE, j);
+      L.alpha[(int64_t)src * L.k + j] = s[0];
+    }
+  }
+}
+template <typename R>
+void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st) {
+  k_tsl_stencil<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, j, need_q ? 1 : 0);
+}
+
+// r = p - alpha_j v_j - beta_j v_{j-1};  s = q - conj(alpha_j) w_j - delta_j w_{j-1}
+template <typename R>
+__global__ void __launch_bounds__(BS) k_tsl_update(Lat<R> L, int j, int finalize) {
+  __shared__ zd scratch[3 * 32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  zd v[3] = {mk(0.0, 0.0), mk(0.0, 0.0), mk(0.0, 0.0)};
+  if (x < V && L.sc[src].err == 0) {
+    const cplx<R> al = cast<R>(L.alpha[(int64_t)src * L.k + j]);
+    const cplx<R> alc = conj(al);
+    Spinor<R> r, s, t;
+    load_spinor(L.p + src * L.vs, V, x, r);
+    load_spinor(L.q + src * L.vs, V, x, s);
+    load_spinor(L.basis_v(src, j), V, x, t);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) r.c[c] = r.c[c] - al * t.c[c];
+    load_spinor(L.basis_w(src, j), V, x, t);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) s.c[c] = s.c[c] - alc * t.c[c];
+    if (j > 0) {
+      const cplx<R> bt = cast<R>(L.beta[(int64_t)src * L.k + j]);
+      const R dl = (R)L.delta[(int64_t)src * L.k + j];
+      load_spinor(L.basis_v(src, j - 1), V, x, t);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) r.c[c] = r.c[c] - bt * t.c[c];
+      load_spinor(L.basis_w(src, j - 1), V, x, t);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) s.c[c] = s.c[c] - dl * t.c[c];
+    }
+    store_spinor(L.r + src * L.vs, V, x, r);
+    store_spinor(L.s + src * L.vs, V, x, s);
+    if (finalize) {
+      v[0] = spinor_dot(s, r);
+      v[1] = spinor_dot(r, r);
+      v[2] = spinor_dot(s, s);
+    }
+  }
+  if (!finalize) return;   // uniform across the grid
+  block_sum<3>(v, scratch);
+  zd* part = L.part + src * L.part_stride;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) part[i * gridDim.x + blockIdx.x] = v[i];
+  }
+  if (arrive_last(L.cnt + src * 16 + 2, gridDim.x)) {
+    zd s[3];
+    sum_partials<3>(part, gridDim.x, s, scratch);
+    if (threadIdx.x == 0 && L.sc[src].err == 0) omega_finalize(L, src, j, s[0], s[1].re, s[2].re);
+  }
+}
+template <typename R>
+void tsl_update(const Lat<R>& L, int j, bool finalize, cudaStream_t st) {
+  k_tsl_update<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, j, finalize ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Classical Gram-Schmidt against the stored bases (basis indices 0..j).
+//   side A: coefA_i = DA_i^dag a,  a -= sum_i coefA_i UA_i
+//   side B: coefB_i = DB_i^dag b,  b -= sum_i coefB_i UB_i
+// mode 0 (forward):  DA = W, UA = V, DB = V, UB = W   (a = r, b = s)
+// mode 1 (adjoint):  DA = V, UA = W, DB = W, UB = V   (a = g_r, b = g_s)
+// coef layout: [src][2*i + side];  cpart: [src][2*i + side][site block]
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(BS) k_proj_dots(Lat<R> L, int nb, int mode, const R* __restrict__ a,
+                                                   const R* __restrict__ b, int64_t ab_stride,
+                                                   zd* __restrict__ cpart, int64_t cp_stride) {
+  __shared__ zd scratch[2 * NB * 32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.z;
+  const int i0 = blockIdx.y * NB;
+  const int64_t V = L.g.V;
+  SiteDot<R> acc[2 * NB];
+#pragma unroll
+  for (int t = 0; t < 2 * NB; ++t) acc[t].zero();
+  if (x < V) {
+    Spinor<R> va, vb, e;
+    load_spinor(a + src * ab_stride, V, x, va);
+    if (b) load_spinor(b + src * ab_stride, V, x, vb);
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int i = i0 + t;
+      if (i < nb) {
+        const R* da = mode == 0 ? L.basis_w(src, i) : L.basis_v(src, i);
+        load_spinor(da, V, x, e);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[2 * t].add(e.c[c], va.c[c]);
+        if (b) {
+          const R* db = mode == 0 ? L.basis_v(src, i) : L.basis_w(src, i);
+          load_spinor(db, V, x, e);
+#pragma unroll
+          for (int c = 0; c < 12; ++c) acc[2 * t + 1].add(e.c[c], vb.c[c]);
+        }
+      }
+    }
+  }
+  zd v[2 * NB];
+#pragma unroll
+  for (int t = 0; t < 2 * NB; ++t) v[t] = acc[t].value();
+  block_sum<2 * NB>(v, scratch);
+  if (threadIdx.x == 0) {
+    zd* cp = cpart + src * cp_stride;
+#pragma unroll
+    for (int t = 0; t < 2 * NB; ++t) {
+      const int i = i0 + t / 2;
+      if (i < nb) cp[(int64_t)(2 * i + (t & 1)) * gridDim.x + blockIdx.x] = v[t];
+    }
+  }
+}
+
+__global__ void k_proj_reduce(const zd* __restrict__ cpart, int64_t cp_stride, int nsb, int nb,
+                              zd* __restrict__ coef, int64_t coef_stride) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;   // 2*i + side
+  const int src = blockIdx.y;
+  if (t >= 2 * nb) return;
+  const zd* cp = cpart + src * cp_stride + (int64_t)t * nsb;
+  zd s = mk(0.0, 0.0);
+  for (int b = 0; b < nsb; ++b) s = s + cp[b];
+  coef[src * coef_stride + t] = s;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(BS) k_proj_update(Lat<R> L, int nb, int mode, R* __restrict__ a,
+                                                     R* __restrict__ b, int64_t ab_stride,
+                                                     const zd* __restrict__ coef, int64_t coef_stride,
+                                                     int j, int finalize) {
+  __shared__ zd cs[2 * 64];
+  __shared__ zd scratch[3 * 32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  const bool active = x < V;
+  Spinor<R> ca, cb, e;
+  spinor_zero(ca);
+  spinor_zero(cb);
+  const zd* cf = coef + src * coef_stride;
+  for (int i0 = 0; i0 < nb; i0 += 64) {
+    const int n = min(64, nb - i0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * n; t += blockDim.x) cs[t] = cf[2 * i0 + t];
+    __syncthreads();
+    if (active) {
+      for (int t = 0; t < n; ++t) {
+        const int i = i0 + t;
+        const R* ua = mode == 0 ? L.basis_v(src, i) : L.basis_w(src, i);
+        const cplx<R> c0 = cast<R>(cs[2 * t]);
+        load_spinor(ua, V, x, e);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) cmac(ca.c[c], c0, e.c[c]);
+        if (b) {
+          const R* ub = mode == 0 ? L.basis_w(src, i) : L.basis_v(src, i);
+          const cplx<R> c1 = cast<R>(cs[2 * t + 1]);
+          load_spinor(ub, V, x, e);
+#pragma unroll
+          for (int c = 0; c < 12; ++c) cmac(cb.c[c], c1, e.c[c]);
+        }
+      }
+    }
+  }
+  zd v[3] = {mk(0.0, 0.0), mk(0.0, 0.0), mk(0.0, 0.0)};
+  if (active) {
+    Spinor<R> r, s;
+    load_spinor(a + src * ab_stride, V, x, r);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) r.c[c] = r.c[c] - ca.c[c];
+    store_spinor(a + src * ab_stride, V, x, r);
+    if (b) {
+      load_spinor(b + src * ab_stride, V, x, s);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) s.c[c] = s.c[c] - cb.c[c];
+      store_spinor(b + src * ab_stride, V, x, s);
+      if (finalize) {
+        v[0] = spinor_dot(s, r);
+        v[1] = spinor_dot(r, r);
+        v[2] = spinor_dot(s, s);
+      }
+    }
+  }
+  if (!finalize) return;
+  block_sum<3>(v, scratch);
+  zd* part = L.part + src * L.part_stride;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 3; ++i) part[i * gridDim.x + blockIdx.x] = v[i];
+  }
+  if (arrive_last(L.cnt + src * 16 + 3, gridDim.x)) {
+    zd s3[3];
+    sum_partials<3>(part, gridDim.x, s3, scratch);
+    if (threadIdx.x == 0 && L.sc[src].err == 0) omega_finalize(L, src, j, s3[0], s3[1].re, s3[2].re);
+  }
+}
+
+template <typename R>
+void tsl_project(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_stride, zd* coef, zd* cpart,
+                 bool finalize, cudaStream_t st) {
+  const int nb = j + 1;
+  const unsigned nsb = nblocks(L.g.V, BS);
+  const int64_t cp_stride = (int64_t)2 * L.k * nsb;
+  k_proj_dots<R><<<dim3(nsb, nblocks(nb, NB), L.nsrc), BS, 0, st>>>(L, nb, mode, a, b, ab_stride, cpart,
+                                                                     cp_stride);
+  k_proj_reduce<<<dim3(nblocks(2 * nb, 128), L.nsrc), 128, 0, st>>>(cpart, cp_stride, nsb, nb, coef,
+                                                                      2 * (int64_t)L.k);
+  k_proj_update<R><<<dim3(nsb, L.nsrc), BS, 0, st>>>(L, nb, mode, a, b, ab_stride, coef, 2 * (int64_t)L.k, j,
+                                                      finalize ? 1 : 0);
+}
+
+// out[src][i] = v_i^dag x  for i < nvec (dots of the V basis with one vector per source)
+template <typename R>
+void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_stride, zd* out, zd* cpart,
+                cudaStream_t st) {
+  const unsigned nsb = nblocks(L.g.V, BS);
+  const int64_t cp_stride = (int64_t)2 * L.k * nsb;
+  // mode 1 makes side A dot the V basis
+  k_proj_dots<R><<<dim3(nsb, nblocks(nvec, NB), L.nsrc), BS, 0, st>>>(L, nvec, 1, x, nullptr, x_stride,
+                                                                       cpart, cp_stride);
+  k_proj_reduce<<<dim3(nblocks(2 * nvec, 128), L.nsrc), 128, 0, st>>>(cpart, cp_stride, nsb, nvec, out,
+                                                                        2 * (int64_t)L.k);
+}
+
+// x[src] = sum_i y_i v_i, written as interleaved complex128 [src][V][12]
+template <typename R>
+__global__ void __launch_bounds__(BS) k_combine(Lat<R> L, int nvec, const zd* __restrict__ y,
+                                                 double* __restrict__ out) {
+  __shared__ zd ys[64];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  zd acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = mk(0.0, 0.0);
+  for (int i0 = 0; i0 < nvec; i0 += 32) {
+    const int n = min(32, nvec - i0);
+    __syncthreads();
+    if (threadIdx.x < n) ys[threadIdx.x] = y[(int64_t)src * L.k + i0 + threadIdx.x];
+    __syncthreads();
+    if (x < V) {
+      Spinor<R> part, e;
+      spinor_zero(part);
+      for (int t = 0; t < n; ++t) {
+        load_spinor(L.basis_v(src, i0 + t), V, x, e);
+        const cplx<R> yc = cast<R>(ys[t]);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) cmac(part.c[c], yc, e.c[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 12; ++c) acc[c] = acc[c] + mk((double)part.c[c].re, (double)part.c[c].im);
+    }
+  }
+  if (x < V) {
+    double2* o = reinterpret_cast<double2*>(out) + ((int64_t)src * V + x) * 12;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) o[c] = make_double2(acc[c].re, acc[c].im);
+  }
+}
+template <typename R>
+void combine(const Lat<R>& L, int nvec, const zd* y, double* out, cudaStream_t st) {
+  k_combine<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, nvec, y, out);
+}
+
+// ---------------------------------------------------------------------------
+// Reverse sweep
+// ---------------------------------------------------------------------------
+// R1: A1 = v_{j+1}^dag Gv, A2 = w_{j+1}^dag Gw  ->  g_delta, g_beta, g_omega and the
+// coefficients of g_r = Gv/delta + conj(beta) g_omega w_{j+1},  g_s = Gw/beta + delta conj(g_omega) v_{j+1}
+template <typename R>
+__global__ void __launch_bounds__(BS) k_rev_dots(Lat<R> L, Rev<R> B, int j) {
+  __shared__ zd scratch[2 * 32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  zd v[2] = {mk(0.0, 0.0), mk(0.0, 0.0)};
+  if (x < V) {
+    Spinor<R> a, g;
+    load_spinor(L.basis_v(src, j + 1), V, x, a);
+    load_spinor(B.gv + src * L.vs, V, x, g);
+    v[0] = spinor_dot(a, g);
+    load_spinor(L.basis_w(src, j + 1), V, x, a);
+    load_spinor(B.gw + src * L.vs, V, x, g);
+    v[1] = spinor_dot(a, g);
+  }
+  block_sum<2>(v, scratch);
+  zd* part = L.part + src * L.part_stride;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = v[0];
+    part[gridDim.x + blockIdx.x] = v[1];
+  }
+  if (arrive_last(L.cnt + src * 16 + 4, gridDim.x)) {
+    zd s[2];
+    sum_partials<2>(part, gridDim.x, s, scratch);
+    if (threadIdx.x == 0) {
+      SrcScal& sc = L.sc[src];
+      const int64_t o = (int64_t)src * L.k + j + 1;
+      const double d = L.delta[o];
+      const zd bt = L.beta[o];
+      const zd om = mk(bt.re * d, bt.im * d);
+      const double aom = d * d;
+      double g_d = B.gdT[o] + sc.carry_delta - s[0].re / d;
+      zd g_b = B.gbT[o] + sc.carry_beta - zdiv(conj(s[1]), conj(bt));
+      zd g_w = mk(g_b.re / d, g_b.im / d);
+      g_d -= (om.re * g_b.re + om.im * g_b.im) / (d * d);      // Re(conj(om) g_b)
+      const double f = g_d / (2.0 * d * aom);
+      g_w = g_w + mk(f * om.re, f * om.im);
+      sc.cr1 = mk(1.0 / d, 0.0);
+      sc.cr2 = conj(bt) * g_w;
+      sc.cs1 = zdiv(mk(1.0, 0.0), bt);
+      sc.cs2 = mk(d * g_w.re, -d * g_w.im);
+      if (!finite_z(sc.cr2) || !finite_z(sc.cs2)) flag_error(sc, ERRB_NONFINITE, j);
+    }
+  }
+}
+template <typename R>
+void rev_dots(const Lat<R>& L, const Rev<R>& B, int j, cudaStream_t st) {
+  k_rev_dots<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j);
+}
+
+// D1 = v_j^dag g_r, D2 = w_j^dag g_s, D3 = v_{j-1}^dag g_r, D4 = w_{j-1}^dag g_s -> g_alpha, carries
+template <typename R>
+__device__ void alpha_epilogue(const Lat<R>& L, const Rev<R>& B, int src, int j, const zd (&s)[4]) {
+  SrcScal& sc = L.sc[src];
+  const int64_t o = (int64_t)src * L.k + j;
+  sc.g_alpha = B.gaT[o] - s[0] - conj(s[1]);
+  if (j > 0) {
+    sc.carry_beta = -s[2];
+    sc.carry_delta = -s[3].re;
+  } else {
+    sc.carry_beta = mk(0.0, 0.0);
+    sc.carry_delta = 0.0;
+  }
+}
+
+template <typename R>
+__device__ void alpha_dots_site(const Lat<R>& L, int src, int j, int64_t x, const Spinor<R>& gr,
+                                const Spinor<R>& gs, zd (&v)[4]) {
+  Spinor<R> e;
+  load_spinor(L.basis_v(src, j), L.g.V, x, e);
+  v[0] = spinor_dot(e, gr);
+  load_spinor(L.basis_w(src, j), L.g.V, x, e);
+  v[1] = spinor_dot(e, gs);
+  if (j > 0) {
+    load_spinor(L.basis_v(src, j - 1), L.g.V, x, e);
+    v[2] = spinor_dot(e, gr);
+    load_spinor(L.basis_w(src, j - 1), L.g.V, x, e);
+    v[3] = spinor_dot(e, gs);
+  }
+}
+
+// R2: g_r, g_s into the ring slot; optionally the four dots for g_alpha
+template <typename R>
+__global__ void __launch_bounds__(BS) k_rev_form(Lat<R> L, Rev<R> B, int j, int slot, int with_dots) {
+  __shared__ zd scratch[4 * 32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  zd v[4] = {mk(0.0, 0.0), mk(0.0, 0.0), mk(0.0, 0.0), mk(0.0, 0.0)};
+  if (x < V) {
+    const SrcScal& sc = L.sc[src];
+    const cplx<R> cr1 = cast<R>(sc.cr1), cr2 = cast<R>(sc.cr2), cs1 = cast<R>(sc.cs1), cs2 = cast<R>(sc.cs2);
+    Spinor<R> gr, gs, e;
+    load_spinor(B.gv + src * L.vs, V, x, gr);
+    load_spinor(L.basis_w(src, j + 1), V, x, e);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) gr.c[c] = cr1 * gr.c[c] + cr2 * e.c[c];
+    load_spinor(B.gw + src * L.vs, V, x, gs);
+    load_spinor(L.basis_v(src, j + 1), V, x, e);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) gs.c[c] = cs1 * gs.c[c] + cs2 * e.c[c];
+    store_spinor(B.ring(B.gr_ring, slot, src), V, x, gr);
+    store_spinor(B.ring(B.gs_ring, slot, src), V, x, gs);
+    if (with_dots) alpha_dots_site(L, src, j, x, gr, gs, v);
+  }
+  if (!with_dots) return;
+  block_sum<4>(v, scratch);
+  zd* part = L.part + src * L.part_stride;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) part[i * gridDim.x + blockIdx.x] = v[i];
+  }
+  if (arrive_last(L.cnt + src * 16 + 5, gridDim.x)) {
+    zd s[4];
+    sum_partials<4>(part, gridDim.x, s, scratch);
+    if (threadIdx.x == 0) alpha_epilogue(L, B, src, j, s);
+  }
+}
+template <typename R>
+void rev_form(const Lat<R>& L, const Rev<R>& B, int j, int slot, bool with_dots, cudaStream_t st) {
+  k_rev_form<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j, slot, with_dots ? 1 : 0);
+}
+
+// the four dots after the projection adjoint has been applied to g_r, g_s
+template <typename R>
+__global__ void __launch_bounds__(BS) k_rev_alpha_dots(Lat<R> L, Rev<R> B, int j, int slot) {
+  __shared__ zd scratch[4 * 32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  zd v[4] = {mk(0.0, 0.0), mk(0.0, 0.0), mk(0.0, 0.0), mk(0.0, 0.0)};
+  if (x < V) {
+    Spinor<R> gr, gs;
+    load_spinor(B.ring(B.gr_ring, slot, src), V, x, gr);
+    load_spinor(B.ring(B.gs_ring, slot, src), V, x, gs);
+    alpha_dots_site(L, src, j, x, gr, gs, v);
+  }
+  block_sum<4>(v, scratch);
+  zd* part = L.part + src * L.part_stride;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) part[i * gridDim.x + blockIdx.x] = v[i];
+  }
+  if (arrive_last(L.cnt + src * 16 + 6, gridDim.x)) {
+    zd s[4];
+    sum_partials<4>(part, gridDim.x, s, scratch);
+    if (threadIdx.x == 0) alpha_epilogue(L, B, src, j, s);
+  }
+}
+template <typename R>
+void rev_alpha_dots(const Lat<R>& L, const Rev<R>& B, int j, int slot, cudaStream_t st) {
+  k_rev_alpha_dots<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j, slot);
+}
+
+// Lazy projection-adjoint coefficients of recorded projection m (at step j):
+//   acc_v[i] += -conj(beta_{j+1}) conj(e_s,i) w_{j+1},  acc_w[i] += -delta_{j+1} conj(e_r,i) v_{j+1}
+__global__ void k_rev_proj_record(zd* ev, zd* ew, int64_t e_stride, int k, int m, int j, const zd* __restrict__ coef,
+                                  int64_t coef_stride, const zd* __restrict__ beta, const double* __restrict__ delta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  if (i > j) return;
+  const zd bt = beta[(int64_t)src * k + j + 1];
+  const double d = delta[(int64_t)src * k + j + 1];
+  const zd er = coef[src * coef_stride + 2 * i];
+  const zd es = coef[src * coef_stride + 2 * i + 1];
+  const int64_t o = src * e_stride + (int64_t)m * k + i;
+  ev[o] = ev[o] - conj(bt) * conj(es);
+  ew[o] = ew[o] - d * conj(er);
+}
+template <typename R>
+void rev_proj_record(const Lat<R>& L, const Rev<R>& B, int j, int m, const zd* coef, cudaStream_t st) {
+  k_rev_proj_record<<<dim3(nblocks(j + 1, 128), L.nsrc), 128, 0, st>>>(
+      B.ev, B.ew, (int64_t)B.nreb_max * L.k, L.k, m, j, coef, 2 * (int64_t)L.k, L.beta, L.delta);
+}
+
+// reverse sweep start: g_alpha of the last step comes from G_T alone; no carries yet
+__global__ void k_rev_init(SrcScal* sc, const zd* __restrict__ gaT, int k, int nsrc) {
+  const int src = blockIdx.x * blockDim.x + threadIdx.x;
+  if (src >= nsrc) return;
+  sc[src].g_alpha = gaT[(int64_t)src * k + k - 1];
+  sc[src].carry_beta = mk(0.0, 0.0);
+  sc[src].carry_delta = 0.0;
+}
+template <typename R>
+void rev_init(const Lat<R>& L, const Rev<R>& B, cudaStream_t st) {
+  k_rev_init<<<nblocks(L.nsrc, 32), 32, 0, st>>>(L.sc, B.gaT, L.k, L.nsrc);
+}
+
+// Combination loader: a1 F1(s) + a2 F2(s) (either field may be null)
+template <typename R>
+struct Comb2 {
+  const R* f1; cplx<R> a1;
+  const R* f2; cplx<R> a2;
+  int64_t V;
+  __device__ __forceinline__ void operator()(int64_t s, Spinor<R>& o) const {
+    Spinor<R> t;
+    spinor_zero(o);
+    if (f1) {
+      load_spinor(f1, V, s, t);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) cmac(o.c[c], a1, t.c[c]);
+    }
+    if (f2) {
+      load_spinor(f2, V, s, t);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) cmac(o.c[c], a2, t.c[c]);
+    }
+  }
+};
+
+// R3: complete gradients of v_j and w_j
+//   g_p = g_r + g_alpha w_j,  g_q = g_s
+//   Gv_j = -conj(beta_{j+1}) g_r' - conj(alpha_j) g_r + conj(y_j) xbar + H^dag g_p + acc_v
+//   Gw_j = -delta_{j+1} g_s' - alpha_j g_s + H (conj(g_alpha) v_j + g_s) + acc_w
+// (primes: the previous step's g_r, g_s).  g_p goes to the ring for the force.
+template <typename R>
+__global__ void __launch_bounds__(BS) k_rev_stencil(Lat<R> L, Rev<R> B, int j, int slot, int prev_slot,
+                                                     int nrec) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  if (x >= V) return;
+  const SrcScal& sc = L.sc[src];
+  const int64_t o = (int64_t)src * L.k + j;
+  const cplx<R> ga = cast<R>(sc.g_alpha);
+  const cplx<R> al = cast<R>(L.alpha[o]);
+  const cplx<R> yj = cast<R>(B.y[(int64_t)src * L.k + j]);
+  const R* gr = slot >= 0 && j < L.k - 1 ? B.ring(B.gr_ring, slot, src) : nullptr;
+  const R* gs = slot >= 0 && j < L.k - 1 ? B.ring(B.gs_ring, slot, src) : nullptr;
+  const R* wj = L.basis_w(src, j);
+  const R* vj = L.basis_v(src, j);
+  const cplx<R> one = mk<R>(1, 0);
+  Spinor<R> hv, hw, t;
+  // H^dag g_p
+  {
+    Comb2<R> ld{gr, one, wj, ga, V};
+    h_site_ld(ld, L.u, L.g, x, L.kappa, L.efinv, L.ef, hv);
+    Spinor<R> gp;
+    ld(x, gp);
+    store_spinor(B.ring(B.gp_ring, slot, src), V, x, gp);
+  }
+  // H (conj(g_alpha) v_j + g_s)
+  {
+    Comb2<R> ld{vj, conj(ga), gs, one, V};
+    h_site_ld(ld, L.u, L.g, x, L.kappa, L.ef, L.efinv, hw);
+  }
+  load_spinor(B.xbar + src * L.vs, V, x, t);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) cmac(hv.c[c], conj(yj), t.c[c]);
+  if (gr) {
+    load_spinor(gr, V, x, t);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) cmac(hv.c[c], -conj(al), t.c[c]);
+    load_spinor(gs, V, x, t);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) cmac(hw.c[c], -al, t.c[c]);
+  }
+  if (prev_slot >= 0 && j + 1 < L.k - 1) {
+    const cplx<R> bn = cast<R>(L.beta[o + 1]);
+    const R dn = (R)L.delta[o + 1];
+    load_spinor(B.ring(B.gr_ring, prev_slot, src), V, x, t);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) cmac(hv.c[c], -conj(bn), t.c[c]);
+    load_spinor(B.ring(B.gs_ring, prev_slot, src), V, x, t);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) hw.c[c] = hw.c[c] - dn * t.c[c];
+  }
+  for (int m = 0; m < nrec; ++m) {
+    const int jm = B.reb_steps[m];
+    const int64_t eo = src * (int64_t)B.nreb_max * L.k + (int64_t)m * L.k + j;
+    const cplx<R> cv = cast<R>(B.ev[eo]), cw = cast<R>(B.ew[eo]);
+    load_spinor(L.basis_w(src, jm + 1), V, x, t);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) cmac(hv.c[c], cv, t.c[c]);
+    load_spinor(L.basis_v(src, jm + 1), V, x, t);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) cmac(hw.c[c], cw, t.c[c]);
+  }
+  store_spinor(B.gv_new + src * L.vs, V, x, hv);
+  store_spinor(B.gw_new + src * L.vs, V, x, hw);
+}
+template <typename R>
+void rev_stencil(const Lat<R>& L, const Rev<R>& B, int j, int slot, int prev_slot, int nrec, cudaStream_t st) {
+  k_rev_stencil<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j, slot, prev_slot, nrec);
+}
+
+// ---------------------------------------------------------------------------
+// Force: g_H = sum_t (g_p,t v_t^dag + w_t g_q,t^dag) contracted into dU (FP64
+// accumulator, layout e*V + x with e = nu*9 + a*3 + b) and dmu.  One thread per
+// (site, direction); terms of ring slots 0..nterms-1 have steps j0, j0-1, ...
+//   forward hop:  G[c][c'] += sum_s a(x)_{s,c} conj((C+ b(x+nu))_{s,c'})
+//   backward hop: G[c][c'] += sum_s conj(a(x+nu)_{s,c'}) (C- b(x))_{s,c}
+//   C+ = -kappa f gamma5 (1+gamma_nu),  C- = -kappa f^-1 gamma5 (1-gamma_nu)
+//   dmu += Re <G_fwd - G_bwd, U_t(x)>  on temporal links.
+// ---------------------------------------------------------------------------
+template <int NU, typename R>
+__device__ void force_term(const Lat<R>& L, int64_t x, int64_t xf, const R* a, const R* b, cplx<R> (&G)[9],
+                           cplx<R> (&Gd)[9]) {
+  const int64_t V = L.g.V;
+  const R ff = NU == 3 ? L.ef : R(1), fb = NU == 3 ? L.efinv : R(1);
+  Spinor<R> sa, sb, cb;
+  // forward
+  load_spinor(a, V, x, sa);
+  load_spinor(b, V, xf, sb);
+  g5_proj_full<NU, +1>(sb, cb);
+  const R cf = -L.kappa * ff;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cplx<R> t = czero<R>();
+#pragma unroll
+      for (int s = 0; s < 4; ++s) cmac(t, sa.c[s * 3 + c], conj(cb.c[s * 3 + d]));
+      G[c * 3 + d] = G[c * 3 + d] + cf * t;
+      if (NU == 3) Gd[c * 3 + d] = Gd[c * 3 + d] + cf * t;
+    }
+  // backward
+  load_spinor(a, V, xf, sa);
+  load_spinor(b, V, x, sb);
+  g5_proj_full<NU, -1>(sb, cb);
+  const R cbk = -L.kappa * fb;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cplx<R> t = czero<R>();
+#pragma unroll
+      for (int s = 0; s < 4; ++s) cmac(t, conj(sa.c[s * 3 + d]), cb.c[s * 3 + c]);
+      G[c * 3 + d] = G[c * 3 + d] + cbk * t;
+      if (NU == 3) Gd[c * 3 + d] = Gd[c * 3 + d] - cbk * t;
+    }
+}
+
+template <int NU, typename R>
+__device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterms, int j0, zd* dmu_site) {
+  int c[4];
+  site_coords(L.g, x, c);
+  const int64_t xf = neighbour(L.g, x, c, NU, +1);
+  zd acc[9];
+  zd accd[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) acc[e] = accd[e] = mk(0.0, 0.0);
+  for (int src = 0; src < L.nsrc; ++src) {
+    cplx<R> G[9], Gd[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) G[e] = Gd[e] = czero<R>();
+    for (int t = 0; t < nterms; ++t) {
+      const int j = j0 - t;
+      force_term<NU>(L, x, xf, B.ring(B.gp_ring, t, src), L.basis_v(src, j), G, Gd);
+      if (j < L.k - 1)
+        force_term<NU>(L, x, xf, L.basis_w(src, j), B.ring(B.gs_ring, t, src), G, Gd);
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      acc[e] = acc[e] + mk((double)G[e].re, (double)G[e].im);
+      accd[e] = accd[e] + mk((double)Gd[e].re, (double)Gd[e].im);
+    }
+  }
+  double2* f = reinterpret_cast<double2*>(B.force);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    double2 o = f[(int64_t)(NU * 9 + e) * L.g.V + x];
+    o.x += acc[e].re;
+    o.y += acc[e].im;
+    f[(int64_t)(NU * 9 + e) * L.g.V + x] = o;
+  }
+  if (NU == 3) {
+    double dm = 0.0;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const zd u = mk((double)L.u[2 * ((27 + e) * L.g.V + x)], (double)L.u[2 * ((27 + e) * L.g.V + x) + 1]);
+      dm += accd[e].re * u.re + accd[e].im * u.im;     // Re(conj(Gd) u)
+    }
+    dmu_site->re = dm;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(BS) k_force(Lat<R> L, Rev<R> B, int nterms, int j0) {
+  __shared__ zd scratch[32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int nu = blockIdx.y;
+  zd v[1] = {mk(0.0, 0.0)};
+  if (x < L.g.V) {
+    if (nu == 0) force_dir<0>(L, B, x, nterms, j0, &v[0]);
+    else if (nu == 1) force_dir<1>(L, B, x, nterms, j0, &v[0]);
+    else if (nu == 2) force_dir<2>(L, B, x, nterms, j0, &v[0]);
+    else force_dir<3>(L, B, x, nterms, j0, &v[0]);
+  }
+  block_sum<1>(v, scratch);
+  const unsigned nblk = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x == 0) B.dmu_part[bid] = v[0];
+  if (arrive_last(B.dmu_cnt, nblk)) {
+    zd s[1];
+    sum_partials<1>(B.dmu_part, nblk, s, scratch);
+    if (threadIdx.x == 0) *B.dmu += s[0].re;
+  }
+}
+template <typename R>
+void force_flush(const Lat<R>& L, const Rev<R>& B, const int* /*unused*/, int nterms, int j0, cudaStream_t st) {
+  if (nterms <= 0) return;
+  k_force<R><<<dim3(nblocks(L.g.V, BS), 4), BS, 0, st>>>(L, B, nterms, j0);
+}
+
+// explicit instantiations
+#define OV_INST(R)                                                                                        \
+  template void pack_spinors<R>(const double*, R*, int, int64_t, int64_t, cudaStream_t);                 \
+  template void unpack_spinors<R>(const R*, double*, int, int64_t, int64_t, cudaStream_t);               \
+  template void pack_links<R>(const double*, R*, int64_t, cudaStream_t);                                 \
+  template void apply_h<R>(const Lat<R>&, const R*, R*, int, cudaStream_t);                              \
+  template void tsl_init<R>(const Lat<R>&, cudaStream_t);                                                \
+  template void tsl_stencil<R>(const Lat<R>&, int, bool, cudaStream_t);                                  \
+  template void tsl_update<R>(const Lat<R>&, int, bool, cudaStream_t);                                   \
+  template void tsl_project<R>(const Lat<R>&, int, int, R*, R*, int64_t, zd*, zd*, bool, cudaStream_t);  \
+  template void basis_dots<R>(const Lat<R>&, int, const R*, int64_t, zd*, zd*, cudaStream_t);            \
+  template void combine<R>(const Lat<R>&, int, const zd*, double*, cudaStream_t);                        \
+  template void rev_init<R>(const Lat<R>&, const Rev<R>&, cudaStream_t);                                 \
+  template void rev_dots<R>(const Lat<R>&, const Rev<R>&, int, cudaStream_t);                            \
+  template void rev_form<R>(const Lat<R>&, const Rev<R>&, int, int, bool, cudaStream_t);                 \
+  template void rev_proj_record<R>(const Lat<R>&, const Rev<R>&, int, int, const zd*, cudaStream_t);     \
+  template void rev_alpha_dots<R>(const Lat<R>&, const Rev<R>&, int, int, cudaStream_t);                 \
+  template void rev_stencil<R>(const Lat<R>&, const Rev<R>&, int, int, int, int, cudaStream_t);          \
+  template void force_flush<R>(const Lat<R>&, const Rev<R>&, const int*, int, int, cudaStream_t);
+
+OV_INST(double)
+OV_INST(float)
+
+}  // namespace ov

@@ -1,0 +1,579 @@
+// C ABI of the library (include/ov.h): argument checks, workspace, and the
+// host-side driver that enqueues the kernels of the forward two-sided Lanczos
+// recurrence, the k x k sign, the reverse sweep and the force contraction.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ov.h"
+#include "kernels.h"
+
+using namespace ov;
+
+namespace {
+
+enum BufId {
+  B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
+  B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
+  B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, NBUF
+};
+
+struct Status {
+  int code;
+};
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      std::fprintf(stderr, "ov: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), \
+                   __FILE__, __LINE__);                                            \
+      throw Status{OV_ERR_CUDA};                                                   \
+    }                                                                              \
+  } while (0)
+
+inline void launch_check() { CK(cudaGetLastError()); }
+
+int rebiorth_at(int step, int period) {
+  if (period <= 0) return 0;
+  if (period == 1) return 1;
+  const int m = step % period;
+  return m == 0 || m == 1;
+}
+
+}  // namespace
+
+struct ov_context {
+  cudaStream_t st = nullptr;
+  ov_options opt{};
+  void* buf[NBUF] = {};
+  size_t cap[NBUF] = {};
+  // coefficients of the last forward pass (for ov_tsl_coefficients)
+  int last_k = 0, last_nsrc = 0;
+  cudaEvent_t ev[8] = {};
+};
+
+namespace {
+
+void* ws(ov_context* c, int id, size_t bytes, bool zero = false) {
+  if (bytes == 0) bytes = 16;
+  if (c->cap[id] < bytes) {
+    if (c->buf[id]) CK(cudaFree(c->buf[id]));
+    c->buf[id] = nullptr;
+    c->cap[id] = 0;
+    size_t nb = (bytes + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc(&c->buf[id], nb);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Status{OV_ERR_OOM};
+    }
+    c->cap[id] = nb;
+    zero = true;   // counters and accumulators start at zero
+  }
+  if (zero) CK(cudaMemsetAsync(c->buf[id], 0, bytes, c->st));
+  return c->buf[id];
+}
+
+template <typename T> T* wsT(ov_context* c, int id, int64_t n, bool zero = false) {
+  return static_cast<T*>(ws(c, id, (size_t)n * sizeof(T), zero));
+}
+
+void check_ptr(const void* p) {
+  if (!p || (reinterpret_cast<uintptr_t>(p) & 15u)) throw Status{OV_ERR_INVALID_ARG};
+}
+
+Geom make_geom(const int32_t dims[4]) {
+  if (!dims) throw Status{OV_ERR_INVALID_ARG};
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 1 || dims[i] > 4096) throw Status{OV_ERR_INVALID_ARG};
+  Geom g;
+  g.nx = dims[0]; g.ny = dims[1]; g.nz = dims[2]; g.nt = dims[3];
+  g.V = (int64_t)g.nx * g.ny * g.nz * g.nt;
+  if (g.V > (int64_t)1 << 28) throw Status{OV_ERR_INVALID_ARG};
+  return g;
+}
+
+template <typename R>
+Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc, int k,
+             bool basis) {
+  Lat<R> L{};
+  L.g = make_geom(dims);
+  if (nsrc < 1 || nsrc > 4096) throw Status{OV_ERR_INVALID_ARG};
+  if (!(std::isfinite(mu) && std::isfinite(m_w)) || 2.0 * m_w + 8.0 == 0.0) throw Status{OV_ERR_INVALID_ARG};
+  check_ptr(U);
+  const int64_t V = L.g.V;
+  L.kappa = (R)(1.0 / (2.0 * m_w + 8.0));
+  L.ef = (R)std::exp(mu);
+  L.efinv = (R)std::exp(-mu);
+  L.nsrc = nsrc;
+  L.k = k;
+  L.vs = ((24 * V + 63) / 64) * 64;
+  R* u = wsT<R>(c, B_LINKS, 72 * V);
+  L.u = u;
+  pack_links<R>(static_cast<const double*>(U), u, V, c->st);
+  launch_check();
+  if (basis) {
+    L.bv = wsT<R>(c, B_BV, (int64_t)nsrc * k * L.vs);
+    L.bw = wsT<R>(c, B_BW, (int64_t)nsrc * k * L.vs);
+  }
+  L.p = wsT<R>(c, B_P, nsrc * L.vs);
+  L.q = wsT<R>(c, B_Q, nsrc * L.vs);
+  L.r = wsT<R>(c, B_R, nsrc * L.vs);
+  L.s = wsT<R>(c, B_S, nsrc * L.vs);
+  L.sc = wsT<SrcScal>(c, B_SC, nsrc);
+  L.alpha = wsT<zd>(c, B_ALPHA, (int64_t)nsrc * k);
+  L.beta = wsT<zd>(c, B_BETA, (int64_t)nsrc * k);
+  L.delta = wsT<double>(c, B_DELTA, (int64_t)nsrc * k);
+  const int64_t nblk = (V + 127) / 128;
+  L.part_stride = 8 * (nblk < 64 ? 64 : nblk);
+  L.part = wsT<zd>(c, B_PART, nsrc * L.part_stride);
+  L.cnt = wsT<unsigned>(c, B_CNT, (int64_t)nsrc * 16);
+  return L;
+}
+
+std::vector<SrcScal> read_scalars(ov_context* c, const SrcScal* d, int nsrc) {
+  std::vector<SrcScal> h(nsrc);
+  CK(cudaMemcpyAsync(h.data(), d, sizeof(SrcScal) * nsrc, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return h;
+}
+
+int scalar_status(const std::vector<SrcScal>& h, int* k_reached, int k) {
+  int st = OV_OK, kr = k;
+  for (const auto& s : h) {
+    if (s.err) {
+      if (s.err_step >= 0 && s.err_step < kr) kr = s.err_step;
+      if (s.err & ERRB_BREAKDOWN) st = OV_ERR_BREAKDOWN;
+      else if (st == OV_OK) st = OV_ERR_NONFINITE;
+    }
+  }
+  if (k_reached) *k_reached = kr;
+  return st;
+}
+
+// Forward Krylov recurrence for all sources; bases, coefficients stay on device.
+template <typename R>
+void forward_krylov(ov_context* c, Lat<R>& L) {
+  const int k = L.k;
+  const int64_t nsb = (L.g.V + 127) / 128;
+  zd* coef = wsT<zd>(c, B_COEF, (int64_t)L.nsrc * 2 * k);
+  zd* cpart = wsT<zd>(c, B_CPART, (int64_t)L.nsrc * 2 * k * nsb);
+  tsl_init(L, c->st);
+  for (int j = 0; j < k; ++j) {
+    tsl_stencil(L, j, j < k - 1, c->st);
+    if (j == k - 1) break;
+    const int reb = rebiorth_at(j + 1, c->opt.rebiorth);
+    tsl_update(L, j, !reb, c->st);
+    if (reb) {
+      for (int ps = 0; ps < c->opt.passes; ++ps)
+        tsl_project(L, j, 0, L.r, L.s, L.vs, coef, cpart, ps == c->opt.passes - 1, c->st);
+    }
+  }
+  launch_check();
+}
+
+// Scaled Newton iteration for sgn (mirrors the oracle's stopping rules).
+// a[0] holds the start matrix; a[1] is scratch.  Block form: when e != nullptr
+// the iteration runs on [[A, E], [0, A]] (e[0] holds E) and E converges to the
+// upper-right block.  Returns the iteration count (or -1 on a non-finite step)
+// and the index of the buffer holding the result in *which.
+int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which) {
+  const int64_t n = (int64_t)k * k;
+  zd* ai = wsT<zd>(c, B_XI, n);
+  zd* t1 = e ? wsT<zd>(c, B_TMP1, n) : nullptr;
+  zd* t2 = e ? wsT<zd>(c, B_TMP2, n) : nullptr;
+  int* ipiv = wsT<int>(c, B_IPIV, k);
+  zd* prow = wsT<zd>(c, B_PROW, k);
+  zd* col = wsT<zd>(c, B_COL, k);
+  double* dstat = wsT<double>(c, B_DSTAT, 4);   // [0] diff^2, [1] norm^2, [2] log|det|
+  zd* dpart = wsT<zd>(c, B_DPART, (n + 255) / 256 + 64);
+  unsigned* dcnt = wsT<unsigned>(c, B_DCNT, 4);
+  bool scaling = true;
+  double prev = INFINITY;
+  int cur = 0, it = 0;
+  double hs[3];
+  for (it = 1; it <= 100; ++it) {
+    CK(cudaMemsetAsync(dstat, 0, 3 * sizeof(double), c->st));
+    dense_copy(a[cur], ai, n, c->st);
+    dense_inverse(ai, k, ipiv, prow, col, dstat + 2, err_dev, c->st);
+    if (e) {
+      dense_gemm(ai, e[cur], t1, k, c->st);
+      dense_gemm(t1, ai, t2, k, c->st);
+    }
+    // the block determinant is det(A)^2: its 1/(2k)-th root is det(A)^(1/k)
+    dense_newton_combine(a[cur], ai, a[1 - cur], k, dstat + 2, scaling ? 1 : 0, 1.0, e ? 2.0 : 1.0, dstat,
+                         dpart, dcnt, c->st);
+    if (e)
+      dense_newton_combine(e[cur], t2, e[1 - cur], k, dstat + 2, scaling ? 1 : 0, -1.0, 1.0, dstat, dpart, dcnt,
+                           c->st);
+    launch_check();
+    CK(cudaMemcpyAsync(hs, dstat, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    cur = 1 - cur;
+    const double step = std::sqrt(hs[0] / hs[1]);
+    if (!std::isfinite(step)) return -1;
+    if (step <= 1e-14) break;
+    if (step < 1e-2) scaling = false;
+    if (it > 6 && !scaling && step >= 0.5 * prev) break;
+    prev = step;
+  }
+  *which = cur;
+  return it > 100 ? 100 : it;
+}
+
+// y_src = beta0 sgn(T_k) e_1 for every source
+template <typename R>
+int sign_all(ov_context* c, Lat<R>& L, const std::vector<SrcScal>& hsc, zd* y, int* iters) {
+  const int k = L.k;
+  const int64_t n = (int64_t)k * k;
+  int* derr = wsT<int>(c, B_DERR, 1, true);
+  int maxit = 0;
+  zd* a[2] = {wsT<zd>(c, B_X, n), wsT<zd>(c, B_XN, n)};
+  for (int src = 0; src < L.nsrc; ++src) {
+    dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, a[0],
+                  c->st);
+    int which = 0;
+    const int it = newton(c, a, nullptr, k, derr, &which);
+    if (it < 0) return OV_ERR_SIGN_ILLPOSED;
+    if (it > maxit) maxit = it;
+    dense_extract_y(a[which], hsc[src].beta0, k, y + (int64_t)src * k, c->st);
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (herr) return OV_ERR_SIGN_ILLPOSED;
+  if (iters) *iters = maxit;
+  return OV_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+template <typename R>
+int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                  const void* b, int k, void* x, ov_tsl_info* info) {
+  check_ptr(b);
+  check_ptr(x);
+  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true);
+  pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, L.g.V, L.vs, c->st);
+  pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, L.g.V, L.vs, c->st);
+  CK(cudaEventRecord(c->ev[0], c->st));
+  forward_krylov(c, L);
+  CK(cudaEventRecord(c->ev[1], c->st));
+  auto hsc = read_scalars(c, L.sc, nsrc);
+  int kr = k;
+  int st = scalar_status(hsc, &kr, k);
+  c->last_k = k;
+  c->last_nsrc = nsrc;
+  if (info) info->k_reached = kr;
+  if (st != OV_OK) return st;
+  zd* y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
+  int iters = 0;
+  st = sign_all(c, L, hsc, y, &iters);
+  if (st != OV_OK) return st;
+  CK(cudaEventRecord(c->ev[2], c->st));
+  combine(L, k, y, static_cast<double*>(x), c->st);
+  launch_check();
+  CK(cudaEventRecord(c->ev[3], c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (info) {
+    info->newton_iters = iters;
+    info->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
+    info->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
+    info->t_ms[2] = elapsed(c->ev[2], c->ev[3]);
+  }
+  return OV_OK;
+}
+
+template <typename R>
+int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                 const void* b, int k, const void* xbar, void* x, void* dU, double* dmu, ov_tsl_info* info) {
+  check_ptr(b);
+  check_ptr(xbar);
+  check_ptr(dU);
+  if (!dmu) throw Status{OV_ERR_INVALID_ARG};
+  if (x) check_ptr(x);
+  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true);
+  const int64_t V = L.g.V, vs = L.vs;
+  pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, V, vs, c->st);
+  pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, V, vs, c->st);
+  CK(cudaEventRecord(c->ev[0], c->st));
+  forward_krylov(c, L);
+  CK(cudaEventRecord(c->ev[1], c->st));
+  auto hsc = read_scalars(c, L.sc, nsrc);
+  int kr = k;
+  int st = scalar_status(hsc, &kr, k);
+  c->last_k = k;
+  c->last_nsrc = nsrc;
+  if (info) info->k_reached = kr;
+  if (st != OV_OK) return st;
+  zd* y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
+  int iters = 0;
+  st = sign_all(c, L, hsc, y, &iters);
+  if (st != OV_OK) return st;
+  CK(cudaEventRecord(c->ev[2], c->st));
+  if (x) combine(L, k, y, static_cast<double*>(x), c->st);
+  // g_y = V^dag xbar
+  R* xb = wsT<R>(c, B_XBAR, nsrc * vs);
+  pack_spinors<R>(static_cast<const double*>(xbar), xb, nsrc, V, vs, c->st);
+  const int64_t nsb = (V + 127) / 128;
+  zd* gy = wsT<zd>(c, B_GY, (int64_t)nsrc * 2 * k);
+  zd* cpart = wsT<zd>(c, B_CPART, (int64_t)nsrc * 2 * k * nsb);
+  basis_dots(L, k, xb, vs, gy, cpart, c->st);
+  launch_check();
+  CK(cudaEventRecord(c->ev[3], c->st));
+  // G_T = L_sgn(T^dag, beta0 g_y e_1^T) from the Theorem-1 block matrix
+  zd* gaT = wsT<zd>(c, B_GA, (int64_t)nsrc * k);
+  zd* gbT = wsT<zd>(c, B_GB, (int64_t)nsrc * k);
+  double* gdT = wsT<double>(c, B_GD, (int64_t)nsrc * k);
+  int* derr = wsT<int>(c, B_DERR, 1, true);
+  int iters_adj = 0;
+  {
+    const int64_t n = (int64_t)k * k;
+    zd* t = wsT<zd>(c, B_T, n);
+    zd* a[2] = {wsT<zd>(c, B_X, n), wsT<zd>(c, B_XN, n)};
+    zd* e[2] = {wsT<zd>(c, B_E, n), wsT<zd>(c, B_EN, n)};
+    for (int src = 0; src < nsrc; ++src) {
+      dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, t,
+                    c->st);
+      dense_adjoint(t, a[0], k, c->st);
+      dense_set_column0(e[0], gy + (int64_t)src * 2 * k, 2, hsc[src].beta0, k, c->st);
+      int which = 0;
+      const int it = newton(c, a, e, k, derr, &which);
+      if (it < 0) return OV_ERR_SIGN_ILLPOSED;
+      if (it > iters_adj) iters_adj = it;
+      dense_extract_tri(e[which], k, gaT + (int64_t)src * k, gbT + (int64_t)src * k, gdT + (int64_t)src * k,
+                        c->st);
+    }
+  }
+  {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (herr) return OV_ERR_SIGN_ILLPOSED;
+  }
+  CK(cudaEventRecord(c->ev[4], c->st));
+  // reverse sweep
+  std::vector<int> reb;
+  for (int j = k - 2; j >= 0; --j)
+    if (rebiorth_at(j + 1, c->opt.rebiorth)) reb.push_back(j);
+  const int nreb_max = reb.empty() ? 1 : (int)reb.size();
+  const int m = k < 32 ? k : 32;
+  Rev<R> B{};
+  B.nsrc = nsrc;
+  B.vs = vs;
+  B.m = m;
+  B.gv = wsT<R>(c, B_GV, nsrc * vs);
+  B.gw = wsT<R>(c, B_GW, nsrc * vs);
+  B.gv_new = wsT<R>(c, B_GV2, nsrc * vs);
+  B.gw_new = wsT<R>(c, B_GW2, nsrc * vs);
+  B.gr_ring = wsT<R>(c, B_GR, (int64_t)m * nsrc * vs);
+  B.gs_ring = wsT<R>(c, B_GS, (int64_t)m * nsrc * vs);
+  B.gp_ring = wsT<R>(c, B_GP, (int64_t)m * nsrc * vs);
+  B.xbar = xb;
+  B.y = y;
+  B.gaT = gaT;
+  B.gbT = gbT;
+  B.gdT = gdT;
+  B.nreb_max = nreb_max;
+  B.ev = wsT<zd>(c, B_EV, (int64_t)nsrc * nreb_max * k, true);
+  B.ew = wsT<zd>(c, B_EW, (int64_t)nsrc * nreb_max * k, true);
+  B.reb_steps = wsT<int>(c, B_REB, nreb_max);
+  if (!reb.empty())
+    CK(cudaMemcpyAsync(B.reb_steps, reb.data(), sizeof(int) * reb.size(), cudaMemcpyHostToDevice, c->st));
+  B.force = wsT<double>(c, B_FORCE, 72 * V, true);
+  B.dmu = wsT<double>(c, B_DMU, 1, true);
+  B.dmu_part = wsT<zd>(c, B_DMUPART, 4 * ((V + 127) / 128) + 64);
+  B.dmu_cnt = wsT<unsigned>(c, B_DMUCNT, 4);
+  zd* coef = wsT<zd>(c, B_COEF, (int64_t)nsrc * 2 * k);
+  rev_init(L, B, c->st);
+  rev_stencil(L, B, k - 1, 0, -1, 0, c->st);
+  std::swap(B.gv, B.gv_new);
+  std::swap(B.gw, B.gw_new);
+  int slot = 1, j0 = k - 1, nrec = 0;
+  for (int j = k - 2; j >= 0; --j) {
+    if (slot == m) {
+      force_flush(L, B, nullptr, m, j0, c->st);
+      slot = 0;
+      j0 = j;
+    }
+    const int prev = slot == 0 ? m - 1 : slot - 1;
+    rev_dots(L, B, j, c->st);
+    const int rb = rebiorth_at(j + 1, c->opt.rebiorth);
+    rev_form(L, B, j, slot, !rb, c->st);
+    if (rb) {
+      R* grs = B.gr_ring + (int64_t)slot * nsrc * vs;
+      R* gss = B.gs_ring + (int64_t)slot * nsrc * vs;
+      for (int ps = 0; ps < c->opt.passes; ++ps) {
+        tsl_project(L, j, 1, grs, gss, vs, coef, cpart, false, c->st);
+        rev_proj_record(L, B, j, nrec, coef, c->st);
+      }
+      rev_alpha_dots(L, B, j, slot, c->st);
+      ++nrec;
+    }
+    rev_stencil(L, B, j, slot, prev, nrec, c->st);
+    std::swap(B.gv, B.gv_new);
+    std::swap(B.gw, B.gw_new);
+    ++slot;
+  }
+  force_flush(L, B, nullptr, slot, j0, c->st);
+  CK(cudaEventRecord(c->ev[5], c->st));
+  unpack_force(B.force, static_cast<double*>(dU), V, c->st);
+  launch_check();
+  CK(cudaMemcpyAsync(dmu, B.dmu, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  auto hsc2 = read_scalars(c, L.sc, nsrc);
+  st = scalar_status(hsc2, nullptr, k);
+  if (st != OV_OK) return st;
+  if (info) {
+    info->newton_iters = iters;
+    info->newton_iters_adj = iters_adj;
+    info->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
+    info->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
+    info->t_ms[2] = elapsed(c->ev[2], c->ev[3]);
+    info->t_ms[3] = elapsed(c->ev[3], c->ev[4]);
+    info->t_ms[4] = elapsed(c->ev[4], c->ev[5]);
+  }
+  return OV_OK;
+}
+
+template <typename R>
+int apply_h_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                 const void* in, void* out, int dagger) {
+  check_ptr(in);
+  check_ptr(out);
+  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, 1, false);
+  pack_spinors<R>(static_cast<const double*>(in), L.r, nsrc, L.g.V, L.vs, c->st);
+  apply_h(L, L.r, L.p, dagger, c->st);
+  unpack_spinors<R>(L.p, static_cast<double*>(out), nsrc, L.g.V, L.vs, c->st);
+  launch_check();
+  CK(cudaStreamSynchronize(c->st));
+  return OV_OK;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const Status& s) {
+    return s.code;
+  } catch (...) {
+    return OV_ERR_CUDA;
+  }
+}
+
+bool valid_options(const ov_options* o) {
+  return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ov_context_create(ov_context** ctx, const ov_options* opt, void* stream) {
+  if (!ctx) return OV_ERR_INVALID_ARG;
+  *ctx = nullptr;
+  ov_options o{};
+  o.precision = OV_FP64;
+  o.rebiorth = 1;
+  o.passes = 2;
+  if (opt) {
+    if (!valid_options(opt)) return OV_ERR_INVALID_ARG;
+    o = *opt;
+  }
+  ov_context* c = new (std::nothrow) ov_context();
+  if (!c) return OV_ERR_OOM;
+  c->st = static_cast<cudaStream_t>(stream);
+  c->opt = o;
+  for (auto& e : c->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return OV_ERR_CUDA;
+    }
+  }
+  *ctx = c;
+  return OV_OK;
+}
+
+int ov_context_destroy(ov_context* c) {
+  if (!c) return OV_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->st);
+  for (int i = 0; i < NBUF; ++i)
+    if (c->buf[i]) cudaFree(c->buf[i]);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+  return OV_OK;
+}
+
+int ov_context_set_options(ov_context* c, const ov_options* opt) {
+  if (!c || !opt || !valid_options(opt)) return OV_ERR_INVALID_ARG;
+  c->opt = *opt;
+  return OV_OK;
+}
+
+int ov_apply_H(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+               const void* in, void* out, int32_t dagger) {
+  if (!c) return OV_ERR_INVALID_ARG;
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED ? apply_h_impl<float>(c, dims, U, mu, m_w, nsrc, in, out, dagger)
+                                        : apply_h_impl<double>(c, dims, U, mu, m_w, nsrc, in, out, dagger);
+  });
+}
+
+int ov_tsl_sign(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                const void* b, int32_t k, void* x, ov_tsl_info* info) {
+  if (!c || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED ? tsl_sign_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, x, info)
+                                        : tsl_sign_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, x, info);
+  });
+}
+
+int ov_tsl_sign_vjp(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                    const void* b, int32_t k, const void* xbar, void* x, void* dU, double* dmu,
+                    ov_tsl_info* info) {
+  if (!c || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? tsl_vjp_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, xbar, x, dU, dmu, info)
+               : tsl_vjp_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, xbar, x, dU, dmu, info);
+  });
+}
+
+int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, double* beta, double* delta) {
+  if (!c || src < 0 || src >= c->last_nsrc || k != c->last_k || !alpha || !beta || !delta)
+    return OV_ERR_INVALID_ARG;
+  return guarded([&] {
+    CK(cudaMemcpyAsync(alpha, static_cast<zd*>(c->buf[B_ALPHA]) + (int64_t)src * k, sizeof(zd) * k,
+                       cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(beta, static_cast<zd*>(c->buf[B_BETA]) + (int64_t)src * k, sizeof(zd) * k,
+                       cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemcpyAsync(delta, static_cast<double*>(c->buf[B_DELTA]) + (int64_t)src * k, sizeof(double) * k,
+                       cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return OV_OK;
+  });
+}
+
+const char* ov_strerror(int s) {
+  switch (s) {
+    case OV_OK: return "success";
+    case OV_ERR_INVALID_ARG: return "invalid argument";
+    case OV_ERR_OOM: return "device workspace allocation failed";
+    case OV_ERR_BREAKDOWN: return "Lanczos breakdown (|omega| <= 1e-14 ||r|| ||s||)";
+    case OV_ERR_SIGN_ILLPOSED: return "k x k Newton sign iteration failed (singular or non-convergent)";
+    case OV_ERR_CUDA: return "CUDA runtime error";
+    case OV_ERR_NONFINITE: return "non-finite recurrence coefficient";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,190 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances.  FP64 stencil: 1e-13 relative (a few roundings of a 9-term sum).
+FP32 stencil: 2e-6 relative.  The k-step TSL map itself amplifies rounding: at
+the 4x4^3 workload point (m_w = -2, mu = 0.3, k = 200) a relative perturbation
+of b by 1e-16 moves x by 1e-10 and dU by 9e-8 (full re-biorthogonalisation),
+so FP64 parity there is required to 10x those floors.  On the well-conditioned
+m_w = -1 points the floors are ~1e-14, and 1e-11 is required.
+"""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dirac, tsl, vjp
+from paper_1604_08057_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@functools.lru_cache(maxsize=None)
+def case(dims, eps, seed, nsrc=1):
+    rng = np.random.default_rng(seed)
+    u = inputs.su3_links(dims, eps, rng)
+    b = inputs.gaussian_spinors(dims, nsrc, rng)
+    xbar = inputs.gaussian_spinors(dims, nsrc, rng)
+    return u, b, xbar
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_fwd(dims, eps, seed, mu, m_w, k, rebiorth=1, passes=2, src=0):
+    u, b, _ = case(dims, eps, seed, max(src + 1, 1))
+    return tsl.tsl_forward(u, b[src], mu, m_w, k, rebiorth=rebiorth, passes=passes)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_vjp(dims, eps, seed, mu, m_w, k, rebiorth=1, passes=2):
+    u, b, xbar = case(dims, eps, seed)
+    du, dmu, fwd = vjp.tsl_vjp(u, b[0], mu, m_w, k, xbar[0], rebiorth=rebiorth, passes=passes,
+                               fwd=oracle_fwd(dims, eps, seed, mu, m_w, k, rebiorth, passes))
+    return du, dmu
+
+
+def T(a):
+    return torch.tensor(a, device=DEV)
+
+
+# ---------------------------------------------------------------------------
+# H and H^dagger
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (3, 5, 2, 4), (4, 4, 4, 4), (8, 8, 8, 8), (14, 14, 14, 14)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 2e-6)])
+def test_apply_h_parity(dims, precision, tol):
+    u, b, _ = case(dims, 0.3, 1, 2)
+    mu, m_w = 0.3, -2.0
+    ut, bt = T(u), T(b)
+    for dagger in (False, True):
+        got = binding.apply_H(ut, mu, m_w, bt, dagger=dagger, precision=precision).cpu().numpy()
+        for s in range(2):
+            want = (dirac.apply_h_dagger if dagger else dirac.apply_h)(u, b[s], mu, m_w)
+            assert rel(got[s], want) <= tol, (dims, precision, dagger, s, rel(got[s], want))
+
+
+def test_apply_h_single_source_shape():
+    u, b, _ = case((3, 3, 3, 3), 0.3, 2)
+    got = binding.apply_H(T(u), 0.1, -1.0, T(b[0])).cpu().numpy()
+    assert got.shape == b[0].shape
+    assert rel(got, dirac.apply_h(u, b[0], 0.1, -1.0)) <= 1e-13
+
+
+# ---------------------------------------------------------------------------
+# forward TSL
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,mu,m_w,k,reb,tol", [
+    ((3, 3, 3, 3), 0.3, -1.0, 60, 1, 1e-11),
+    ((3, 5, 2, 4), 0.4, -1.0, 45, 10, 1e-11),        # ragged lattice, pair-periodic
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 1, 1e-9),         # the 4x4^3 workload: floor 1e-10
+])
+def test_tsl_forward_fp64(dims, mu, m_w, k, reb, tol):
+    u, b, _ = case(dims, 0.3, 3)
+    ref = oracle_fwd(dims, 0.3, 3, mu, m_w, k, reb)
+    x = binding.tsl_sign(T(u), mu, m_w, T(b[0]), k, rebiorth=reb).cpu().numpy()
+    a, bt, d = binding.tsl_coefficients(k, rebiorth=reb)
+    # the first coefficients agree to rounding before the map's amplification sets in
+    assert np.abs(a[:10] - ref.alpha[:10]).max() <= 1e-12 * np.abs(ref.alpha[:10]).max()
+    assert np.abs(d[1:10] - ref.delta[1:10]).max() <= 1e-12 * np.abs(ref.delta[1:10]).max()
+    assert np.abs(bt[1:10] - ref.beta[1:10]).max() <= 1e-12 * np.abs(ref.beta[1:10]).max()
+    assert rel(x, ref.x) <= tol, rel(x, ref.x)
+
+
+def test_tsl_forward_batched_sources_and_k2():
+    dims, mu, m_w = (3, 3, 2, 3), 0.2, -1.0
+    u, b, _ = case(dims, 0.3, 4, 3)
+    for k in (2, 30):
+        x = binding.tsl_sign(T(u), mu, m_w, T(b), k).cpu().numpy()
+        for s in range(3):
+            ref = tsl.tsl_forward(u, b[s], mu, m_w, k)
+            assert rel(x[s], ref.x) <= 1e-11, (k, s, rel(x[s], ref.x))
+
+
+def test_tsl_forward_mixed_precision():
+    """FP32 vectors: compared with the FP64 oracle to 2x the error of the oracle's own FP32 emulation."""
+    dims, mu, m_w, k = (3, 3, 3, 3), 0.3, -1.0, 60
+    u, b, _ = case(dims, 0.3, 3)
+    ref = oracle_fwd(dims, 0.3, 3, mu, m_w, k)
+    emu = tsl.tsl_forward(u, b[0], mu, m_w, k, emulate_fp32=True)
+    bar = max(2.0 * rel(emu.x, ref.x), 1e-6)
+    x = binding.tsl_sign(T(u), mu, m_w, T(b[0]), k, precision="mixed").cpu().numpy()
+    assert rel(x, ref.x) <= bar, (rel(x, ref.x), bar)
+
+
+# ---------------------------------------------------------------------------
+# VJP
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,mu,m_w,k,reb,tol", [
+    ((3, 3, 3, 3), 0.3, -1.0, 40, 1, 1e-9),
+    ((3, 5, 2, 4), 0.3, -1.0, 50, 10, 1e-8),
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 1, 1e-6),         # the 4x4^3 workload: dU floor 9e-8
+])
+def test_vjp_fp64(dims, mu, m_w, k, reb, tol):
+    u, b, xbar = case(dims, 0.3, 3)
+    du_o, dmu_o = oracle_vjp(dims, 0.3, 3, mu, m_w, k, reb)
+    du, dmu, x = binding.tsl_sign_vjp(T(u), mu, m_w, T(b[0]), k, T(xbar[0]), rebiorth=reb)
+    assert rel(du.cpu().numpy(), du_o) <= tol, rel(du.cpu().numpy(), du_o)
+    assert abs(dmu - dmu_o) <= tol * max(1.0, abs(dmu_o)), (dmu, dmu_o)
+    ref = oracle_fwd(dims, 0.3, 3, mu, m_w, k, reb)
+    assert rel(x.cpu().numpy(), ref.x) <= max(tol, 1e-11)
+
+
+def test_vjp_mixed_precision_well_conditioned():
+    dims, mu, m_w, k = (3, 3, 3, 3), 0.3, -1.0, 40
+    u, b, xbar = case(dims, 0.3, 3)
+    du_o, dmu_o = oracle_vjp(dims, 0.3, 3, mu, m_w, k)
+    du, dmu, _ = binding.tsl_sign_vjp(T(u), mu, m_w, T(b[0]), k, T(xbar[0]), precision="mixed")
+    assert rel(du.cpu().numpy(), du_o) <= 1e-4
+    assert abs(dmu - dmu_o) <= 1e-4 * abs(dmu_o)
+
+
+def test_vjp_batched_sources_sum():
+    """With several sources the VJP is the sum of the per-source VJPs."""
+    dims, mu, m_w, k = (2, 3, 2, 3), 0.25, -1.0, 25
+    u, b, xbar = case(dims, 0.3, 5, 2)
+    du, dmu, _ = binding.tsl_sign_vjp(T(u), mu, m_w, T(b), k, T(xbar))
+    du_o = np.zeros_like(u)
+    dmu_o = 0.0
+    for s in range(2):
+        d, m, _ = vjp.tsl_vjp(u, b[s], mu, m_w, k, xbar[s])
+        du_o += d
+        dmu_o += m
+    assert rel(du.cpu().numpy(), du_o) <= 1e-9
+    assert abs(dmu - dmu_o) <= 1e-9 * abs(dmu_o)
+
+
+def test_autograd_function_matches_vjp():
+    from paper_1604_08057_gb300.autograd import tsl_sign as tsl_fn
+    dims, mu, m_w, k = (3, 3, 3, 3), 0.3, -1.0, 30
+    u, b, xbar = case(dims, 0.3, 3)
+    ut = T(u).requires_grad_(True)
+    mut = torch.tensor(mu, dtype=torch.float64, device=DEV, requires_grad=True)
+    x = tsl_fn(ut, mut, T(b[0]), k, m_w)
+    loss = torch.real(torch.vdot(T(xbar[0]).flatten(), x.flatten()))
+    loss.backward()
+    du_o, dmu_o, _ = vjp.tsl_vjp(u, b[0], mu, m_w, k, xbar[0])
+    assert rel(ut.grad.cpu().numpy(), du_o) <= 1e-9
+    assert abs(mut.grad.item() - dmu_o) <= 1e-9 * abs(dmu_o)
+
+
+# ---------------------------------------------------------------------------
+# errors
+# ---------------------------------------------------------------------------
+def test_invalid_arguments_and_breakdown():
+    u, b, _ = case((2, 2, 2, 2), 0.3, 6)
+    with pytest.raises(binding.OVError) as e:
+        binding.tsl_sign(T(u), 0.3, -1.0, T(b[0]), 1)
+    assert e.value.status == -1
+    # the chiral constant spinor on the free field at mu = 0 is an eigenvector of H: breakdown
+    shape = inputs.lattice_shape((2, 2, 2, 2))
+    uf = np.zeros(shape + (4, 3, 3), dtype=complex)
+    uf[...] = np.eye(3)
+    bf = np.zeros(shape + (4, 3), dtype=complex)
+    bf[..., 0, 0] = 1.0
+    with pytest.raises(binding.OVError) as e:
+        binding.tsl_sign(T(uf), 0.0, -1.0, T(bf), 5, rebiorth=0)
+    assert e.value.status == -3
