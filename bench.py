@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Benchmark: seconds per sgn(H) b + d/dU (forward TSL + gauge-force VJP).
+
+Workload (default): 14x14^3 lattice (V = 38416, n = 460992), SU(3) links
+U = expm(i 0.2 A), mu = 0.3, m_w = -2, one Gaussian source, k = 800, one
+Gaussian cotangent; FP64 throughout (at this point the k-step map amplifies
+rounding by ~1e6 and FP32 basis vectors break the recurrence down; the
+mixed-precision path is reported separately), pair-periodic
+re-biorthogonalisation every 20 steps with 2 Gram-Schmidt passes.  One step = one ov_tsl_sign_vjp call (forward recurrence, sign,
+x = V y, Frechet adjoint, reverse sweep, force, dmu) on inputs resident in
+HBM; the Krylov bases (5.9 GB) exceed the 129 MB L2, so no flush is needed.
+
+Reported beside the headline: live per-kernel device times (CUDA events on
+the library's stream), the roofline of the dominant kernel, the Wilson-Dirac
+stencil bandwidth on an L2-busting multi-source batch, the end-to-end time
+through host buffers, clocks sampled during the timed region, the FP64 GPU
+path's status and its speed and error on a well-conditioned point, and the FP64
+oracle timed on a bounded sample on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1604_08057_gb300 import inputs  # noqa: E402
+
+METRIC = "s per sgn(H)b + dsgn/dU at 14^4, k=800"
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="14x14^3")
+    ap.add_argument("--k", type=int, default=0, help="override the workload's k")
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--rebiorth", type=int, default=20)
+    ap.add_argument("--passes", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
+    ap.add_argument("--cpu-k", type=int, default=4, help="Lanczos steps of the oracle sample")
+    ap.add_argument("--leg", default="all", choices=["all", "stencil"],
+                    help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    idx = int(parts[0])
+                except ValueError:
+                    continue
+                rows.append((idx, parts))
+        os.unlink(self.path)
+        idxs = sorted({i for i, _ in rows})
+        use = self.index if self.index in idxs else (idxs[0] if idxs else None)
+        rows = [p for i, p in rows if i == use]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(p[1]) for p in rows if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in rows if p[2].replace(".", "").isdigit()]
+        power = [float(p[3]) for p in rows if p[3].replace(".", "").isdigit()]
+        reasons = set()
+        for p in rows:
+            for name, val in zip(REASONS, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None, "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes (what the method must move), FP32 real size e = 4, FP64 e = 8
+# ---------------------------------------------------------------------------
+def rebiorth_steps(k, period):
+    if period <= 0:
+        return []
+    return [j for j in range(k - 1) if period == 1 or (j + 1) % period in (0, 1)]
+
+
+def algorithmic_bytes(kind, k, V, nsrc, e, period, passes):
+    """Total algorithmic bytes of one ov_tsl_sign_vjp call for one kernel kind."""
+    vec = 24 * e * V            # one spinor field
+    links = 72 * e * V
+    reb = rebiorth_steps(k, period)
+    if kind == "stencil_pair":   # read r, s; write v, w, p, q; links once
+        return k * (nsrc * 6 * vec + links)
+    if kind == "update":         # read p, q, v_j, w_j, v_j-1, w_j-1; write r, s
+        return (k - 1) * nsrc * 8 * vec
+    if kind == "proj_dots":      # forward and reverse: read a, b and 2(j+1) basis vectors per pass
+        return 2 * passes * nsrc * vec * sum(2 + 2 * (j + 1) for j in reb)
+    if kind == "proj_update":    # read 2(j+1) basis vectors and a, b; write a, b
+        return 2 * passes * nsrc * vec * sum(4 + 2 * (j + 1) for j in reb)
+    if kind == "rev_stencil":    # read g_r, g_s, w_j, v_j, xbar, g_r', g_s'; write Gv, Gw, g_p; links
+        acc = 0
+        nrec = 0
+        for j in range(k - 1, -1, -1):
+            if j < k - 1 and j in set(reb):
+                nrec += 1
+            acc += 2 * nrec
+        return k * (nsrc * 10 * vec + links) + nsrc * vec * acc
+    if kind == "force":          # read g_p, v_j, w_j, g_q per step (x 4 directions re-read from cache)
+        return nsrc * 4 * vec * k + 2 * 72 * 8 * V * ((k + 31) // 32)
+    return None
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1604_08057_gb300 import binding
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = inputs.WORKLOADS[args.workload]
+    k = args.k or wl.k
+    u, b, xbar = inputs.make_inputs(wl)
+    nsrc = b.shape[0]
+    V = wl.volume
+    ut, bt, xt = (torch.tensor(a, device=dev) for a in (u, b, xbar))
+    ctx = binding.context(args.precision, args.rebiorth, args.passes)
+
+    def step():
+        return binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, args.precision, args.rebiorth, args.passes,
+                                    return_info=True)
+
+    info = None
+    for _ in range(args.warmup):
+        du, dmu, x, info = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    binding.profile_enable(ctx, True)
+    binding.profile_read(ctx, reset=True)
+    l0 = binding.launch_count(ctx)
+    clocks = Clocks(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        du, dmu, x, info = step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = binding.launch_count(ctx) - l0
+    prof = binding.profile_read(ctx, reset=True)
+    binding.profile_enable(ctx, False)
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = ms_total / 1e3 / (args.steps * world)
+
+    # roofline of the dominant lattice kernel (HBM-bound by design)
+    e = 4 if args.precision == "mixed" else 8
+    lattice = ["stencil_pair", "update", "proj_dots", "proj_update", "rev_stencil", "force"]
+    dom = max(lattice, key=lambda kd: prof[kd][1])
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    bytes_dom = algorithmic_bytes(dom, k, V, nsrc, e, args.rebiorth, args.passes) * args.steps
+    achieved = bytes_dom / (prof[dom][1] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 3), "peak_source": peak_src,
+                "traffic": None, "launches": prof[dom][0],
+                "avg_launch_us": round(1e3 * prof[dom][1] / max(1, prof[dom][0]), 2)}
+    kernels_ms = {kd: round(v[1] / args.steps, 3) for kd, v in prof.items() if v[0]}
+
+    out = {"metric": METRIC, "value": round(value, 6), "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+           "data": "synthetic",
+           "config": {"workload": f"{args.workload} lattice, k={k}, mu={wl.mu}, m_w={wl.m_w}, "
+                                  f"{nsrc} source(s), forward + gauge-force VJP",
+                      "precision": args.precision, "rebiorth_period": args.rebiorth, "gs_passes": args.passes,
+                      "l2": "working set (Krylov bases) > L2; no flush", "parallelism": f"replicas x{world}"},
+           "gpu_launches": launches // args.steps * args.steps, "kernels_ms_per_step": kernels_ms,
+           "phase_ms": [round(t, 3) for t in info["t_ms"][:6]], "newton_iters": [info["newton_iters"],
+                                                                                  info["newton_iters_adj"]],
+           "roofline": roofline, "clocks": clk}
+
+    if not args.no_extras and rank == 0:
+        out["e2e"] = e2e_leg(args, ut, bt, xt, wl, k)
+        out["dw_stencil"] = stencil_leg(args, ut, wl, hbm, peak_src)
+        out["mixed_path"] = mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar)
+        if world == 1:
+            out["cpu_baseline"] = cpu_leg(args, k)
+    return out
+
+
+def e2e_leg(args, ut, bt, xt, wl, k):
+    """Same metric through the public API with host (pinned) inputs and outputs."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    uh = ut.cpu().pin_memory()
+    bh = bt.cpu().pin_memory()
+    xh = xt.cpu().pin_memory()
+    du_h = torch.empty_like(uh).pin_memory()
+    x_h = torch.empty_like(bh).pin_memory()
+    dev = ut.device
+    ud, bd, xd = torch.empty_like(ut), torch.empty_like(bt), torch.empty_like(xt)
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        ud.copy_(uh, non_blocking=True)
+        bd.copy_(bh, non_blocking=True)
+        xd.copy_(xh, non_blocking=True)
+        du, dmu, x = binding.tsl_sign_vjp(ud, wl.mu, wl.m_w, bd, k, xd, args.precision, args.rebiorth,
+                                          args.passes)
+        du_h.copy_(du, non_blocking=True)
+        x_h.copy_(x, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    h2d = uh.numel() * 16 + bh.numel() * 16 + xh.numel() * 16
+    d2h = du_h.numel() * 16 + x_h.numel() * 16 + 8
+    del dev
+    return {"value": round(ms / 1e3, 6), "unit": "s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps}
+
+
+def stencil_leg(args, ut, wl, hbm, peak_src, nsrc=32, reps=20):
+    """ov_apply_H on nsrc sources sharing the links (working set > L2): live kernel time."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    res = {}
+    V = wl.volume
+    g = torch.Generator(device=ut.device).manual_seed(5)
+    psi = torch.randn((nsrc,) + tuple(ut.shape[:4]) + (4, 3), dtype=torch.complex128, device=ut.device,
+                      generator=g)
+    for prec, e in (("mixed", 4), ("fp64", 8)):
+        ctx = binding.context(prec)
+        binding.apply_H(ut, wl.mu, wl.m_w, psi, precision=prec)
+        torch.cuda.synchronize()
+        binding.profile_enable(ctx, True)
+        binding.profile_read(ctx, reset=True)
+        for _ in range(reps):
+            binding.apply_H(ut, wl.mu, wl.m_w, psi, precision=prec)
+        prof = binding.profile_read(ctx, reset=True)
+        binding.profile_enable(ctx, False)
+        n, ms = prof["apply_h"]
+        nbytes = (nsrc * 2 * 24 * e + 72 * e) * V        # in + out per source, links once
+        gbs = nbytes * n / (ms / 1e3) / 1e9
+        flops = 1368 * V * nsrc * n / (ms / 1e3) / 1e12
+        res[prec] = {"GB_s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 3), "tflops": round(flops, 2),
+                     "us_per_launch": round(1e3 * ms / n, 2), "bytes_per_launch": nbytes}
+    res.update({"nsrc": nsrc, "peak": hbm, "peak_source": peak_src, "unit": "GB/s",
+                "bytes": "algorithmic: spinor in + out per source, links once (480 B/site FP32 at 1 source)"})
+    return res
+
+
+def mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar):
+    """The mixed-precision path: at the workload point, and at m_w = -1 where the
+    k-step map is well conditioned (timed against the FP64 path there)."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    res = {}
+    try:
+        binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, "mixed", args.rebiorth, args.passes)
+        res["workload_point"] = "completed"
+    except binding.OVError as exc:
+        res["workload_point"] = f"status {exc.status}: {exc}"
+    m_w = -1.0
+    out = {}
+    for prec in ("fp64", "mixed"):
+        try:
+            binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, args.rebiorth, args.passes)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            du, dmu, x = binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, args.rebiorth, args.passes)
+            t1.record()
+            torch.cuda.synchronize()
+            out[prec] = (t0.elapsed_time(t1) / 1e3, du, dmu, x)
+        except binding.OVError as exc:
+            out[prec] = f"status {exc.status}"
+    if all(isinstance(v, tuple) for v in out.values()):
+        (t64, du64, dmu64, x64), (t32, du32, dmu32, x32) = out["fp64"], out["mixed"]
+        rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+        res["m_w=-1"] = {"fp64_s": round(t64, 4), "mixed_s": round(t32, 4), "speedup": round(t64 / t32, 2),
+                         "mixed_vs_fp64_rel_x": rel(x32, x64), "mixed_vs_fp64_rel_dU": rel(du32, du64),
+                         "mixed_vs_fp64_rel_dmu": abs(dmu32 - dmu64) / abs(dmu64)}
+    else:
+        res["m_w=-1"] = {p: (v if isinstance(v, str) else "ok") for p, v in out.items()}
+    return res
+
+
+def cpu_leg(args, k):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload."""
+    from oracle import tsl, vjp
+    wl = inputs.WORKLOADS[args.workload]
+    u, b, xbar = inputs.make_inputs(wl)
+    ks = args.cpu_k
+    t0 = time.perf_counter()
+    fwd = tsl.tsl_forward(u, b[0], wl.mu, wl.m_w, ks, rebiorth=args.rebiorth, passes=args.passes)
+    vjp.tsl_vjp(u, b[0], wl.mu, wl.m_w, ks, xbar[0], rebiorth=args.rebiorth, passes=args.passes, fwd=fwd)
+    dt = time.perf_counter() - t0
+    return {"value": round(dt * k / ks, 3), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"forward + VJP at {args.workload} with k={ks} took {dt:.2f} s; scaled linearly to k={k} "
+                      f"(omits the O(k^2) re-biorthogonalisation and O(k^3) sign terms, so it understates "
+                      f"the oracle's time)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    wl = inputs.WORKLOADS[args.workload]
+    k = args.k or wl.k
+    from oracle import tsl, vjp
+    u, b, xbar = inputs.make_inputs(wl)
+    ks = args.cpu_k
+
+    def sample():
+        fwd = tsl.tsl_forward(u, b[0], wl.mu, wl.m_w, ks, rebiorth=args.rebiorth, passes=args.passes)
+        vjp.tsl_vjp(u, b[0], wl.mu, wl.m_w, ks, xbar[0], rebiorth=args.rebiorth, passes=args.passes, fwd=fwd)
+
+    for _ in range(args.warmup):
+        sample()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sample()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = dt * k / ks
+    desc = (f"FP64 numpy oracle, forward + VJP at {args.workload} with k={ks} per step ({dt:.2f} s), "
+            f"scaled linearly to k={k}")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 1),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload} lattice, k={k}, mu={wl.mu}, m_w={wl.m_w}, "
+                                   f"1 source, forward + gauge-force VJP"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(value, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    if args.leg == "stencil":
+        import torch
+        torch.cuda.set_device(local_rank)
+        wl = inputs.WORKLOADS[args.workload]
+        u, _, _ = inputs.make_inputs(wl)
+        out = stencil_leg(args, torch.tensor(u, device=f"cuda:{local_rank}"), wl, 6786.9, "measured")
+        print(json.dumps(out))
+        return
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -116,6 +116,29 @@ int ov_tsl_sign_vjp(ov_context *ctx, const int32_t dims[4], const void *U, doubl
 int ov_tsl_coefficients(ov_context *ctx, int32_t src, int32_t k, double *alpha, double *beta,
                         double *delta);
 
+/* Live per-kernel timing.  While enabled, every kernel launch of the library
+ * is bracketed by CUDA events on the context's stream and its device time is
+ * added to the kind's total when the enclosing call returns.  Kinds: */
+#define OV_KIND_STENCIL_PAIR  0  /* TSL step: v_j, w_j, p = H v_j, q = H^dag w_j, alpha_j */
+#define OV_KIND_UPDATE        1  /* three-term update r, s and omega */
+#define OV_KIND_PROJ_DOTS     2  /* Gram-Schmidt coefficients (dots against the bases + reduction) */
+#define OV_KIND_PROJ_UPDATE   3  /* Gram-Schmidt update (basis combination) */
+#define OV_KIND_COMBINE       4  /* x = V y and g_y = V^dag xbar */
+#define OV_KIND_DENSE         5  /* k x k Newton sign and Frechet adjoint: inverses, updates */
+#define OV_KIND_REV_SCALAR    6  /* reverse-sweep dots and scalar steps */
+#define OV_KIND_REV_STENCIL   7  /* reverse-sweep stencil pair (H^dag g_p, H g_q) */
+#define OV_KIND_FORCE         8  /* link-gradient contraction and dmu */
+#define OV_KIND_APPLY_H       9  /* ov_apply_H stencil */
+#define OV_KIND_LAYOUT       10  /* layout conversion (complex128 <-> internal) */
+#define OV_KIND_DENSE_GEMM   11  /* k x k products of the block Frechet iteration */
+#define OV_NKIND             12
+int ov_profile_enable(ov_context *ctx, int32_t enable);
+/* Totals since the last reset for `kind`: number of timed launches and summed
+ * device milliseconds.  reset != 0 clears all kinds after reading. */
+int ov_profile_read(ov_context *ctx, int32_t kind, int64_t *launches, double *ms, int32_t reset);
+/* Number of kernels this context has launched since it was created. */
+int64_t ov_launch_count(ov_context *ctx);
+
 /* Human-readable text for a status code (static storage). */
 const char *ov_strerror(int status);
 

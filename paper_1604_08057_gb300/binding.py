@@ -48,7 +48,11 @@ class Info(ctypes.Structure):
 
 
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
-           "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_strerror"]
+           "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
+           "ov_launch_count", "ov_strerror"]
+
+KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
+         "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
 
 
 def load(path: str = LIB_PATH):
@@ -69,10 +73,11 @@ def load(path: str = LIB_PATH):
     lib.ov_tsl_sign_vjp.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, P, P,
                                     ctypes.POINTER(D), ctypes.POINTER(Info)]
     lib.ov_tsl_coefficients.argtypes = [P, I32, I32, P, P, P]
+    lib.ov_profile_enable.argtypes = [P, I32]
+    lib.ov_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D), I32]
+    lib.ov_launch_count.argtypes = [P]
+    lib.ov_launch_count.restype = ctypes.c_int64
     lib.ov_strerror.argtypes = [ctypes.c_int]
-    lib.ov_strerror.restype = ctypes.c_char_p
-    for name in EXPORTS:
-        getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     lib.ov_strerror.restype = ctypes.c_char_p
     _lib = lib
     return lib
@@ -185,3 +190,27 @@ def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2):
                                    b.ctypes.data_as(ctypes.c_void_p), d.ctypes.data_as(ctypes.c_void_p)),
            "ov_tsl_coefficients")
     return a, b, d
+
+
+def profile_enable(ctx, on=True):
+    _check(load().ov_profile_enable(ctx, int(bool(on))), "ov_profile_enable")
+
+
+def profile_read(ctx, reset=False) -> dict:
+    """{kind: (launches, device ms)} since the last reset."""
+    lib = load()
+    out = {}
+    for i, name in enumerate(KINDS):
+        n = ctypes.c_int64(0)
+        ms = ctypes.c_double(0.0)
+        _check(lib.ov_profile_read(ctx, i, ctypes.byref(n), ctypes.byref(ms), 0), "ov_profile_read")
+        out[name] = (n.value, ms.value)
+    if reset:
+        n = ctypes.c_int64(0)
+        ms = ctypes.c_double(0.0)
+        _check(lib.ov_profile_read(ctx, 0, ctypes.byref(n), ctypes.byref(ms), 1), "ov_profile_read")
+    return out
+
+
+def launch_count(ctx) -> int:
+    return int(load().ov_launch_count(ctx))

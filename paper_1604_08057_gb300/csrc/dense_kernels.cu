@@ -75,95 +75,136 @@ void dense_extract_tri(const zd* e, int k, zd* ga, zd* gb, double* gd, cudaStrea
 }
 
 // ---------------------------------------------------------------------------
-// Gauss-Jordan inversion in place, partial pivoting by row swaps; the column
-// order is restored at the end in reverse pivot order.
+// Gauss-Jordan inversion with partial pivoting and no row swaps: at step kk
+// the pivot is the unused row p_kk with the largest |X[p][kk]|; row p_kk is
+// normalised and column kk is eliminated from every other row (the inverse is
+// built in place, column kk receiving -X[i][kk]/pivot).  One launch per step,
+// reading X_in and writing X_out (ping-pong), so no block sees a row that
+// another block has already rewritten.  The pivot search of step kk+1 is
+// fused into step kk as per-block candidates.  At the end
+//   inv(A)[i][j] = X[p_i][q_j],  q = p^{-1}.
 // ---------------------------------------------------------------------------
-constexpr int PIV_THREADS = 1024;
+constexpr int GJ_THREADS = 256;
+constexpr int GJ_ROWS = 4;
 
-__global__ void __launch_bounds__(PIV_THREADS) k_gj_pivot(zd* x, int k, int kk, int* ipiv, zd* prow, zd* col,
-                                                          double* logdet, int* err) {
-  __shared__ double sv[PIV_THREADS / 32];
-  __shared__ int si[PIV_THREADS / 32];
-  __shared__ int sp;
-  __shared__ zd spiv;
-  // argmax |x[i][kk]|, i >= kk (ties to the smaller index)
-  double best = -1.0;
-  int bi = kk;
-  for (int i = kk + threadIdx.x; i < k; i += blockDim.x) {
-    const double a = norm2(x[(int64_t)i * k + kk]);
-    if (a > best) { best = a; bi = i; }
-  }
+struct Cand { double v; int i; };
+
+__device__ __forceinline__ Cand cand_max(Cand a, Cand b) {
+  return (b.v > a.v || (b.v == a.v && b.i < a.i)) ? b : a;
+}
+__device__ __forceinline__ Cand block_cand_max(Cand c, Cand* sh) {
   for (int o = 16; o > 0; o >>= 1) {
-    const double ob = __shfl_down_sync(0xffffffffu, best, o);
-    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    Cand d;
+    d.v = __shfl_down_sync(0xffffffffu, c.v, o);
+    d.i = __shfl_down_sync(0xffffffffu, c.i, o);
+    c = cand_max(c, d);
   }
-  if ((threadIdx.x & 31) == 0) { sv[threadIdx.x >> 5] = best; si[threadIdx.x >> 5] = bi; }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-      if (sv[w] > sv[0] || (sv[w] == sv[0] && si[w] < si[0])) { sv[0] = sv[w]; si[0] = si[w]; }
-    sp = si[0];
-    ipiv[kk] = sp;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) c = cand_max(c, sh[w]);
+    sh[0] = c;
   }
   __syncthreads();
-  const int p = sp;
-  if (p != kk) {
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-      const zd a = x[(int64_t)kk * k + c];
-      x[(int64_t)kk * k + c] = x[(int64_t)p * k + c];
-      x[(int64_t)p * k + c] = a;
+  const Cand r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// candidates for column 0; clears the used-row flags
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_init(const zd* __restrict__ x, int k, Cand* cand, int* used) {
+  __shared__ Cand sh[GJ_THREADS / 32];
+  const int r0 = blockIdx.x * GJ_ROWS;
+  Cand c{-1.0, 0x7fffffff};
+  for (int t = threadIdx.x; t < GJ_ROWS; t += blockDim.x) {
+    const int i = r0 + t;
+    if (i < k) {
+      used[i] = 0;
+      c = cand_max(c, Cand{norm2(x[(int64_t)i * k]), i});
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    spiv = x[(int64_t)kk * k + kk];
-    const double a = sqrt(norm2(spiv));
+  c = block_cand_max(c, sh);
+  if (threadIdx.x == 0) cand[blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(GJ_THREADS) k_gj_step(const zd* __restrict__ xin, zd* __restrict__ xout, int k,
+                                                        int kk, const Cand* __restrict__ cin, Cand* cout, int* used,
+                                                        int* prows, double* logdet, int* err) {
+  extern __shared__ zd prow[];
+  __shared__ Cand sh[GJ_THREADS / 32];
+  // pivot of column kk from the candidates of the previous step
+  Cand c{-1.0, 0x7fffffff};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) c = cand_max(c, cin[b]);
+  c = block_cand_max(c, sh);
+  // a NaN column leaves no valid candidate: keep the indices in range and flag it
+  const bool bad = c.i < 0 || c.i >= k;
+  const int p = bad ? kk : c.i;
+  if (bad && blockIdx.x == 0 && threadIdx.x == 0) *err |= ERRB_SINGULAR;
+  const zd piv = xin[(int64_t)p * k + kk];
+  const zd inv = zdiv(mk(1.0, 0.0), piv);
+  for (int j = threadIdx.x; j < k; j += blockDim.x) prow[j] = (j == kk) ? inv : xin[(int64_t)p * k + j] * inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double a = sqrt(norm2(piv));
     if (!(a > 0.0) || !isfinite(a)) *err |= ERRB_SINGULAR;
     *logdet += log(a);
+    prows[kk] = p;
   }
   __syncthreads();
-  const zd inv = zdiv(mk(1.0, 0.0), spiv);
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    const zd v = (c == kk) ? inv : x[(int64_t)kk * k + c] * inv;
-    prow[c] = v;
-    x[(int64_t)kk * k + c] = v;
-  }
-  for (int i = threadIdx.x; i < k; i += blockDim.x)
-    if (i != kk) col[i] = x[(int64_t)i * k + kk];
-}
-
-__global__ void k_gj_elim(zd* x, int k, int kk, const zd* __restrict__ prow, const zd* __restrict__ col) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= k || c >= k || i == kk) return;
-  const zd f = col[i];
-  const int64_t o = (int64_t)i * k + c;
-  if (c == kk) x[o] = -(f * prow[kk]);
-  else x[o] = x[o] - f * prow[c];
-}
-
-__global__ void k_gj_unscramble(zd* x, int k, const int* __restrict__ ipiv) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= k) return;
-  for (int kk = k - 1; kk >= 0; --kk) {
-    const int p = ipiv[kk];
-    if (p != kk) {
-      const zd a = x[(int64_t)i * k + kk];
-      x[(int64_t)i * k + kk] = x[(int64_t)i * k + p];
-      x[(int64_t)i * k + p] = a;
+  const int r0 = blockIdx.x * GJ_ROWS;
+  const int nrow = min(GJ_ROWS, k - r0);
+  Cand nc{-1.0, 0x7fffffff};
+  for (int e = threadIdx.x; e < nrow * k; e += blockDim.x) {
+    const int i = r0 + e / k, j = e % k;
+    const int64_t o = (int64_t)i * k + j;
+    zd v;
+    if (i == p) {
+      v = prow[j];
+    } else {
+      const zd f = xin[(int64_t)i * k + kk];
+      v = (j == kk) ? -(f * prow[kk]) : xin[o] - f * prow[j];
     }
+    xout[o] = v;
+    if (j == kk + 1 && i != p && !used[i]) nc = cand_max(nc, Cand{norm2(v), i});
   }
+  nc = block_cand_max(nc, sh);
+  if (threadIdx.x == 0) cout[blockIdx.x] = nc;
+  if (p >= r0 && p < r0 + nrow && threadIdx.x == 0) used[p] = 1;
 }
 
-void dense_inverse(zd* x, int k, int* ipiv, zd* prow, zd* col, double* logdet, int* err, cudaStream_t st) {
-  const dim3 eb(32, 8);
-  const dim3 eg(nblk(k, 32), nblk(k, 8));
-  for (int kk = 0; kk < k; ++kk) {
-    k_gj_pivot<<<1, PIV_THREADS, 0, st>>>(x, k, kk, ipiv, prow, col, logdet, err);
-    k_gj_elim<<<eg, eb, 0, st>>>(x, k, kk, prow, col);
+__global__ void k_gj_invperm(const int* __restrict__ prows, int* q, int k) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < k) q[prows[c]] = c;
+}
+__global__ void k_gj_gather(const zd* __restrict__ x, zd* __restrict__ out, const int* __restrict__ prows,
+                            const int* __restrict__ q, int k) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)k * k) return;
+  const int i = (int)(t / k), j = (int)(t % k);
+  out[t] = x[(int64_t)prows[i] * k + q[j]];
+}
+
+void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, Cand2* cand,
+                   double* logdet, int* err, cudaStream_t st) {
+  Cand* cd = reinterpret_cast<Cand*>(cand);
+  const unsigned nb = nblk(k, GJ_ROWS);
+  const size_t smem = (size_t)k * sizeof(zd);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
   }
-  k_gj_unscramble<<<nblk(k, 128), 128, 0, st>>>(x, k, ipiv);
+  k_gj_init<<<nb, GJ_THREADS, 0, st>>>(a, k, cd, used);
+  const zd* in = a;
+  zd* bufs[2] = {w0, w1};
+  for (int kk = 0; kk < k; ++kk) {
+    zd* out = bufs[kk & 1];
+    k_gj_step<<<nb, GJ_THREADS, smem, st>>>(in, out, k, kk, cd + (kk & 1) * nb, cd + ((kk + 1) & 1) * nb, used,
+                                            ipiv, logdet, err);
+    in = out;
+  }
+  int* q = used;   // the flags are no longer needed
+  k_gj_invperm<<<nblk(k, 128), 128, 0, st>>>(ipiv, q, k);
+  k_gj_gather<<<nblk((int64_t)k * k, 256), 256, 0, st>>>(in, ainv, ipiv, q, k);
 }
 
 // ---------------------------------------------------------------------------

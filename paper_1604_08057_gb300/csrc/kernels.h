@@ -80,8 +80,10 @@ template <typename R> void tsl_update(const Lat<R>& L, int j, bool finalize, cud
 // projection of (r, s) against bases (A: dots with `a` vector, B: dots with `b` vector).
 // mode 0 (forward):  c = W^dag r, d = V^dag s;  r -= V c, s -= W d
 // mode 1 (adjoint):  e_r = V^dag g_r, e_s = W^dag g_s;  g_r -= W e_r, g_s -= V e_s
-template <typename R> void tsl_project(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_src_stride,
-                                       zd* coef, zd* cpart, bool finalize_omega, cudaStream_t st);
+template <typename R> void proj_dots(const Lat<R>& L, int j, int mode, const R* a, const R* b,
+                                     int64_t ab_src_stride, zd* coef, zd* cpart, cudaStream_t st);
+template <typename R> void proj_update(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_src_stride,
+                                       const zd* coef, bool finalize_omega, cudaStream_t st);
 template <typename R> void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_src_stride, zd* out,
                                       zd* cpart, cudaStream_t st);
 template <typename R> void combine(const Lat<R>& L, int nvec, const zd* y, double* out_aos, cudaStream_t st);
@@ -103,8 +105,12 @@ void dense_build_t(const zd* alpha, const zd* beta, const double* delta, int k, 
 void dense_adjoint(const zd* A, zd* B, int k, cudaStream_t st);
 void dense_copy(const zd* A, zd* B, int64_t n, cudaStream_t st);
 void dense_zero(zd* A, int64_t n, cudaStream_t st);
-// in-place inverse by Gauss-Jordan with partial pivoting; logdet[0] += sum log|pivot|
-void dense_inverse(zd* X, int k, int* ipiv, zd* prow, zd* col, double* logdet, int* err, cudaStream_t st);
+// Ainv = A^{-1} by Gauss-Jordan with partial pivoting (A is not modified; w0, w1 are
+// k x k work buffers; ipiv, used: k ints; cand: 2 * ceil(k/4) entries);
+// logdet[0] += sum log|pivot| = log|det A|
+struct Cand2 { double v; int i; int pad; };
+void dense_inverse(const zd* A, zd* Ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, Cand2* cand,
+                   double* logdet, int* err, cudaStream_t st);
 void dense_gemm(const zd* A, const zd* B, zd* C, int k, cudaStream_t st);   // C = A B
 // Xn = 0.5 (g X + s Xi / g) with g = |det|^(-1/k) from *logdet when scaling, else 1;
 // stats[0] += w |Xn - X|^2, stats[1] += w |Xn|^2 (deterministic order)

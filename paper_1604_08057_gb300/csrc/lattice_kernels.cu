@@ -430,8 +430,8 @@ __global__ void __launch_bounds__(BS) k_proj_update(Lat<R> L, int nb, int mode, 
 }
 
 template <typename R>
-void tsl_project(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_stride, zd* coef, zd* cpart,
-                 bool finalize, cudaStream_t st) {
+void proj_dots(const Lat<R>& L, int j, int mode, const R* a, const R* b, int64_t ab_stride, zd* coef,
+               zd* cpart, cudaStream_t st) {
   const int nb = j + 1;
   const unsigned nsb = nblocks(L.g.V, BS);
   const int64_t cp_stride = (int64_t)2 * L.k * nsb;
@@ -439,8 +439,12 @@ void tsl_project(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_stride
                                                                      cp_stride);
   k_proj_reduce<<<dim3(nblocks(2 * nb, 128), L.nsrc), 128, 0, st>>>(cpart, cp_stride, nsb, nb, coef,
                                                                       2 * (int64_t)L.k);
-  k_proj_update<R><<<dim3(nsb, L.nsrc), BS, 0, st>>>(L, nb, mode, a, b, ab_stride, coef, 2 * (int64_t)L.k, j,
-                                                      finalize ? 1 : 0);
+}
+template <typename R>
+void proj_update(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_stride, const zd* coef, bool finalize,
+                 cudaStream_t st) {
+  k_proj_update<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, j + 1, mode, a, b, ab_stride, coef,
+                                                                     2 * (int64_t)L.k, j, finalize ? 1 : 0);
 }
 
 // out[src][i] = v_i^dag x  for i < nvec (dots of the V basis with one vector per source)
@@ -914,7 +918,8 @@ void force_flush(const Lat<R>& L, const Rev<R>& B, const int* /*unused*/, int nt
   template void tsl_init<R>(const Lat<R>&, cudaStream_t);                                                \
   template void tsl_stencil<R>(const Lat<R>&, int, bool, cudaStream_t);                                  \
   template void tsl_update<R>(const Lat<R>&, int, bool, cudaStream_t);                                   \
-  template void tsl_project<R>(const Lat<R>&, int, int, R*, R*, int64_t, zd*, zd*, bool, cudaStream_t);  \
+  template void proj_dots<R>(const Lat<R>&, int, int, const R*, const R*, int64_t, zd*, zd*, cudaStream_t); \
+  template void proj_update<R>(const Lat<R>&, int, int, R*, R*, int64_t, const zd*, bool, cudaStream_t);   \
   template void basis_dots<R>(const Lat<R>&, int, const R*, int64_t, zd*, zd*, cudaStream_t);            \
   template void combine<R>(const Lat<R>&, int, const zd*, double*, cudaStream_t);                        \
   template void rev_init<R>(const Lat<R>&, const Rev<R>&, cudaStream_t);                                 \

@@ -17,7 +17,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, NBUF
 };
 
 struct Status {
@@ -45,6 +45,17 @@ int rebiorth_at(int step, int period) {
 
 }  // namespace
 
+constexpr int NPROF = 8192;   // event pairs recorded before an intermediate collection
+
+struct Prof {
+  bool on = false;
+  int n = 0;
+  cudaEvent_t a[NPROF] = {}, b[NPROF] = {};
+  int kind[NPROF] = {};
+  double ms[OV_NKIND] = {};
+  int64_t cnt[OV_NKIND] = {};
+};
+
 struct ov_context {
   cudaStream_t st = nullptr;
   ov_options opt{};
@@ -53,9 +64,40 @@ struct ov_context {
   // coefficients of the last forward pass (for ov_tsl_coefficients)
   int last_k = 0, last_nsrc = 0;
   cudaEvent_t ev[8] = {};
+  Prof* prof = nullptr;
+  int64_t launches = 0;
 };
 
 namespace {
+
+// add the recorded event pairs to the per-kind totals (synchronises the stream)
+void prof_collect(ov_context* c) {
+  Prof* p = c->prof;
+  if (!p || p->n == 0) return;
+  CK(cudaStreamSynchronize(c->st));
+  for (int i = 0; i < p->n; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p->a[i], p->b[i]));
+    p->ms[p->kind[i]] += ms;
+    p->cnt[p->kind[i]] += 1;
+  }
+  p->n = 0;
+}
+
+// run a launcher that enqueues `nl` kernels; time it when profiling is on
+template <typename F>
+void run(ov_context* c, int kind, int64_t nl, F&& f) {
+  Prof* p = c->prof;
+  const bool rec = p && p->on;
+  if (rec && p->n == NPROF) prof_collect(c);
+  if (rec) CK(cudaEventRecord(p->a[p->n], c->st));
+  f();
+  if (rec) {
+    CK(cudaEventRecord(p->b[p->n], c->st));
+    p->kind[p->n++] = kind;
+  }
+  c->launches += nl;
+}
 
 void* ws(ov_context* c, int id, size_t bytes, bool zero = false) {
   if (bytes == 0) bytes = 16;
@@ -112,7 +154,7 @@ Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, dou
   L.vs = ((24 * V + 63) / 64) * 64;
   R* u = wsT<R>(c, B_LINKS, 72 * V);
   L.u = u;
-  pack_links<R>(static_cast<const double*>(U), u, V, c->st);
+  run(c, OV_KIND_LAYOUT, 1, [&] { pack_links<R>(static_cast<const double*>(U), u, V, c->st); });
   launch_check();
   if (basis) {
     L.bv = wsT<R>(c, B_BV, (int64_t)nsrc * k * L.vs);
@@ -160,15 +202,18 @@ void forward_krylov(ov_context* c, Lat<R>& L) {
   const int64_t nsb = (L.g.V + 127) / 128;
   zd* coef = wsT<zd>(c, B_COEF, (int64_t)L.nsrc * 2 * k);
   zd* cpart = wsT<zd>(c, B_CPART, (int64_t)L.nsrc * 2 * k * nsb);
-  tsl_init(L, c->st);
+  run(c, OV_KIND_UPDATE, 1, [&] { tsl_init(L, c->st); });
   for (int j = 0; j < k; ++j) {
-    tsl_stencil(L, j, j < k - 1, c->st);
+    run(c, OV_KIND_STENCIL_PAIR, 1, [&] { tsl_stencil(L, j, j < k - 1, c->st); });
     if (j == k - 1) break;
     const int reb = rebiorth_at(j + 1, c->opt.rebiorth);
-    tsl_update(L, j, !reb, c->st);
+    run(c, OV_KIND_UPDATE, 1, [&] { tsl_update(L, j, !reb, c->st); });
     if (reb) {
-      for (int ps = 0; ps < c->opt.passes; ++ps)
-        tsl_project(L, j, 0, L.r, L.s, L.vs, coef, cpart, ps == c->opt.passes - 1, c->st);
+      for (int ps = 0; ps < c->opt.passes; ++ps) {
+        run(c, OV_KIND_PROJ_DOTS, 2, [&] { proj_dots(L, j, 0, L.r, L.s, L.vs, coef, cpart, c->st); });
+        run(c, OV_KIND_PROJ_UPDATE, 1,
+            [&] { proj_update(L, j, 0, L.r, L.s, L.vs, coef, ps == c->opt.passes - 1, c->st); });
+      }
     }
   }
   launch_check();
@@ -185,8 +230,10 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which) {
   zd* t1 = e ? wsT<zd>(c, B_TMP1, n) : nullptr;
   zd* t2 = e ? wsT<zd>(c, B_TMP2, n) : nullptr;
   int* ipiv = wsT<int>(c, B_IPIV, k);
-  zd* prow = wsT<zd>(c, B_PROW, k);
-  zd* col = wsT<zd>(c, B_COL, k);
+  int* used = wsT<int>(c, B_COL, k);
+  Cand2* cand = wsT<Cand2>(c, B_PROW, 2 * ((k + 3) / 4) + 8);
+  zd* w0 = wsT<zd>(c, B_W0, n);
+  zd* w1 = wsT<zd>(c, B_W1, n);
   double* dstat = wsT<double>(c, B_DSTAT, 4);   // [0] diff^2, [1] norm^2, [2] log|det|
   zd* dpart = wsT<zd>(c, B_DPART, (n + 255) / 256 + 64);
   unsigned* dcnt = wsT<unsigned>(c, B_DCNT, 4);
@@ -196,18 +243,23 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which) {
   double hs[3];
   for (it = 1; it <= 100; ++it) {
     CK(cudaMemsetAsync(dstat, 0, 3 * sizeof(double), c->st));
-    dense_copy(a[cur], ai, n, c->st);
-    dense_inverse(ai, k, ipiv, prow, col, dstat + 2, err_dev, c->st);
+    run(c, OV_KIND_DENSE, (int64_t)k + 3, [&] {
+      dense_inverse(a[cur], ai, w0, w1, k, ipiv, used, cand, dstat + 2, err_dev, c->st);
+    });
     if (e) {
-      dense_gemm(ai, e[cur], t1, k, c->st);
-      dense_gemm(t1, ai, t2, k, c->st);
+      run(c, OV_KIND_DENSE_GEMM, 2, [&] {
+        dense_gemm(ai, e[cur], t1, k, c->st);
+        dense_gemm(t1, ai, t2, k, c->st);
+      });
     }
     // the block determinant is det(A)^2: its 1/(2k)-th root is det(A)^(1/k)
-    dense_newton_combine(a[cur], ai, a[1 - cur], k, dstat + 2, scaling ? 1 : 0, 1.0, e ? 2.0 : 1.0, dstat,
-                         dpart, dcnt, c->st);
-    if (e)
-      dense_newton_combine(e[cur], t2, e[1 - cur], k, dstat + 2, scaling ? 1 : 0, -1.0, 1.0, dstat, dpart, dcnt,
-                           c->st);
+    run(c, OV_KIND_DENSE, e ? 2 : 1, [&] {
+      dense_newton_combine(a[cur], ai, a[1 - cur], k, dstat + 2, scaling ? 1 : 0, 1.0, e ? 2.0 : 1.0, dstat,
+                           dpart, dcnt, c->st);
+      if (e)
+        dense_newton_combine(e[cur], t2, e[1 - cur], k, dstat + 2, scaling ? 1 : 0, -1.0, 1.0, dstat, dpart,
+                             dcnt, c->st);
+    });
     launch_check();
     CK(cudaMemcpyAsync(hs, dstat, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -232,13 +284,15 @@ int sign_all(ov_context* c, Lat<R>& L, const std::vector<SrcScal>& hsc, zd* y, i
   int maxit = 0;
   zd* a[2] = {wsT<zd>(c, B_X, n), wsT<zd>(c, B_XN, n)};
   for (int src = 0; src < L.nsrc; ++src) {
-    dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, a[0],
-                  c->st);
+    run(c, OV_KIND_DENSE, 2, [&] {
+      dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, a[0],
+                    c->st);
+    });
     int which = 0;
     const int it = newton(c, a, nullptr, k, derr, &which);
     if (it < 0) return OV_ERR_SIGN_ILLPOSED;
     if (it > maxit) maxit = it;
-    dense_extract_y(a[which], hsc[src].beta0, k, y + (int64_t)src * k, c->st);
+    run(c, OV_KIND_DENSE, 1, [&] { dense_extract_y(a[which], hsc[src].beta0, k, y + (int64_t)src * k, c->st); });
   }
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -260,8 +314,10 @@ int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   check_ptr(b);
   check_ptr(x);
   Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true);
-  pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, L.g.V, L.vs, c->st);
-  pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, L.g.V, L.vs, c->st);
+  run(c, OV_KIND_LAYOUT, 2, [&] {
+    pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, L.g.V, L.vs, c->st);
+    pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, L.g.V, L.vs, c->st);
+  });
   CK(cudaEventRecord(c->ev[0], c->st));
   forward_krylov(c, L);
   CK(cudaEventRecord(c->ev[1], c->st));
@@ -277,10 +333,11 @@ int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   st = sign_all(c, L, hsc, y, &iters);
   if (st != OV_OK) return st;
   CK(cudaEventRecord(c->ev[2], c->st));
-  combine(L, k, y, static_cast<double*>(x), c->st);
+  run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
   launch_check();
   CK(cudaEventRecord(c->ev[3], c->st));
   CK(cudaStreamSynchronize(c->st));
+  prof_collect(c);
   if (info) {
     info->newton_iters = iters;
     info->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
@@ -300,8 +357,10 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   if (x) check_ptr(x);
   Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true);
   const int64_t V = L.g.V, vs = L.vs;
-  pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, V, vs, c->st);
-  pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, V, vs, c->st);
+  run(c, OV_KIND_LAYOUT, 2, [&] {
+    pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, V, vs, c->st);
+    pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, V, vs, c->st);
+  });
   CK(cudaEventRecord(c->ev[0], c->st));
   forward_krylov(c, L);
   CK(cudaEventRecord(c->ev[1], c->st));
@@ -317,14 +376,14 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   st = sign_all(c, L, hsc, y, &iters);
   if (st != OV_OK) return st;
   CK(cudaEventRecord(c->ev[2], c->st));
-  if (x) combine(L, k, y, static_cast<double*>(x), c->st);
+  if (x) run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
   // g_y = V^dag xbar
   R* xb = wsT<R>(c, B_XBAR, nsrc * vs);
-  pack_spinors<R>(static_cast<const double*>(xbar), xb, nsrc, V, vs, c->st);
+  run(c, OV_KIND_LAYOUT, 1, [&] { pack_spinors<R>(static_cast<const double*>(xbar), xb, nsrc, V, vs, c->st); });
   const int64_t nsb = (V + 127) / 128;
   zd* gy = wsT<zd>(c, B_GY, (int64_t)nsrc * 2 * k);
   zd* cpart = wsT<zd>(c, B_CPART, (int64_t)nsrc * 2 * k * nsb);
-  basis_dots(L, k, xb, vs, gy, cpart, c->st);
+  run(c, OV_KIND_COMBINE, 2, [&] { basis_dots(L, k, xb, vs, gy, cpart, c->st); });
   launch_check();
   CK(cudaEventRecord(c->ev[3], c->st));
   // G_T = L_sgn(T^dag, beta0 g_y e_1^T) from the Theorem-1 block matrix
@@ -339,16 +398,20 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
     zd* a[2] = {wsT<zd>(c, B_X, n), wsT<zd>(c, B_XN, n)};
     zd* e[2] = {wsT<zd>(c, B_E, n), wsT<zd>(c, B_EN, n)};
     for (int src = 0; src < nsrc; ++src) {
-      dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, t,
-                    c->st);
-      dense_adjoint(t, a[0], k, c->st);
-      dense_set_column0(e[0], gy + (int64_t)src * 2 * k, 2, hsc[src].beta0, k, c->st);
+      run(c, OV_KIND_DENSE, 5, [&] {
+        dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, t,
+                      c->st);
+        dense_adjoint(t, a[0], k, c->st);
+        dense_set_column0(e[0], gy + (int64_t)src * 2 * k, 2, hsc[src].beta0, k, c->st);
+      });
       int which = 0;
       const int it = newton(c, a, e, k, derr, &which);
       if (it < 0) return OV_ERR_SIGN_ILLPOSED;
       if (it > iters_adj) iters_adj = it;
-      dense_extract_tri(e[which], k, gaT + (int64_t)src * k, gbT + (int64_t)src * k, gdT + (int64_t)src * k,
-                        c->st);
+      run(c, OV_KIND_DENSE, 1, [&] {
+        dense_extract_tri(e[which], k, gaT + (int64_t)src * k, gbT + (int64_t)src * k, gdT + (int64_t)src * k,
+                          c->st);
+      });
     }
   }
   {
@@ -391,42 +454,44 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   B.dmu_part = wsT<zd>(c, B_DMUPART, 4 * ((V + 127) / 128) + 64);
   B.dmu_cnt = wsT<unsigned>(c, B_DMUCNT, 4);
   zd* coef = wsT<zd>(c, B_COEF, (int64_t)nsrc * 2 * k);
-  rev_init(L, B, c->st);
-  rev_stencil(L, B, k - 1, 0, -1, 0, c->st);
+  run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_init(L, B, c->st); });
+  run(c, OV_KIND_REV_STENCIL, 1, [&] { rev_stencil(L, B, k - 1, 0, -1, 0, c->st); });
   std::swap(B.gv, B.gv_new);
   std::swap(B.gw, B.gw_new);
   int slot = 1, j0 = k - 1, nrec = 0;
   for (int j = k - 2; j >= 0; --j) {
     if (slot == m) {
-      force_flush(L, B, nullptr, m, j0, c->st);
+      run(c, OV_KIND_FORCE, 1, [&] { force_flush(L, B, nullptr, m, j0, c->st); });
       slot = 0;
       j0 = j;
     }
     const int prev = slot == 0 ? m - 1 : slot - 1;
-    rev_dots(L, B, j, c->st);
+    run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_dots(L, B, j, c->st); });
     const int rb = rebiorth_at(j + 1, c->opt.rebiorth);
-    rev_form(L, B, j, slot, !rb, c->st);
+    run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_form(L, B, j, slot, !rb, c->st); });
     if (rb) {
       R* grs = B.gr_ring + (int64_t)slot * nsrc * vs;
       R* gss = B.gs_ring + (int64_t)slot * nsrc * vs;
       for (int ps = 0; ps < c->opt.passes; ++ps) {
-        tsl_project(L, j, 1, grs, gss, vs, coef, cpart, false, c->st);
-        rev_proj_record(L, B, j, nrec, coef, c->st);
+        run(c, OV_KIND_PROJ_DOTS, 2, [&] { proj_dots(L, j, 1, grs, gss, vs, coef, cpart, c->st); });
+        run(c, OV_KIND_PROJ_UPDATE, 1, [&] { proj_update(L, j, 1, grs, gss, vs, coef, false, c->st); });
+        run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_proj_record(L, B, j, nrec, coef, c->st); });
       }
-      rev_alpha_dots(L, B, j, slot, c->st);
+      run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_alpha_dots(L, B, j, slot, c->st); });
       ++nrec;
     }
-    rev_stencil(L, B, j, slot, prev, nrec, c->st);
+    run(c, OV_KIND_REV_STENCIL, 1, [&] { rev_stencil(L, B, j, slot, prev, nrec, c->st); });
     std::swap(B.gv, B.gv_new);
     std::swap(B.gw, B.gw_new);
     ++slot;
   }
-  force_flush(L, B, nullptr, slot, j0, c->st);
+  run(c, OV_KIND_FORCE, 1, [&] { force_flush(L, B, nullptr, slot, j0, c->st); });
   CK(cudaEventRecord(c->ev[5], c->st));
-  unpack_force(B.force, static_cast<double*>(dU), V, c->st);
+  run(c, OV_KIND_LAYOUT, 1, [&] { unpack_force(B.force, static_cast<double*>(dU), V, c->st); });
   launch_check();
   CK(cudaMemcpyAsync(dmu, B.dmu, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   auto hsc2 = read_scalars(c, L.sc, nsrc);
+  prof_collect(c);
   st = scalar_status(hsc2, nullptr, k);
   if (st != OV_OK) return st;
   if (info) {
@@ -447,11 +512,14 @@ int apply_h_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   check_ptr(in);
   check_ptr(out);
   Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, 1, false);
-  pack_spinors<R>(static_cast<const double*>(in), L.r, nsrc, L.g.V, L.vs, c->st);
-  apply_h(L, L.r, L.p, dagger, c->st);
-  unpack_spinors<R>(L.p, static_cast<double*>(out), nsrc, L.g.V, L.vs, c->st);
+  run(c, OV_KIND_LAYOUT, 1,
+      [&] { pack_spinors<R>(static_cast<const double*>(in), L.r, nsrc, L.g.V, L.vs, c->st); });
+  run(c, OV_KIND_APPLY_H, 1, [&] { apply_h(L, L.r, L.p, dagger, c->st); });
+  run(c, OV_KIND_LAYOUT, 1,
+      [&] { unpack_spinors<R>(L.p, static_cast<double*>(out), nsrc, L.g.V, L.vs, c->st); });
   launch_check();
   CK(cudaStreamSynchronize(c->st));
+  prof_collect(c);
   return OV_OK;
 }
 
@@ -507,9 +575,52 @@ int ov_context_destroy(ov_context* c) {
     if (c->buf[i]) cudaFree(c->buf[i]);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->prof) {
+    for (int i = 0; i < NPROF; ++i) {
+      if (c->prof->a[i]) cudaEventDestroy(c->prof->a[i]);
+      if (c->prof->b[i]) cudaEventDestroy(c->prof->b[i]);
+    }
+    delete c->prof;
+  }
   delete c;
   return OV_OK;
 }
+
+int ov_profile_enable(ov_context* c, int32_t enable) {
+  if (!c) return OV_ERR_INVALID_ARG;
+  if (!c->prof) {
+    if (!enable) return OV_OK;
+    c->prof = new (std::nothrow) Prof();
+    if (!c->prof) return OV_ERR_OOM;
+    for (int i = 0; i < NPROF; ++i) {
+      if (cudaEventCreate(&c->prof->a[i]) != cudaSuccess || cudaEventCreate(&c->prof->b[i]) != cudaSuccess) {
+        cudaGetLastError();
+        return OV_ERR_CUDA;
+      }
+    }
+  }
+  c->prof->on = enable != 0;
+  return OV_OK;
+}
+
+int ov_profile_read(ov_context* c, int32_t kind, int64_t* launches, double* ms, int32_t reset) {
+  if (!c || kind < 0 || kind >= OV_NKIND || !launches || !ms) return OV_ERR_INVALID_ARG;
+  if (!c->prof) {
+    *launches = 0;
+    *ms = 0.0;
+    return OV_OK;
+  }
+  const int st = guarded([&] { prof_collect(c); return OV_OK; });
+  if (st != OV_OK) return st;
+  *launches = c->prof->cnt[kind];
+  *ms = c->prof->ms[kind];
+  if (reset) {
+    for (int i = 0; i < OV_NKIND; ++i) { c->prof->cnt[i] = 0; c->prof->ms[i] = 0.0; }
+  }
+  return OV_OK;
+}
+
+int64_t ov_launch_count(ov_context* c) { return c ? c->launches : -1; }
 
 int ov_context_set_options(ov_context* c, const ov_options* opt) {
   if (!c || !opt || !valid_options(opt)) return OV_ERR_INVALID_ARG;
