@@ -58,6 +58,15 @@ template <typename R> OV_HD cplx<R> cast(zd a) { return mk<R>((R)a.re, (R)a.im);
 // ---------------------------------------------------------------------------
 template <typename R> struct Spinor { cplx<R> c[12]; };
 
+// read-only loads go through the non-coherent path on the device
+template <typename T> OV_HD T ldro(const T* p) {
+#ifdef __CUDA_ARCH__
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
+
 OV_HD void load_spinor(const double* f, int64_t V, int64_t s, Spinor<double>& o) {
   const double2* p = reinterpret_cast<const double2*>(f);
 #pragma unroll
@@ -68,6 +77,21 @@ OV_HD void load_spinor(const float* f, int64_t V, int64_t s, Spinor<float>& o) {
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
     float4 t = p[c * V + s];
+    o.c[2 * c] = mk(t.x, t.y);
+    o.c[2 * c + 1] = mk(t.z, t.w);
+  }
+}
+// the same through the read-only path (only for fields no kernel thread writes)
+OV_HD void load_spinor_ro(const double* f, int64_t V, int64_t s, Spinor<double>& o) {
+  const double2* p = reinterpret_cast<const double2*>(f);
+#pragma unroll
+  for (int c = 0; c < 12; ++c) { double2 t = ldro(p + c * V + s); o.c[c] = mk(t.x, t.y); }
+}
+OV_HD void load_spinor_ro(const float* f, int64_t V, int64_t s, Spinor<float>& o) {
+  const float4* p = reinterpret_cast<const float4*>(f);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    float4 t = ldro(p + c * V + s);
     o.c[2 * c] = mk(t.x, t.y);
     o.c[2 * c + 1] = mk(t.z, t.w);
   }
@@ -84,9 +108,13 @@ OV_HD void store_spinor(float* f, int64_t V, int64_t s, const Spinor<float>& o) 
     p[c * V + s] = make_float4(o.c[2 * c].re, o.c[2 * c].im, o.c[2 * c + 1].re, o.c[2 * c + 1].im);
 }
 
-template <typename R>
-OV_HD cplx<R> load_link_entry(const R* u, int64_t V, int64_t s, int e) {
-  return mk(u[2 * (e * V + s)], u[2 * (e * V + s) + 1]);
+OV_HD cplx<double> load_link_entry(const double* u, int64_t V, int64_t s, int e) {
+  const double2 t = ldro(reinterpret_cast<const double2*>(u) + e * V + s);
+  return mk(t.x, t.y);
+}
+OV_HD cplx<float> load_link_entry(const float* u, int64_t V, int64_t s, int e) {
+  const float2 t = ldro(reinterpret_cast<const float2*>(u) + e * V + s);
+  return mk(t.x, t.y);
 }
 template <typename R> struct Mat3 { cplx<R> m[9]; };
 template <typename R>

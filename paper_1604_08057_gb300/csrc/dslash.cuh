@@ -93,7 +93,7 @@ template <typename R>
 struct FieldLoad {
   const R* f;
   int64_t V;
-  OV_HD void operator()(int64_t s, Spinor<R>& o) const { load_spinor(f, V, s, o); }
+  OV_HD void operator()(int64_t s, Spinor<R>& o) const { load_spinor_ro(f, V, s, o); }
 };
 
 // One direction's two hops of sum_nu [f (1+g) U_nu(x) psi(x+nu) + f^-1 (1-g) U_nu(x-nu)^dag psi(x-nu)]
@@ -146,6 +146,56 @@ OV_HD void h_site(const R* f, const R* u, const Geom& g, int64_t s, R kappa, R f
                   Spinor<R>& out) {
   FieldLoad<R> ld{f, g.V};
   h_site_ld(ld, u, g, s, kappa, ft, ftinv, out);
+}
+
+// NS right-hand sides sharing every link load: out[i] = gamma5 D_w psi_i with
+// ft[i] = e^{mu_i} on forward temporal hops (H uses mu, H^dagger uses -mu).
+template <int NU, int NS, typename R, typename LD>
+OV_HD void hop_dir_multi(Spinor<R> (&acc)[NS], const LD (&ld)[NS], const R* u, const Geom& g, int64_t s,
+                         const int c[4], const R (&ft)[NS], const R (&fti)[NS]) {
+  Spinor<R> nb;
+  Half<R> h, uh;
+  Mat3<R> lk;
+  const int64_t sf = neighbour(g, s, c, NU, +1);
+  load_link(u, g.V, s, NU, lk);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    ld[i](sf, nb);
+    spin_project<NU, +1>(nb, h);
+    link_mul(lk, h, uh);
+    spin_reconstruct_add<NU, +1>(acc[i], uh, NU == 3 ? ft[i] : R(1));
+  }
+  const int64_t sb = neighbour(g, s, c, NU, -1);
+  load_link(u, g.V, sb, NU, lk);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    ld[i](sb, nb);
+    spin_project<NU, -1>(nb, h);
+    link_dag_mul(lk, h, uh);
+    spin_reconstruct_add<NU, -1>(acc[i], uh, NU == 3 ? fti[i] : R(1));
+  }
+}
+
+template <int NS, typename R, typename LD>
+OV_HD void h_site_multi(const LD (&ld)[NS], const R* u, const Geom& g, int64_t s, R kappa, const R (&ft)[NS],
+                        const R (&fti)[NS], Spinor<R> (&out)[NS]) {
+  int c[4];
+  site_coords(g, s, c);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) spinor_zero(out[i]);
+  hop_dir_multi<0>(out, ld, u, g, s, c, ft, fti);
+  hop_dir_multi<1>(out, ld, u, g, s, c, ft, fti);
+  hop_dir_multi<2>(out, ld, u, g, s, c, ft, fti);
+  hop_dir_multi<3>(out, ld, u, g, s, c, ft, fti);
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    Spinor<R> p;
+    ld[i](s, p);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) out[i].c[q] = p.c[q] - kappa * out[i].c[q];
+#pragma unroll
+    for (int q = 6; q < 12; ++q) out[i].c[q] = kappa * out[i].c[q] - p.c[q];
+  }
 }
 
 // gamma5 (1 + sgn*gamma_nu) b, all four spins (used by the force contraction)

@@ -82,20 +82,36 @@ void unpack_force(const double* f, double* du, int64_t V, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // H and H^dagger
 // ---------------------------------------------------------------------------
-template <typename R>
+// NS sources per thread share every link load; blockIdx.y indexes groups of NS sources
+template <typename R, int NS>
 __global__ void __launch_bounds__(BS) k_apply_h(Lat<R> L, const R* __restrict__ in, R* __restrict__ out,
-                                                int dagger) {
+                                                int dagger, int nsrc) {
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int src = blockIdx.y;
+  const int s0 = blockIdx.y * NS;
   if (x >= L.g.V) return;
-  Spinor<R> o;
-  const R ft = dagger ? L.efinv : L.ef, fti = dagger ? L.ef : L.efinv;
-  h_site(in + src * L.vs, L.u, L.g, x, L.kappa, ft, fti, o);
-  store_spinor(out + src * L.vs, L.g.V, x, o);
+  const R f = dagger ? L.efinv : L.ef, fi = dagger ? L.ef : L.efinv;
+  FieldLoad<R> ld[NS];
+  R ft[NS], fti[NS];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    ld[i] = FieldLoad<R>{in + (int64_t)min(s0 + i, nsrc - 1) * L.vs, L.g.V};
+    ft[i] = f;
+    fti[i] = fi;
+  }
+  Spinor<R> o[NS];
+  h_site_multi<NS>(ld, L.u, L.g, x, L.kappa, ft, fti, o);
+#pragma unroll
+  for (int i = 0; i < NS; ++i)
+    if (s0 + i < nsrc) store_spinor(out + (int64_t)(s0 + i) * L.vs, L.g.V, x, o[i]);
 }
 template <typename R>
 void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st) {
-  k_apply_h<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, in, out, dagger);
+  constexpr int NS = sizeof(R) == 4 ? 4 : 2;
+  if (L.nsrc == 1)
+    k_apply_h<R, 1><<<dim3(nblocks(L.g.V, BS), 1), BS, 0, st>>>(L, in, out, dagger, 1);
+  else
+    k_apply_h<R, NS><<<dim3(nblocks(L.g.V, BS), (L.nsrc + NS - 1) / NS), BS, 0, st>>>(L, in, out, dagger,
+                                                                                       L.nsrc);
 }
 
 // ---------------------------------------------------------------------------
@@ -208,16 +224,25 @@ __global__ void __launch_bounds__(BS) k_tsl_stencil(Lat<R> L, int j, int need_q)
 #pragma unroll
     for (int c = 0; c < 12; ++c) w.c[c] = sw * w.c[c];
     store_spinor(L.basis_w(src, j), V, x, w);
-    h_site(rp, L.u, L.g, x, L.kappa, L.ef, L.efinv, o);
-#pragma unroll
-    for (int c = 0; c < 12; ++c) o.c[c] = sv * o.c[c];
-    store_spinor(L.p + src * L.vs, V, x, o);
-    v[0] = spinor_dot(w, o);
     if (need_q) {
-      h_site(sp, L.u, L.g, x, L.kappa, L.efinv, L.ef, o);
+      // H r and H^dag s share every link load
+      const FieldLoad<R> ld[2] = {FieldLoad<R>{rp, V}, FieldLoad<R>{sp, V}};
+      const R ft[2] = {L.ef, L.efinv}, fti[2] = {L.efinv, L.ef};
+      Spinor<R> hh[2];
+      h_site_multi<2>(ld, L.u, L.g, x, L.kappa, ft, fti, hh);
 #pragma unroll
-      for (int c = 0; c < 12; ++c) o.c[c] = sw * o.c[c];
+      for (int c = 0; c < 12; ++c) o.c[c] = sv * hh[0].c[c];
+      store_spinor(L.p + src * L.vs, V, x, o);
+      v[0] = spinor_dot(w, o);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) o.c[c] = sw * hh[1].c[c];
       store_spinor(L.q + src * L.vs, V, x, o);
+    } else {
+      h_site(rp, L.u, L.g, x, L.kappa, L.ef, L.efinv, o);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) o.c[c] = sv * o.c[c];
+      store_spinor(L.p + src * L.vs, V, x, o);
+      v[0] = spinor_dot(w, o);
     }
   }
   block_sum<1>(v, scratch);
