@@ -33,10 +33,28 @@ template <typename R> OV_HD R norm2(cplx<R> a) { return a.re * a.re + a.im * a.i
 template <typename R> OV_HD cplx<R> cdot(cplx<R> a, cplx<R> b) {
   return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
 }
-// acc += a * b
+OV_HD double fma_(double a, double b, double c) { return fma(a, b, c); }
+OV_HD float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+// acc += a * b, as four fused multiply-adds
 template <typename R> OV_HD void cmac(cplx<R>& acc, cplx<R> a, cplx<R> b) {
-  acc.re += a.re * b.re - a.im * b.im;
-  acc.im += a.re * b.im + a.im * b.re;
+  acc.re = fma_(a.re, b.re, acc.re);
+  acc.re = fma_(-a.im, b.im, acc.re);
+  acc.im = fma_(a.re, b.im, acc.im);
+  acc.im = fma_(a.im, b.re, acc.im);
+}
+// acc -= a * b
+template <typename R> OV_HD void cmsub(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma_(-a.re, b.re, acc.re);
+  acc.re = fma_(a.im, b.im, acc.re);
+  acc.im = fma_(-a.re, b.im, acc.im);
+  acc.im = fma_(-a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename R> OV_HD void cdotac(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma_(a.re, b.re, acc.re);
+  acc.re = fma_(a.im, b.im, acc.re);
+  acc.im = fma_(a.re, b.im, acc.im);
+  acc.im = fma_(-a.im, b.re, acc.im);
 }
 template <typename R> OV_HD cplx<R> czero() { return mk<R>(0, 0); }
 
@@ -194,10 +212,7 @@ template <typename R> struct SiteDot;
 template <> struct SiteDot<double> {
   zd acc;
   OV_HD void zero() { acc = mk(0.0, 0.0); }
-  OV_HD void add(cplx<double> a, cplx<double> b) {
-    acc.re += a.re * b.re + a.im * b.im;
-    acc.im += a.re * b.im - a.im * b.re;
-  }
+  OV_HD void add(cplx<double> a, cplx<double> b) { cdotac(acc, a, b); }
   OV_HD zd value() const { return acc; }
 };
 template <> struct SiteDot<float> {

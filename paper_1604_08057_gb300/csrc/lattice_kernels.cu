@@ -279,16 +279,16 @@ __global__ void __launch_bounds__(BS) k_tsl_update(Lat<R> L, int j, int finalize
     load_spinor(L.q + src * L.vs, V, x, s);
     load_spinor(L.basis_v(src, j), V, x, t);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) r.c[c] = r.c[c] - al * t.c[c];
+    for (int c = 0; c < 12; ++c) cmsub(r.c[c], al, t.c[c]);
     load_spinor(L.basis_w(src, j), V, x, t);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) s.c[c] = s.c[c] - alc * t.c[c];
+    for (int c = 0; c < 12; ++c) cmsub(s.c[c], alc, t.c[c]);
     if (j > 0) {
       const cplx<R> bt = cast<R>(L.beta[(int64_t)src * L.k + j]);
       const R dl = (R)L.delta[(int64_t)src * L.k + j];
       load_spinor(L.basis_v(src, j - 1), V, x, t);
 #pragma unroll
-      for (int c = 0; c < 12; ++c) r.c[c] = r.c[c] - bt * t.c[c];
+      for (int c = 0; c < 12; ++c) cmsub(r.c[c], bt, t.c[c]);
       load_spinor(L.basis_w(src, j - 1), V, x, t);
 #pragma unroll
       for (int c = 0; c < 12; ++c) s.c[c] = s.c[c] - dl * t.c[c];
