@@ -47,6 +47,7 @@ extern "C" {
 #define OV_ERR_SIGN_ILLPOSED  -4  /* k x k Newton sign did not converge or hit a singular iterate */
 #define OV_ERR_CUDA           -5  /* a CUDA runtime call failed */
 #define OV_ERR_NONFINITE      -6  /* a NaN or Inf appeared in a recurrence coefficient */
+#define OV_ERR_SCRATCH_LIMIT  -7  /* the problem does not fit the fixed scratch of ov_apply_H_noalloc */
 
 /* Precision of lattice vectors, links and stencil arithmetic.
  * OV_FP64 : everything in FP64.
@@ -138,6 +139,28 @@ int ov_profile_enable(ov_context *ctx, int32_t enable);
 int ov_profile_read(ov_context *ctx, int32_t kind, int64_t *launches, double *ms, int32_t reset);
 /* Number of kernels this context has launched since it was created. */
 int64_t ov_launch_count(ov_context *ctx);
+
+/* Allocation-free H(mu) psi.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory when they apply the
+ * operator (a framework allocator that already owns the device memory, an
+ * inner loop that cannot afford the device synchronisation of cudaMalloc and
+ * cudaFree, a plug-in whose host forbids allocations after start-up).
+ * Same operator, arguments and layouts as ov_apply_H, always in FP64, but
+ * without a context: the work is enqueued on `stream` (a cudaStream_t, NULL =
+ * legacy default stream) and the call returns without waiting for it.
+ * Workspace: one file-scope device array of OV_NOALLOC_SCRATCH_BYTES, which
+ * every GPU that loads the library holds until the process exits; the call
+ * allocates and frees nothing.  It needs (72 V + 2 nsrc ceil64(24 V)) * 8
+ * bytes (ceil64 rounds up to a multiple of 64) and returns
+ * OV_ERR_SCRATCH_LIMIT when that exceeds the array.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  All calls share
+ * the one array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads on one device) race and corrupt each other's
+ * results; calls ordered on one stream are safe. */
+#define OV_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ov_apply_H_noalloc(const int32_t dims[4], const void *U, double mu, double m_w, int32_t nsrc,
+                       const void *in, void *out, int32_t dagger, void *stream);
 
 /* Human-readable text for a status code (static storage). */
 const char *ov_strerror(int status);

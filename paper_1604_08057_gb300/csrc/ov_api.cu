@@ -683,6 +683,7 @@ const char* ov_strerror(int s) {
     case OV_ERR_SIGN_ILLPOSED: return "k x k Newton sign iteration failed (singular or non-convergent)";
     case OV_ERR_CUDA: return "CUDA runtime error";
     case OV_ERR_NONFINITE: return "non-finite recurrence coefficient";
+    case OV_ERR_SCRATCH_LIMIT: return "problem too large for the fixed 32 MiB scratch of ov_apply_H_noalloc";
     default: return "unknown status";
   }
 }
