@@ -6,7 +6,7 @@ U = expm(i 0.2 A), mu = 0.3, m_w = -2, one Gaussian source, k = 800, one
 Gaussian cotangent; FP64 throughout (at this point the k-step map amplifies
 rounding by ~1e6 and FP32 basis vectors break the recurrence down; the
 mixed-precision path is reported separately), pair-periodic
-re-biorthogonalisation every 20 steps with 2 Gram-Schmidt passes.  One step = one ov_tsl_sign_vjp call (forward recurrence, sign,
+re-biorthogonalisation every 20 steps with one Gram-Schmidt pass.  One step = one ov_tsl_sign_vjp call (forward recurrence, sign,
 x = V y, Frechet adjoint, reverse sweep, force, dmu) on inputs resident in
 HBM; the Krylov bases (5.9 GB) exceed the 129 MB L2, so no flush is needed.
 
@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--k", type=int, default=0, help="override the workload's k")
     ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
     ap.add_argument("--rebiorth", type=int, default=20)
-    ap.add_argument("--passes", type=int, default=2)
+    ap.add_argument("--passes", type=int, default=1)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
     ap.add_argument("--cpu-k", type=int, default=4, help="Lanczos steps of the oracle sample")
     ap.add_argument("--leg", default="all", choices=["all", "stencil"],

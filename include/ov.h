@@ -71,8 +71,10 @@ typedef struct {
   int32_t newton_iters_adj; /* Newton iterations of the Frechet adjoint (VJP only) */
   int32_t reserved;
   double  min_abs_re_ritz;  /* unused (0) unless computed by the caller */
-  double  t_ms[8];          /* phase times: 0 forward Krylov, 1 k x k sign, 2 combine,
-                               3 Frechet adjoint, 4 reverse sweep, 5 force/dmu, 6-7 unused */
+  double  t_ms[8];          /* phase times (ms).  ov_tsl_sign: 0 forward Krylov, 1 k x k sign,
+                               2 combine.  ov_tsl_sign_vjp: 0 forward Krylov, 1 g_y = V^dag xbar,
+                               2 k x k sign and Frechet adjoint, 3 combine, 4 reverse sweep and
+                               force.  Others unused. */
 } ov_tsl_info;
 
 typedef struct ov_context ov_context;

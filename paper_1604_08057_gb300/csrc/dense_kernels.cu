@@ -153,18 +153,24 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_step(const zd* __restrict__ x
   const int r0 = blockIdx.x * GJ_ROWS;
   const int nrow = min(GJ_ROWS, k - r0);
   Cand nc{-1.0, 0x7fffffff};
-  for (int e = threadIdx.x; e < nrow * k; e += blockDim.x) {
-    const int i = r0 + e / k, j = e % k;
-    const int64_t o = (int64_t)i * k + j;
-    zd v;
-    if (i == p) {
-      v = prow[j];
-    } else {
-      const zd f = xin[(int64_t)i * k + kk];
-      v = (j == kk) ? -(f * prow[kk]) : xin[o] - f * prow[j];
+  for (int r = 0; r < nrow; ++r) {
+    const int i = r0 + r;
+    const zd f = xin[(int64_t)i * k + kk];
+    const zd* xr = xin + (int64_t)i * k;
+    zd* yr = xout + (int64_t)i * k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      zd v;
+      if (i == p) {
+        v = prow[j];
+      } else if (j == kk) {
+        v = -(f * prow[kk]);
+      } else {
+        v = xr[j];
+        cmsub(v, f, prow[j]);
+      }
+      yr[j] = v;
+      if (j == kk + 1 && i != p && !used[i]) nc = cand_max(nc, Cand{norm2(v), i});
     }
-    xout[o] = v;
-    if (j == kk + 1 && i != p && !used[i]) nc = cand_max(nc, Cand{norm2(v), i});
   }
   nc = block_cand_max(nc, sh);
   if (threadIdx.x == 0) cout[blockIdx.x] = nc;
@@ -189,7 +195,7 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int*
   const unsigned nb = nblk(k, GJ_ROWS);
   const size_t smem = (size_t)k * sizeof(zd);
   static bool attr = false;
-  if (!attr) {
+  if (smem > 48 * 1024 && !attr) {
     cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr = true;
   }
@@ -211,8 +217,9 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int*
 // C = A B, complex FP64, 32 x 32 tiles, 2 x 2 outputs per thread
 // ---------------------------------------------------------------------------
 constexpr int GT = 32, GK = 16;
+// C = op(A) op(B); op = identity (0) or conjugate transpose (1)
 __global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, const zd* __restrict__ b,
-                                              zd* __restrict__ c, int k) {
+                                              zd* __restrict__ c, int k, int ha, int hb) {
   __shared__ zd as[GT][GK + 1];
   __shared__ zd bs[GK][GT + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -222,12 +229,17 @@ __global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, const zd
     for (int q = 0; q < 2; ++q) acc[r][q] = mk(0.0, 0.0);
   for (int k0 = 0; k0 < k; k0 += GK) {
     for (int t = threadIdx.x; t < GT * GK; t += 256) {
-      const int r = t / GK, q = t % GK;
+      // op(A)[gi][gk]: row-major read along gk, or (conjugated) along gi for the adjoint
+      const int r = ha ? t % GT : t / GK, q = ha ? t / GT : t % GK;
       const int gi = row0 + r, gk = k0 + q;
-      as[r][q] = (gi < k && gk < k) ? a[(int64_t)gi * k + gk] : mk(0.0, 0.0);
-      const int r2 = t / GT, q2 = t % GT;
+      zd av = mk(0.0, 0.0);
+      if (gi < k && gk < k) av = ha ? conj(a[(int64_t)gk * k + gi]) : a[(int64_t)gi * k + gk];
+      as[r][q] = av;
+      const int r2 = hb ? t % GK : t / GT, q2 = hb ? t / GK : t % GT;
       const int gk2 = k0 + r2, gj = col0 + q2;
-      bs[r2][q2] = (gk2 < k && gj < k) ? b[(int64_t)gk2 * k + gj] : mk(0.0, 0.0);
+      zd bv = mk(0.0, 0.0);
+      if (gk2 < k && gj < k) bv = hb ? conj(b[(int64_t)gj * k + gk2]) : b[(int64_t)gk2 * k + gj];
+      bs[r2][q2] = bv;
     }
     __syncthreads();
 #pragma unroll
@@ -248,7 +260,10 @@ __global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, const zd
     }
 }
 void dense_gemm(const zd* a, const zd* b, zd* c, int k, cudaStream_t st) {
-  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, b, c, k);
+  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, b, c, k, 0, 0);
+}
+void dense_gemm_op(const zd* a, int ha, const zd* b, int hb, zd* c, int k, cudaStream_t st) {
+  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, b, c, k, ha, hb);
 }
 
 // Xn = 0.5 (g X + s Xi / g);  stats += w * (|Xn - X|^2, |Xn|^2)

@@ -112,6 +112,8 @@ struct Cand2 { double v; int i; int pad; };
 void dense_inverse(const zd* A, zd* Ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, Cand2* cand,
                    double* logdet, int* err, cudaStream_t st);
 void dense_gemm(const zd* A, const zd* B, zd* C, int k, cudaStream_t st);   // C = A B
+// C = op(A) op(B), op = conjugate transpose when the flag is set
+void dense_gemm_op(const zd* A, int hA, const zd* B, int hB, zd* C, int k, cudaStream_t st);
 // Xn = 0.5 (g X + s Xi / g) with g = |det|^(-1/k) from *logdet when scaling, else 1;
 // stats[0] += w |Xn - X|^2, stats[1] += w |Xn|^2 (deterministic order)
 void dense_newton_combine(const zd* X, const zd* Xi, zd* Xn, int k, const double* logdet, int scaling,

@@ -17,7 +17,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, NBUF
 };
 
 struct Status {
@@ -224,7 +224,16 @@ void forward_krylov(ov_context* c, Lat<R>& L) {
 // the iteration runs on [[A, E], [0, A]] (e[0] holds E) and E converges to the
 // upper-right block.  Returns the iteration count (or -1 on a non-finite step)
 // and the index of the buffer holding the result in *which.
-int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which) {
+struct NewtonRecord {
+  zd* inv = nullptr;        // NREC slots of k x k inverses
+  double* logdet = nullptr; // NREC log|det| values
+  std::vector<int> scaling; // scaling flag of each recorded iteration
+  int cap = 0;
+  bool ok = true;           // false when the iteration outgrew the record
+};
+constexpr int NREC = 48;
+
+int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, NewtonRecord* rec = nullptr) {
   const int64_t n = (int64_t)k * k;
   zd* ai = wsT<zd>(c, B_XI, n);
   zd* t1 = e ? wsT<zd>(c, B_TMP1, n) : nullptr;
@@ -246,6 +255,16 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which) {
     run(c, OV_KIND_DENSE, (int64_t)k + 3, [&] {
       dense_inverse(a[cur], ai, w0, w1, k, ipiv, used, cand, dstat + 2, err_dev, c->st);
     });
+    if (rec) {
+      const int slot = it - 1;
+      if (slot < rec->cap) {
+        run(c, OV_KIND_DENSE, 1, [&] { dense_copy(ai, rec->inv + (int64_t)slot * n, n, c->st); });
+        CK(cudaMemcpyAsync(rec->logdet + slot, dstat + 2, sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+        rec->scaling.push_back(scaling ? 1 : 0);
+      } else {
+        rec->ok = false;
+      }
+    }
     if (e) {
       run(c, OV_KIND_DENSE_GEMM, 2, [&] {
         dense_gemm(ai, e[cur], t1, k, c->st);
@@ -372,11 +391,6 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   if (info) info->k_reached = kr;
   if (st != OV_OK) return st;
   zd* y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
-  int iters = 0;
-  st = sign_all(c, L, hsc, y, &iters);
-  if (st != OV_OK) return st;
-  CK(cudaEventRecord(c->ev[2], c->st));
-  if (x) run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
   // g_y = V^dag xbar
   R* xb = wsT<R>(c, B_XBAR, nsrc * vs);
   run(c, OV_KIND_LAYOUT, 1, [&] { pack_spinors<R>(static_cast<const double*>(xbar), xb, nsrc, V, vs, c->st); });
@@ -385,33 +399,103 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   zd* cpart = wsT<zd>(c, B_CPART, (int64_t)nsrc * 2 * k * nsb);
   run(c, OV_KIND_COMBINE, 2, [&] { basis_dots(L, k, xb, vs, gy, cpart, c->st); });
   launch_check();
-  CK(cudaEventRecord(c->ev[3], c->st));
-  // G_T = L_sgn(T^dag, beta0 g_y e_1^T) from the Theorem-1 block matrix
+  CK(cudaEventRecord(c->ev[2], c->st));
+  // per source: y = beta0 sgn(T) e1 by Newton, recording the inverses; then
+  // G_T = L_sgn(T^dag, beta0 g_y e1^T).  The Theorem-1 block iteration on
+  // [[T^dag, G], [0, T^dag]] has diagonal iterates X_i^dag (X_i: the iterates on
+  // T, same scalings), so its upper-right block follows from the recorded X_i^{-1}:
+  //   E <- (g_i E - X_i^{-dag} E X_i^{-dag} / g_i) / 2,
+  // continued with X^{-1} = sgn(T) once the diagonal has converged.
   zd* gaT = wsT<zd>(c, B_GA, (int64_t)nsrc * k);
   zd* gbT = wsT<zd>(c, B_GB, (int64_t)nsrc * k);
   double* gdT = wsT<double>(c, B_GD, (int64_t)nsrc * k);
   int* derr = wsT<int>(c, B_DERR, 1, true);
-  int iters_adj = 0;
+  int iters = 0, iters_adj = 0;
   {
     const int64_t n = (int64_t)k * k;
-    zd* t = wsT<zd>(c, B_T, n);
     zd* a[2] = {wsT<zd>(c, B_X, n), wsT<zd>(c, B_XN, n)};
     zd* e[2] = {wsT<zd>(c, B_E, n), wsT<zd>(c, B_EN, n)};
+    zd* t = wsT<zd>(c, B_T, n);
+    zd* t1 = wsT<zd>(c, B_TMP1, n);
+    zd* t2 = wsT<zd>(c, B_TMP2, n);
+    double* dstat = wsT<double>(c, B_DSTAT, 4);
+    zd* dpart = wsT<zd>(c, B_DPART, (n + 255) / 256 + 64);
+    unsigned* dcnt = wsT<unsigned>(c, B_DCNT, 4);
+    NewtonRecord rec;
+    rec.inv = wsT<zd>(c, B_REC, (int64_t)NREC * n);
+    rec.logdet = wsT<double>(c, B_RECLD, NREC);
+    rec.cap = NREC;
     for (int src = 0; src < nsrc; ++src) {
-      run(c, OV_KIND_DENSE, 5, [&] {
-        dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, t,
+      rec.scaling.clear();
+      rec.ok = true;
+      run(c, OV_KIND_DENSE, 2, [&] {
+        dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, a[0],
                       c->st);
-        dense_adjoint(t, a[0], k, c->st);
-        dense_set_column0(e[0], gy + (int64_t)src * 2 * k, 2, hsc[src].beta0, k, c->st);
       });
       int which = 0;
-      const int it = newton(c, a, e, k, derr, &which);
+      const int it = newton(c, a, nullptr, k, derr, &which, &rec);
       if (it < 0) return OV_ERR_SIGN_ILLPOSED;
-      if (it > iters_adj) iters_adj = it;
-      run(c, OV_KIND_DENSE, 1, [&] {
-        dense_extract_tri(e[which], k, gaT + (int64_t)src * k, gbT + (int64_t)src * k, gdT + (int64_t)src * k,
-                          c->st);
-      });
+      if (it > iters) iters = it;
+      zd* f = a[which];
+      run(c, OV_KIND_DENSE, 1, [&] { dense_extract_y(f, hsc[src].beta0, k, y + (int64_t)src * k, c->st); });
+      if (rec.ok) {
+        int ce = 0;
+        run(c, OV_KIND_DENSE, 2,
+            [&] { dense_set_column0(e[0], gy + (int64_t)src * 2 * k, 2, hsc[src].beta0, k, c->st); });
+        for (int i = 0; i < it; ++i) {
+          const zd* yi = rec.inv + (int64_t)i * n;
+          run(c, OV_KIND_DENSE_GEMM, 2, [&] {
+            dense_gemm_op(yi, 1, e[ce], 0, t1, k, c->st);
+            dense_gemm_op(t1, 0, yi, 1, t2, k, c->st);
+          });
+          run(c, OV_KIND_DENSE, 1, [&] {
+            dense_newton_combine(e[ce], t2, e[1 - ce], k, rec.logdet + i, rec.scaling[i], -1.0, 1.0, dstat, dpart,
+                                 dcnt, c->st);
+          });
+          ce = 1 - ce;
+        }
+        double prev = INFINITY;
+        int extra = 0;
+        for (extra = 1; extra <= 4; ++extra) {
+          CK(cudaMemsetAsync(dstat, 0, 3 * sizeof(double), c->st));
+          run(c, OV_KIND_DENSE_GEMM, 2, [&] {
+            dense_gemm_op(f, 1, e[ce], 0, t1, k, c->st);
+            dense_gemm_op(t1, 0, f, 1, t2, k, c->st);
+          });
+          run(c, OV_KIND_DENSE, 1, [&] {
+            dense_newton_combine(e[ce], t2, e[1 - ce], k, dstat + 2, 0, -1.0, 1.0, dstat, dpart, dcnt, c->st);
+          });
+          ce = 1 - ce;
+          double hs[2];
+          CK(cudaMemcpyAsync(hs, dstat, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+          CK(cudaStreamSynchronize(c->st));
+          const double step = std::sqrt(hs[0] / hs[1]);
+          if (!std::isfinite(step)) return OV_ERR_SIGN_ILLPOSED;
+          if (step <= 1e-14 || step >= 0.5 * prev) break;
+          prev = step;
+        }
+        if (it + extra > iters_adj) iters_adj = it + extra;
+        run(c, OV_KIND_DENSE, 1, [&] {
+          dense_extract_tri(e[ce], k, gaT + (int64_t)src * k, gbT + (int64_t)src * k, gdT + (int64_t)src * k,
+                            c->st);
+        });
+      } else {
+        // the sign needed more iterations than the record holds: run the block iteration itself
+        run(c, OV_KIND_DENSE, 5, [&] {
+          dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, t,
+                        c->st);
+          dense_adjoint(t, a[0], k, c->st);
+          dense_set_column0(e[0], gy + (int64_t)src * 2 * k, 2, hsc[src].beta0, k, c->st);
+        });
+        int wb = 0;
+        const int itb = newton(c, a, e, k, derr, &wb);
+        if (itb < 0) return OV_ERR_SIGN_ILLPOSED;
+        if (itb > iters_adj) iters_adj = itb;
+        run(c, OV_KIND_DENSE, 1, [&] {
+          dense_extract_tri(e[wb], k, gaT + (int64_t)src * k, gbT + (int64_t)src * k, gdT + (int64_t)src * k,
+                            c->st);
+        });
+      }
     }
   }
   {
@@ -420,6 +504,8 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
     CK(cudaStreamSynchronize(c->st));
     if (herr) return OV_ERR_SIGN_ILLPOSED;
   }
+  CK(cudaEventRecord(c->ev[3], c->st));
+  if (x) run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
   CK(cudaEventRecord(c->ev[4], c->st));
   // reverse sweep
   std::vector<int> reb;

@@ -77,16 +77,17 @@ def test_apply_h_single_source_shape():
 # ---------------------------------------------------------------------------
 # forward TSL
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("dims,mu,m_w,k,reb,tol", [
-    ((3, 3, 3, 3), 0.3, -1.0, 60, 1, 1e-11),
-    ((3, 5, 2, 4), 0.4, -1.0, 45, 10, 1e-11),        # ragged lattice, pair-periodic
-    ((4, 4, 4, 4), 0.3, -2.0, 200, 1, 1e-9),         # the 4x4^3 workload: floor 1e-10
+@pytest.mark.parametrize("dims,mu,m_w,k,reb,passes,tol", [
+    ((3, 3, 3, 3), 0.3, -1.0, 60, 1, 2, 1e-11),
+    ((3, 5, 2, 4), 0.4, -1.0, 45, 10, 2, 1e-11),     # ragged lattice, pair-periodic
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 1, 2, 1e-9),      # the 4x4^3 workload: floor 1e-10
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 20, 1, 1e-9),     # benchmark schedule: P = 20, one pass
 ])
-def test_tsl_forward_fp64(dims, mu, m_w, k, reb, tol):
+def test_tsl_forward_fp64(dims, mu, m_w, k, reb, passes, tol):
     u, b, _ = case(dims, 0.3, 3)
-    ref = oracle_fwd(dims, 0.3, 3, mu, m_w, k, reb)
-    x = binding.tsl_sign(T(u), mu, m_w, T(b[0]), k, rebiorth=reb).cpu().numpy()
-    a, bt, d = binding.tsl_coefficients(k, rebiorth=reb)
+    ref = oracle_fwd(dims, 0.3, 3, mu, m_w, k, reb, passes)
+    x = binding.tsl_sign(T(u), mu, m_w, T(b[0]), k, rebiorth=reb, passes=passes).cpu().numpy()
+    a, bt, d = binding.tsl_coefficients(k, rebiorth=reb, passes=passes)
     # the first coefficients agree to rounding before the map's amplification sets in
     assert np.abs(a[:10] - ref.alpha[:10]).max() <= 1e-12 * np.abs(ref.alpha[:10]).max()
     assert np.abs(d[1:10] - ref.delta[1:10]).max() <= 1e-12 * np.abs(ref.delta[1:10]).max()
@@ -118,18 +119,19 @@ def test_tsl_forward_mixed_precision():
 # ---------------------------------------------------------------------------
 # VJP
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("dims,mu,m_w,k,reb,tol", [
-    ((3, 3, 3, 3), 0.3, -1.0, 40, 1, 1e-9),
-    ((3, 5, 2, 4), 0.3, -1.0, 50, 10, 1e-8),
-    ((4, 4, 4, 4), 0.3, -2.0, 200, 1, 1e-6),         # the 4x4^3 workload: dU floor 9e-8
+@pytest.mark.parametrize("dims,mu,m_w,k,reb,passes,tol", [
+    ((3, 3, 3, 3), 0.3, -1.0, 40, 1, 2, 1e-9),
+    ((3, 5, 2, 4), 0.3, -1.0, 50, 10, 2, 1e-8),
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 1, 2, 1e-6),      # the 4x4^3 workload: dU floor 9e-8
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 20, 1, 5e-6),     # benchmark schedule: dU floor 7.4e-7
 ])
-def test_vjp_fp64(dims, mu, m_w, k, reb, tol):
+def test_vjp_fp64(dims, mu, m_w, k, reb, passes, tol):
     u, b, xbar = case(dims, 0.3, 3)
-    du_o, dmu_o = oracle_vjp(dims, 0.3, 3, mu, m_w, k, reb)
-    du, dmu, x = binding.tsl_sign_vjp(T(u), mu, m_w, T(b[0]), k, T(xbar[0]), rebiorth=reb)
+    du_o, dmu_o = oracle_vjp(dims, 0.3, 3, mu, m_w, k, reb, passes)
+    du, dmu, x = binding.tsl_sign_vjp(T(u), mu, m_w, T(b[0]), k, T(xbar[0]), rebiorth=reb, passes=passes)
     assert rel(du.cpu().numpy(), du_o) <= tol, rel(du.cpu().numpy(), du_o)
     assert abs(dmu - dmu_o) <= tol * max(1.0, abs(dmu_o)), (dmu, dmu_o)
-    ref = oracle_fwd(dims, 0.3, 3, mu, m_w, k, reb)
+    ref = oracle_fwd(dims, 0.3, 3, mu, m_w, k, reb, passes)
     assert rel(x.cpu().numpy(), ref.x) <= max(tol, 1e-11)
 
 
