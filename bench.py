@@ -169,6 +169,7 @@ def run_ours(args, rank, world, local_rank):
     V = wl.volume
     ut, bt, xt = (torch.tensor(a, device=dev) for a in (u, b, xbar))
     ctx = binding.context(args.precision, args.rebiorth, args.passes)
+    tune = binding.autotune(ut, wl.mu, wl.m_w, nsrc, args.precision, args.rebiorth, args.passes)
 
     def step():
         return binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, args.precision, args.rebiorth, args.passes,
@@ -253,7 +254,7 @@ def run_ours(args, rank, world, local_rank):
            "gpu_launches": launches // args.steps * args.steps, "kernels_ms_per_step": kernels_ms,
            "phase_ms": [round(t, 3) for t in info["t_ms"][:6]], "newton_iters": [info["newton_iters"],
                                                                                   info["newton_iters_adj"]],
-           "roofline": roofline, "clocks": clk}
+           "roofline": roofline, "clocks": clk, "autotune": tune}
 
     if not args.no_extras and rank == 0:
         out["e2e"] = e2e_leg(args, ut, bt, xt, wl, k)
@@ -326,6 +327,7 @@ def stencil_leg(args, ut, wl, hbm, peak_src, nsrc=32, reps=20):
                       generator=g)
     for prec, e in (("mixed", 4), ("fp64", 8)):
         ctx = binding.context(prec)
+        tune = binding.autotune(ut, wl.mu, wl.m_w, nsrc, prec)
         binding.apply_H(ut, wl.mu, wl.m_w, psi, precision=prec)
         torch.cuda.synchronize()
         binding.profile_enable(ctx, True)
@@ -339,7 +341,8 @@ def stencil_leg(args, ut, wl, hbm, peak_src, nsrc=32, reps=20):
         gbs = nbytes * n / (ms / 1e3) / 1e9
         flops = 1368 * V * nsrc * n / (ms / 1e3) / 1e12
         res[prec] = {"GB_s": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 3), "tflops": round(flops, 2),
-                     "us_per_launch": round(1e3 * ms / n, 2), "bytes_per_launch": nbytes}
+                     "us_per_launch": round(1e3 * ms / n, 2), "bytes_per_launch": nbytes,
+                     "variant": tune["apply_variant"], "variant_us": tune["apply_us"]}
     res.update({"nsrc": nsrc, "peak": hbm, "peak_source": peak_src, "unit": "GB/s",
                 "bytes": "algorithmic: spinor in + out per source, links once (480 B/site FP32 at 1 source)"})
     return res
@@ -347,12 +350,14 @@ def stencil_leg(args, ut, wl, hbm, peak_src, nsrc=32, reps=20):
 
 def mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar):
     """The mixed-precision path: at the workload point, and at m_w = -1 where the
-    k-step map is well conditioned (timed against the FP64 path there)."""
+    k-step map is well conditioned (timed against the FP64 path there).  FP32
+    bases need two Gram-Schmidt passes (one pass breaks down at m_w = -1)."""
     import torch
     from paper_1604_08057_gb300 import binding
-    res = {}
+    res = {"gs_passes": 2}
+    passes = 2
     try:
-        binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, "mixed", args.rebiorth, args.passes)
+        binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, "mixed", args.rebiorth, passes)
         res["workload_point"] = "completed"
     except binding.OVError as exc:
         res["workload_point"] = f"status {exc.status}: {exc}"
@@ -360,12 +365,12 @@ def mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar):
     out = {}
     for prec in ("fp64", "mixed"):
         try:
-            binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, args.rebiorth, args.passes)
+            binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, args.rebiorth, passes)
             torch.cuda.synchronize()
             t0 = torch.cuda.Event(enable_timing=True)
             t1 = torch.cuda.Event(enable_timing=True)
             t0.record()
-            du, dmu, x = binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, args.rebiorth, args.passes)
+            du, dmu, x = binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, args.rebiorth, passes)
             t1.record()
             torch.cuda.synchronize()
             out[prec] = (t0.elapsed_time(t1) / 1e3, du, dmu, x)

@@ -111,6 +111,27 @@ int ov_tsl_sign_vjp(ov_context *ctx, const int32_t dims[4], const void *U, doubl
                     double m_w, int32_t nsrc, const void *b, int32_t k, const void *xbar,
                     void *x, void *dU, double *dmu, ov_tsl_info *info);
 
+/* Launch-shape autotuner.  Times every compiled variant of the two stencil
+ * kernels -- ov_apply_H (sources per thread x threads per block) and the
+ * TSL step's H/H^dagger pair (both products sharing each link load in one
+ * thread, or computed one after the other, x threads per block) -- on this
+ * lattice, nsrc sources and the context's precision, and keeps the fastest
+ * of each in the context for later calls.  U is as in ov_apply_H; the
+ * spinor data used for timing is internal scratch.  rep may be NULL. */
+typedef struct {
+  int32_t apply_variant;    /* chosen variant of the ov_apply_H stencil */
+  int32_t pair_variant;     /* chosen variant of the TSL stencil pair */
+  int32_t n_apply, n_pair;  /* number of variants timed */
+  float apply_us[16];       /* device microseconds per launch, per variant */
+  float pair_us[16];
+} ov_tune_report;
+int ov_autotune(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                int32_t nsrc, ov_tune_report *rep);
+/* Select the stencil variants by number for the context's precision (0 is
+ * the default; out-of-range numbers are rejected).  For tests and for
+ * reusing a tuning result. */
+int ov_set_stencil_variants(ov_context *ctx, int32_t apply_variant, int32_t pair_variant);
+
 /* Recurrence coefficients of source `src` from the last ov_tsl_sign or
  * ov_tsl_sign_vjp call on this context (k must equal that call's k), copied
  * to HOST arrays: alpha[2k] and beta[2k] interleaved complex, delta[k].

@@ -37,6 +37,12 @@ class Options(ctypes.Structure):
                 ("passes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("apply_variant", ctypes.c_int32), ("pair_variant", ctypes.c_int32),
+                ("n_apply", ctypes.c_int32), ("n_pair", ctypes.c_int32),
+                ("apply_us", ctypes.c_float * 16), ("pair_us", ctypes.c_float * 16)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("k_reached", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
                 ("newton_iters_adj", ctypes.c_int32), ("reserved", ctypes.c_int32),
@@ -49,7 +55,8 @@ class Info(ctypes.Structure):
 
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
-           "ov_launch_count", "ov_apply_H_noalloc", "ov_strerror"]
+           "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
+           "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -75,6 +82,8 @@ def load(path: str = LIB_PATH):
     lib.ov_tsl_coefficients.argtypes = [P, I32, I32, P, P, P]
     lib.ov_profile_enable.argtypes = [P, I32]
     lib.ov_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D), I32]
+    lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
+    lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
     lib.ov_launch_count.argtypes = [P]
     lib.ov_launch_count.restype = ctypes.c_int64
     lib.ov_strerror.argtypes = [ctypes.c_int]
@@ -214,3 +223,22 @@ def profile_read(ctx, reset=False) -> dict:
 
 def launch_count(ctx) -> int:
     return int(load().ov_launch_count(ctx))
+
+
+def autotune(u, mu, m_w, nsrc=1, precision="fp64", rebiorth=1, passes=2) -> dict:
+    """Time the stencil launch variants on this lattice and keep the fastest in the context."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    rep = TuneReport()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_autotune(ctx, dims, _ptr(u), float(mu), float(m_w), int(nsrc), ctypes.byref(rep)),
+           "ov_autotune")
+    return {"apply_variant": rep.apply_variant, "pair_variant": rep.pair_variant,
+            "apply_us": [round(v, 2) for v in rep.apply_us[:rep.n_apply]],
+            "pair_us": [round(v, 2) for v in rep.pair_us[:rep.n_pair]]}
+
+
+def set_stencil_variants(apply_variant, pair_variant, precision="fp64", rebiorth=1, passes=2):
+    ctx = context(precision, rebiorth, passes)
+    _check(load().ov_set_stencil_variants(ctx, int(apply_variant), int(pair_variant)), "ov_set_stencil_variants")

@@ -72,10 +72,14 @@ struct Rev {
 template <typename R> void pack_spinors(const double* src_aos, R* dst, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
 template <typename R> void unpack_spinors(const R* src, double* dst_aos, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
 template <typename R> void pack_links(const double* src_aos, R* dst, int64_t V, cudaStream_t st);
-template <typename R> void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st);
+// launch variants of the two stencil kernels (chosen by the autotuner; 0 = default)
+int apply_h_variants();
+int tsl_stencil_variants();
+template <typename R> void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st,
+                                   int variant = 0);
 
 template <typename R> void tsl_init(const Lat<R>& L, cudaStream_t st);
-template <typename R> void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st);
+template <typename R> void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st, int variant = 0);
 template <typename R> void tsl_update(const Lat<R>& L, int j, bool finalize, cudaStream_t st);
 // projection of (r, s) against bases (A: dots with `a` vector, B: dots with `b` vector).
 // mode 0 (forward):  c = W^dag r, d = V^dag s;  r -= V c, s -= W d

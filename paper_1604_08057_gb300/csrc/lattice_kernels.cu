@@ -83,9 +83,9 @@ void unpack_force(const double* f, double* du, int64_t V, cudaStream_t st) {
 // H and H^dagger
 // ---------------------------------------------------------------------------
 // NS sources per thread share every link load; blockIdx.y indexes groups of NS sources
-template <typename R, int NS>
-__global__ void __launch_bounds__(BS) k_apply_h(Lat<R> L, const R* __restrict__ in, R* __restrict__ out,
-                                                int dagger, int nsrc) {
+template <typename R, int NS, int BSZ>
+__global__ void __launch_bounds__(BSZ) k_apply_h(Lat<R> L, const R* __restrict__ in, R* __restrict__ out,
+                                                 int dagger, int nsrc) {
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int s0 = blockIdx.y * NS;
   if (x >= L.g.V) return;
@@ -104,14 +104,32 @@ __global__ void __launch_bounds__(BS) k_apply_h(Lat<R> L, const R* __restrict__ 
   for (int i = 0; i < NS; ++i)
     if (s0 + i < nsrc) store_spinor(out + (int64_t)(s0 + i) * L.vs, L.g.V, x, o[i]);
 }
-template <typename R>
-void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st) {
-  constexpr int NS = sizeof(R) == 4 ? 4 : 2;
-  if (L.nsrc == 1)
-    k_apply_h<R, 1><<<dim3(nblocks(L.g.V, BS), 1), BS, 0, st>>>(L, in, out, dagger, 1);
+
+// launch variants (sources per thread, threads per block); 0 is the default
+static const int kApplyVariants[][2] = {{1, 128}, {1, 64}, {1, 256}, {2, 64}, {2, 128}, {4, 64}, {4, 128}};
+int apply_h_variants() { return (int)(sizeof(kApplyVariants) / sizeof(kApplyVariants[0])); }
+
+template <typename R, int NS, int BSZ>
+static void launch_apply(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st) {
+  const int ns = L.nsrc < NS ? 1 : NS;   // a lone source never needs the wider variant
+  if (ns == 1)
+    k_apply_h<R, 1, BSZ><<<dim3(nblocks(L.g.V, BSZ), L.nsrc), BSZ, 0, st>>>(L, in, out, dagger, L.nsrc);
   else
-    k_apply_h<R, NS><<<dim3(nblocks(L.g.V, BS), (L.nsrc + NS - 1) / NS), BS, 0, st>>>(L, in, out, dagger,
-                                                                                       L.nsrc);
+    k_apply_h<R, NS, BSZ><<<dim3(nblocks(L.g.V, BSZ), (L.nsrc + NS - 1) / NS), BSZ, 0, st>>>(L, in, out, dagger,
+                                                                                           L.nsrc);
+}
+
+template <typename R>
+void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st, int variant) {
+  switch (variant) {
+    case 1: launch_apply<R, 1, 64>(L, in, out, dagger, st); break;
+    case 2: launch_apply<R, 1, 256>(L, in, out, dagger, st); break;
+    case 3: launch_apply<R, 2, 64>(L, in, out, dagger, st); break;
+    case 4: launch_apply<R, 2, 128>(L, in, out, dagger, st); break;
+    case 5: launch_apply<R, 4, 64>(L, in, out, dagger, st); break;
+    case 6: launch_apply<R, 4, 128>(L, in, out, dagger, st); break;
+    default: launch_apply<R, 1, 128>(L, in, out, dagger, st); break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -204,8 +222,8 @@ void tsl_init(const Lat<R>& L, cudaStream_t st) {
 // TSL step j: v_j = sv r_{j-1}, w_j = sw s_{j-1} stored in the bases;
 // p = H v_j, q = H^dag w_j; alpha_j = w_j^dag p.
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(BS) k_tsl_stencil(Lat<R> L, int j, int need_q) {
+template <typename R, int PAIR, int BSZ>
+__global__ void __launch_bounds__(BSZ) k_tsl_stencil(Lat<R> L, int j, int need_q) {
   __shared__ zd scratch[32];
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int src = blockIdx.y;
@@ -224,7 +242,7 @@ __global__ void __launch_bounds__(BS) k_tsl_stencil(Lat<R> L, int j, int need_q)
 #pragma unroll
     for (int c = 0; c < 12; ++c) w.c[c] = sw * w.c[c];
     store_spinor(L.basis_w(src, j), V, x, w);
-    if (need_q) {
+    if (need_q && PAIR) {
       // H r and H^dag s share every link load
       const FieldLoad<R> ld[2] = {FieldLoad<R>{rp, V}, FieldLoad<R>{sp, V}};
       const R ft[2] = {L.ef, L.efinv}, fti[2] = {L.efinv, L.ef};
@@ -243,6 +261,12 @@ __global__ void __launch_bounds__(BS) k_tsl_stencil(Lat<R> L, int j, int need_q)
       for (int c = 0; c < 12; ++c) o.c[c] = sv * o.c[c];
       store_spinor(L.p + src * L.vs, V, x, o);
       v[0] = spinor_dot(w, o);
+      if (need_q) {
+        h_site(sp, L.u, L.g, x, L.kappa, L.efinv, L.ef, o);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) o.c[c] = sw * o.c[c];
+        store_spinor(L.q + src * L.vs, V, x, o);
+      }
     }
   }
   block_sum<1>(v, scratch);
@@ -258,9 +282,19 @@ __global__ void __launch_bounds__(BS) k_tsl_stencil(Lat<R> L, int j, int need_q)
     }
   }
 }
+static const int kPairVariants[][2] = {{1, 128}, {1, 64}, {0, 128}, {0, 64}, {0, 256}};
+int tsl_stencil_variants() { return (int)(sizeof(kPairVariants) / sizeof(kPairVariants[0])); }
+
 template <typename R>
-void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st) {
-  k_tsl_stencil<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, j, need_q ? 1 : 0);
+void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st, int variant) {
+  const int q = need_q ? 1 : 0;
+  switch (variant) {
+    case 1: k_tsl_stencil<R, 1, 64><<<dim3(nblocks(L.g.V, 64), L.nsrc), 64, 0, st>>>(L, j, q); break;
+    case 2: k_tsl_stencil<R, 0, 128><<<dim3(nblocks(L.g.V, 128), L.nsrc), 128, 0, st>>>(L, j, q); break;
+    case 3: k_tsl_stencil<R, 0, 64><<<dim3(nblocks(L.g.V, 64), L.nsrc), 64, 0, st>>>(L, j, q); break;
+    case 4: k_tsl_stencil<R, 0, 256><<<dim3(nblocks(L.g.V, 256), L.nsrc), 256, 0, st>>>(L, j, q); break;
+    default: k_tsl_stencil<R, 1, 128><<<dim3(nblocks(L.g.V, 128), L.nsrc), 128, 0, st>>>(L, j, q); break;
+  }
 }
 
 // r = p - alpha_j v_j - beta_j v_{j-1};  s = q - conj(alpha_j) w_j - delta_j w_{j-1}
@@ -939,9 +973,9 @@ void force_flush(const Lat<R>& L, const Rev<R>& B, const int* /*unused*/, int nt
   template void pack_spinors<R>(const double*, R*, int, int64_t, int64_t, cudaStream_t);                 \
   template void unpack_spinors<R>(const R*, double*, int, int64_t, int64_t, cudaStream_t);               \
   template void pack_links<R>(const double*, R*, int64_t, cudaStream_t);                                 \
-  template void apply_h<R>(const Lat<R>&, const R*, R*, int, cudaStream_t);                              \
+  template void apply_h<R>(const Lat<R>&, const R*, R*, int, cudaStream_t, int);                         \
   template void tsl_init<R>(const Lat<R>&, cudaStream_t);                                                \
-  template void tsl_stencil<R>(const Lat<R>&, int, bool, cudaStream_t);                                  \
+  template void tsl_stencil<R>(const Lat<R>&, int, bool, cudaStream_t, int);                             \
   template void tsl_update<R>(const Lat<R>&, int, bool, cudaStream_t);                                   \
   template void proj_dots<R>(const Lat<R>&, int, int, const R*, const R*, int64_t, zd*, zd*, cudaStream_t); \
   template void proj_update<R>(const Lat<R>&, int, int, R*, R*, int64_t, const zd*, bool, cudaStream_t);   \

@@ -66,6 +66,8 @@ struct ov_context {
   cudaEvent_t ev[8] = {};
   Prof* prof = nullptr;
   int64_t launches = 0;
+  int tuned_apply[2] = {0, 0};  // per precision (OV_FP64, OV_MIXED)
+  int tuned_pair[2] = {0, 0};
 };
 
 namespace {
@@ -204,7 +206,7 @@ void forward_krylov(ov_context* c, Lat<R>& L) {
   zd* cpart = wsT<zd>(c, B_CPART, (int64_t)L.nsrc * 2 * k * nsb);
   run(c, OV_KIND_UPDATE, 1, [&] { tsl_init(L, c->st); });
   for (int j = 0; j < k; ++j) {
-    run(c, OV_KIND_STENCIL_PAIR, 1, [&] { tsl_stencil(L, j, j < k - 1, c->st); });
+    run(c, OV_KIND_STENCIL_PAIR, 1, [&] { tsl_stencil(L, j, j < k - 1, c->st, c->tuned_pair[c->opt.precision]); });
     if (j == k - 1) break;
     const int reb = rebiorth_at(j + 1, c->opt.rebiorth);
     run(c, OV_KIND_UPDATE, 1, [&] { tsl_update(L, j, !reb, c->st); });
@@ -600,12 +602,47 @@ int apply_h_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, 1, false);
   run(c, OV_KIND_LAYOUT, 1,
       [&] { pack_spinors<R>(static_cast<const double*>(in), L.r, nsrc, L.g.V, L.vs, c->st); });
-  run(c, OV_KIND_APPLY_H, 1, [&] { apply_h(L, L.r, L.p, dagger, c->st); });
+  run(c, OV_KIND_APPLY_H, 1, [&] { apply_h(L, L.r, L.p, dagger, c->st, c->tuned_apply[c->opt.precision]); });
   run(c, OV_KIND_LAYOUT, 1,
       [&] { unpack_spinors<R>(L.p, static_cast<double*>(out), nsrc, L.g.V, L.vs, c->st); });
   launch_check();
   CK(cudaStreamSynchronize(c->st));
   prof_collect(c);
+  return OV_OK;
+}
+
+template <typename R>
+int autotune_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                  ov_tune_report* rep) {
+  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, 2, true);
+  CK(cudaMemsetAsync(L.r, 0, sizeof(R) * nsrc * L.vs, c->st));
+  CK(cudaMemsetAsync(L.s, 0, sizeof(R) * nsrc * L.vs, c->st));
+  CK(cudaMemsetAsync(L.sc, 0, sizeof(SrcScal) * nsrc, c->st));
+  cudaEvent_t e0 = c->ev[6], e1 = c->ev[7];
+  auto time_us = [&](auto&& launch) {
+    launch();
+    CK(cudaEventRecord(e0, c->st));
+    for (int r = 0; r < 5; ++r) launch();
+    CK(cudaEventRecord(e1, c->st));
+    CK(cudaEventSynchronize(e1));
+    launch_check();
+    return 1e3f * elapsed(e0, e1) / 5.f;
+  };
+  ov_tune_report r{};
+  r.n_apply = apply_h_variants();
+  r.n_pair = tsl_stencil_variants();
+  for (int v = 0; v < r.n_apply && v < 16; ++v)
+    r.apply_us[v] = time_us([&] { apply_h(L, L.r, L.p, 0, c->st, v); });
+  for (int v = 0; v < r.n_pair && v < 16; ++v)
+    r.pair_us[v] = time_us([&] { tsl_stencil(L, 0, true, c->st, v); });
+  for (int v = 1; v < r.n_apply && v < 16; ++v)
+    if (r.apply_us[v] < r.apply_us[r.apply_variant]) r.apply_variant = v;
+  for (int v = 1; v < r.n_pair && v < 16; ++v)
+    if (r.pair_us[v] < r.pair_us[r.pair_variant]) r.pair_variant = v;
+  c->tuned_apply[c->opt.precision] = r.apply_variant;
+  c->tuned_pair[c->opt.precision] = r.pair_variant;
+  c->launches += 6 * (r.n_apply + r.n_pair);
+  if (rep) *rep = r;
   return OV_OK;
 }
 
@@ -743,6 +780,24 @@ int ov_tsl_sign_vjp(ov_context* c, const int32_t dims[4], const void* U, double 
                ? tsl_vjp_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, xbar, x, dU, dmu, info)
                : tsl_vjp_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, xbar, x, dU, dmu, info);
   });
+}
+
+int ov_autotune(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                ov_tune_report* rep) {
+  if (!c) return OV_ERR_INVALID_ARG;
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED ? autotune_impl<float>(c, dims, U, mu, m_w, nsrc, rep)
+                                        : autotune_impl<double>(c, dims, U, mu, m_w, nsrc, rep);
+  });
+}
+
+int ov_set_stencil_variants(ov_context* c, int32_t apply_variant, int32_t pair_variant) {
+  if (!c || apply_variant < 0 || apply_variant >= apply_h_variants() || pair_variant < 0 ||
+      pair_variant >= tsl_stencil_variants())
+    return OV_ERR_INVALID_ARG;
+  c->tuned_apply[c->opt.precision] = apply_variant;
+  c->tuned_pair[c->opt.precision] = pair_variant;
+  return OV_OK;
 }
 
 int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, double* beta, double* delta) {
