@@ -126,19 +126,36 @@ OV_HD void store_spinor(float* f, int64_t V, int64_t s, const Spinor<float>& o) 
     p[c * V + s] = make_float4(o.c[2 * c].re, o.c[2 * c].im, o.c[2 * c + 1].re, o.c[2 * c + 1].im);
 }
 
+// Links, FP64: 36 complex per site, entry e = nu*9 + a*3 + b at e*V + s (double2).
+// Links, FP32: each direction's 9 complex padded to 10 and stored as 5 float4
+// chunks (two complex each), chunk q of direction nu at (5*nu + q)*V + s, so a
+// link is 5 sixteen-byte loads.  80 V floats per field.
+constexpr int kLinkRealsF32 = 80;
+constexpr int kLinkRealsF64 = 72;
+template <typename R> constexpr int link_reals() { return sizeof(R) == 4 ? kLinkRealsF32 : kLinkRealsF64; }
+
 OV_HD cplx<double> load_link_entry(const double* u, int64_t V, int64_t s, int e) {
   const double2 t = ldro(reinterpret_cast<const double2*>(u) + e * V + s);
   return mk(t.x, t.y);
 }
 OV_HD cplx<float> load_link_entry(const float* u, int64_t V, int64_t s, int e) {
-  const float2 t = ldro(reinterpret_cast<const float2*>(u) + e * V + s);
-  return mk(t.x, t.y);
+  const int nu = e / 9, r = e % 9;
+  const float4 t = ldro(reinterpret_cast<const float4*>(u) + (5 * nu + r / 2) * V + s);
+  return (r & 1) ? mk(t.z, t.w) : mk(t.x, t.y);
 }
 template <typename R> struct Mat3 { cplx<R> m[9]; };
-template <typename R>
-OV_HD void load_link(const R* u, int64_t V, int64_t s, int nu, Mat3<R>& o) {
+OV_HD void load_link(const double* u, int64_t V, int64_t s, int nu, Mat3<double>& o) {
 #pragma unroll
   for (int e = 0; e < 9; ++e) o.m[e] = load_link_entry(u, V, s, nu * 9 + e);
+}
+OV_HD void load_link(const float* u, int64_t V, int64_t s, int nu, Mat3<float>& o) {
+  const float4* p = reinterpret_cast<const float4*>(u) + (int64_t)5 * nu * V + s;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const float4 t = ldro(p + q * V);
+    o.m[2 * q] = mk(t.x, t.y);
+    if (q < 4) o.m[2 * q + 1] = mk(t.z, t.w);
+  }
 }
 
 template <typename R> OV_HD void spinor_zero(Spinor<R>& a) {

@@ -86,6 +86,7 @@ void dense_extract_tri(const zd* e, int k, zd* ga, zd* gb, double* gd, cudaStrea
 // ---------------------------------------------------------------------------
 constexpr int GJ_THREADS = 256;
 constexpr int GJ_ROWS = 4;
+constexpr int GJ_JPT = 4;   // columns per thread held in registers (k <= 1024)
 
 struct Cand { double v; int i; };
 
@@ -153,23 +154,59 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_step(const zd* __restrict__ x
   const int r0 = blockIdx.x * GJ_ROWS;
   const int nrow = min(GJ_ROWS, k - r0);
   Cand nc{-1.0, 0x7fffffff};
-  for (int r = 0; r < nrow; ++r) {
-    const int i = r0 + r;
-    const zd f = xin[(int64_t)i * k + kk];
-    const zd* xr = xin + (int64_t)i * k;
-    zd* yr = xout + (int64_t)i * k;
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
-      zd v;
-      if (i == p) {
-        v = prow[j];
-      } else if (j == kk) {
-        v = -(f * prow[kk]);
-      } else {
-        v = xr[j];
-        cmsub(v, f, prow[j]);
+  if (k <= GJ_THREADS * GJ_JPT) {
+    // all loads of the block's rows are issued before any arithmetic
+    zd xv[GJ_ROWS][GJ_JPT], fr[GJ_ROWS];
+#pragma unroll
+    for (int r = 0; r < GJ_ROWS; ++r) {
+      const int i = r0 + r;
+      fr[r] = r < nrow ? xin[(int64_t)i * k + kk] : mk(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < GJ_JPT; ++q) {
+        const int j = threadIdx.x + q * GJ_THREADS;
+        xv[r][q] = (r < nrow && j < k) ? xin[(int64_t)i * k + j] : mk(0.0, 0.0);
       }
-      yr[j] = v;
-      if (j == kk + 1 && i != p && !used[i]) nc = cand_max(nc, Cand{norm2(v), i});
+    }
+#pragma unroll
+    for (int r = 0; r < GJ_ROWS; ++r) {
+      const int i = r0 + r;
+      if (r >= nrow) break;
+#pragma unroll
+      for (int q = 0; q < GJ_JPT; ++q) {
+        const int j = threadIdx.x + q * GJ_THREADS;
+        if (j >= k) break;
+        zd v;
+        if (i == p) {
+          v = prow[j];
+        } else if (j == kk) {
+          v = -(fr[r] * prow[kk]);
+        } else {
+          v = xv[r][q];
+          cmsub(v, fr[r], prow[j]);
+        }
+        xout[(int64_t)i * k + j] = v;
+        if (j == kk + 1 && i != p && !used[i]) nc = cand_max(nc, Cand{norm2(v), i});
+      }
+    }
+  } else {
+    for (int r = 0; r < nrow; ++r) {
+      const int i = r0 + r;
+      const zd f = xin[(int64_t)i * k + kk];
+      const zd* xr = xin + (int64_t)i * k;
+      zd* yr = xout + (int64_t)i * k;
+      for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        zd v;
+        if (i == p) {
+          v = prow[j];
+        } else if (j == kk) {
+          v = -(f * prow[kk]);
+        } else {
+          v = xr[j];
+          cmsub(v, f, prow[j]);
+        }
+        yr[j] = v;
+        if (j == kk + 1 && i != p && !used[i]) nc = cand_max(nc, Cand{norm2(v), i});
+      }
     }
   }
   nc = block_cand_max(nc, sh);

@@ -198,6 +198,55 @@ OV_HD void h_site_multi(const LD (&ld)[NS], const R* u, const Geom& g, int64_t s
   }
 }
 
+// Link-gradient contribution of one rank-one term a b^dagger for direction NU,
+// on half spinors.  With h = P_+(b(x+nu)) the upper pair of (1+gamma_nu) b(x+nu),
+//   sum_s a(x)_s conj((gamma5 (1+gamma_nu) b(x+nu))_s) = sum_t a~_t conj(h_t),
+// where a~ = P_-(a(x)) (the lower pair enters through gamma5 and the adjoint
+// of the reconstruction); likewise for the backward hop with the signs swapped:
+//   forward:  G[c][d] += cf * sum_t a~_t[c] conj(h_t[d]),   a~ = P_-(a(x)),   h = P_+(b(x+nu))
+//   backward: G[c][d] += cb * sum_t conj(a'_t[d]) h'_t[c],  a' = P_+(a(x+nu)), h' = P_-(b(x))
+// (cf = -kappa f_nu, cb = -kappa / f_nu).  Gd collects forward minus backward.
+template <int NU, typename R>
+OV_HD void force_half_fwd(const Spinor<R>& ax, const Spinor<R>& bxf, R cf, cplx<R> (&G)[9], cplx<R> (&Gd)[9],
+                          bool with_d) {
+  Half<R> at, h;
+  spin_project<NU, -1>(ax, at);
+  spin_project<NU, +1>(bxf, h);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cplx<R> t = czero<R>();
+      cdotac(t, h.h[0][d], at.h[0][c]);   // conj(h) * a~
+      cdotac(t, h.h[1][d], at.h[1][c]);
+      G[c * 3 + d] = G[c * 3 + d] + cf * t;
+      if (with_d) Gd[c * 3 + d] = Gd[c * 3 + d] + cf * t;
+    }
+}
+template <int NU, typename R>
+OV_HD void force_half_bwd(const Spinor<R>& axf, const Spinor<R>& bx, R cb, cplx<R> (&G)[9], cplx<R> (&Gd)[9],
+                          bool with_d) {
+  Half<R> at, h;
+  spin_project<NU, +1>(axf, at);
+  spin_project<NU, -1>(bx, h);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cplx<R> t = czero<R>();
+      cdotac(t, at.h[0][d], h.h[0][c]);   // conj(a') * h'
+      cdotac(t, at.h[1][d], h.h[1][c]);
+      G[c * 3 + d] = G[c * 3 + d] + cb * t;
+      if (with_d) Gd[c * 3 + d] = Gd[c * 3 + d] - cb * t;
+    }
+}
+template <int NU, typename R>
+OV_HD void force_half(const Spinor<R>& ax, const Spinor<R>& bxf, const Spinor<R>& axf, const Spinor<R>& bx,
+                      R cf, R cb, cplx<R> (&G)[9], cplx<R> (&Gd)[9], bool with_d) {
+  force_half_fwd<NU>(ax, bxf, cf, G, Gd, with_d);
+  force_half_bwd<NU>(axf, bx, cb, G, Gd, with_d);
+}
+
 // gamma5 (1 + sgn*gamma_nu) b, all four spins (used by the force contraction)
 template <int NU, int SGN, typename R>
 OV_HD void g5_proj_full(const Spinor<R>& b, Spinor<R>& o) {

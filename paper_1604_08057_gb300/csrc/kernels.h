@@ -29,7 +29,7 @@ template <typename R>
 struct Lat {
   Geom g;
   R kappa, ef, efinv;        // kappa, e^{mu}, e^{-mu}
-  const R* u;                // internal links (72 V reals)
+  const R* u;                // internal links (link_reals<R>() * V reals)
   int nsrc, k;
   int64_t vs;                // reals per lattice vector (padded)
   R* bv;                     // basis V: [src][k][vs]

@@ -48,10 +48,20 @@ __global__ void k_pack_links(const double* __restrict__ aos, R* __restrict__ u, 
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (x >= V) return;
   const double2* in = reinterpret_cast<const double2*>(aos) + x * 36;
-  for (int e = 0; e < 36; ++e) {
-    double2 t = in[e];
-    u[2 * (e * V + x)] = (R)t.x;
-    u[2 * (e * V + x) + 1] = (R)t.y;
+  if constexpr (sizeof(R) == 8) {
+    for (int e = 0; e < 36; ++e) {
+      double2 t = in[e];
+      u[2 * (e * V + x)] = t.x;
+      u[2 * (e * V + x) + 1] = t.y;
+    }
+  } else {
+    float4* o = reinterpret_cast<float4*>(u);
+    for (int nu = 0; nu < 4; ++nu)
+      for (int q = 0; q < 5; ++q) {
+        const double2 a = in[nu * 9 + 2 * q];
+        const double2 b = q < 4 ? in[nu * 9 + 2 * q + 1] : make_double2(0.0, 0.0);
+        o[(5 * nu + q) * V + x] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+      }
   }
 }
 
@@ -863,37 +873,13 @@ __device__ void force_term(const Lat<R>& L, int64_t x, int64_t xf, const R* a, c
                            cplx<R> (&Gd)[9]) {
   const int64_t V = L.g.V;
   const R ff = NU == 3 ? L.ef : R(1), fb = NU == 3 ? L.efinv : R(1);
-  Spinor<R> sa, sb, cb;
-  // forward
+  Spinor<R> sa, sb;
   load_spinor(a, V, x, sa);
   load_spinor(b, V, xf, sb);
-  g5_proj_full<NU, +1>(sb, cb);
-  const R cf = -L.kappa * ff;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      cplx<R> t = czero<R>();
-#pragma unroll
-      for (int s = 0; s < 4; ++s) cmac(t, sa.c[s * 3 + c], conj(cb.c[s * 3 + d]));
-      G[c * 3 + d] = G[c * 3 + d] + cf * t;
-      if (NU == 3) Gd[c * 3 + d] = Gd[c * 3 + d] + cf * t;
-    }
-  // backward
+  force_half_fwd<NU>(sa, sb, -L.kappa * ff, G, Gd, NU == 3);
   load_spinor(a, V, xf, sa);
   load_spinor(b, V, x, sb);
-  g5_proj_full<NU, -1>(sb, cb);
-  const R cbk = -L.kappa * fb;
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      cplx<R> t = czero<R>();
-#pragma unroll
-      for (int s = 0; s < 4; ++s) cmac(t, conj(sa.c[s * 3 + d]), cb.c[s * 3 + c]);
-      G[c * 3 + d] = G[c * 3 + d] + cbk * t;
-      if (NU == 3) Gd[c * 3 + d] = Gd[c * 3 + d] - cbk * t;
-    }
+  force_half_bwd<NU>(sa, sb, -L.kappa * fb, G, Gd, NU == 3);
 }
 
 template <int NU, typename R>
@@ -906,19 +892,28 @@ __device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterm
 #pragma unroll
   for (int e = 0; e < 9; ++e) acc[e] = accd[e] = mk(0.0, 0.0);
   for (int src = 0; src < L.nsrc; ++src) {
-    cplx<R> G[9], Gd[9];
+    if constexpr (sizeof(R) == 8) {
+      // FP64 fields: accumulate straight into the FP64 sums
+      for (int t = 0; t < nterms; ++t) {
+        const int j = j0 - t;
+        force_term<NU>(L, x, xf, B.ring(B.gp_ring, t, src), L.basis_v(src, j), acc, accd);
+        if (j < L.k - 1) force_term<NU>(L, x, xf, L.basis_w(src, j), B.ring(B.gs_ring, t, src), acc, accd);
+      }
+    } else {
+      // FP32 fields: FP32 partial sums over one ring of terms, then FP64
+      cplx<R> G[9], Gd[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) G[e] = Gd[e] = czero<R>();
-    for (int t = 0; t < nterms; ++t) {
-      const int j = j0 - t;
-      force_term<NU>(L, x, xf, B.ring(B.gp_ring, t, src), L.basis_v(src, j), G, Gd);
-      if (j < L.k - 1)
-        force_term<NU>(L, x, xf, L.basis_w(src, j), B.ring(B.gs_ring, t, src), G, Gd);
-    }
+      for (int e = 0; e < 9; ++e) G[e] = Gd[e] = czero<R>();
+      for (int t = 0; t < nterms; ++t) {
+        const int j = j0 - t;
+        force_term<NU>(L, x, xf, B.ring(B.gp_ring, t, src), L.basis_v(src, j), G, Gd);
+        if (j < L.k - 1) force_term<NU>(L, x, xf, L.basis_w(src, j), B.ring(B.gs_ring, t, src), G, Gd);
+      }
 #pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      acc[e] = acc[e] + mk((double)G[e].re, (double)G[e].im);
-      accd[e] = accd[e] + mk((double)Gd[e].re, (double)Gd[e].im);
+      for (int e = 0; e < 9; ++e) {
+        acc[e] = acc[e] + mk((double)G[e].re, (double)G[e].im);
+        accd[e] = accd[e] + mk((double)Gd[e].re, (double)Gd[e].im);
+      }
     }
   }
   double2* f = reinterpret_cast<double2*>(B.force);
@@ -933,39 +928,37 @@ __device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterm
     double dm = 0.0;
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
-      const zd u = mk((double)L.u[2 * ((27 + e) * L.g.V + x)], (double)L.u[2 * ((27 + e) * L.g.V + x) + 1]);
-      dm += accd[e].re * u.re + accd[e].im * u.im;     // Re(conj(Gd) u)
+      const cplx<R> u = load_link_entry(L.u, L.g.V, x, 27 + e);
+      dm += accd[e].re * (double)u.re + accd[e].im * (double)u.im;     // Re(conj(Gd) u)
     }
     dmu_site->re = dm;
   }
 }
 
-template <typename R>
+// one launch per direction (smaller register footprint); the dmu partials come from NU = 3
+template <int NU, typename R>
 __global__ void __launch_bounds__(BS) k_force(Lat<R> L, Rev<R> B, int nterms, int j0) {
   __shared__ zd scratch[32];
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int nu = blockIdx.y;
   zd v[1] = {mk(0.0, 0.0)};
-  if (x < L.g.V) {
-    if (nu == 0) force_dir<0>(L, B, x, nterms, j0, &v[0]);
-    else if (nu == 1) force_dir<1>(L, B, x, nterms, j0, &v[0]);
-    else if (nu == 2) force_dir<2>(L, B, x, nterms, j0, &v[0]);
-    else force_dir<3>(L, B, x, nterms, j0, &v[0]);
-  }
+  if (x < L.g.V) force_dir<NU>(L, B, x, nterms, j0, &v[0]);
+  if (NU != 3) return;
   block_sum<1>(v, scratch);
-  const unsigned nblk = gridDim.x * gridDim.y;
-  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-  if (threadIdx.x == 0) B.dmu_part[bid] = v[0];
-  if (arrive_last(B.dmu_cnt, nblk)) {
+  if (threadIdx.x == 0) B.dmu_part[blockIdx.x] = v[0];
+  if (arrive_last(B.dmu_cnt, gridDim.x)) {
     zd s[1];
-    sum_partials<1>(B.dmu_part, nblk, s, scratch);
+    sum_partials<1>(B.dmu_part, gridDim.x, s, scratch);
     if (threadIdx.x == 0) *B.dmu += s[0].re;
   }
 }
 template <typename R>
 void force_flush(const Lat<R>& L, const Rev<R>& B, const int* /*unused*/, int nterms, int j0, cudaStream_t st) {
   if (nterms <= 0) return;
-  k_force<R><<<dim3(nblocks(L.g.V, BS), 4), BS, 0, st>>>(L, B, nterms, j0);
+  const unsigned nb = nblocks(L.g.V, BS);
+  k_force<0, R><<<nb, BS, 0, st>>>(L, B, nterms, j0);
+  k_force<1, R><<<nb, BS, 0, st>>>(L, B, nterms, j0);
+  k_force<2, R><<<nb, BS, 0, st>>>(L, B, nterms, j0);
+  k_force<3, R><<<nb, BS, 0, st>>>(L, B, nterms, j0);
 }
 
 // explicit instantiations

@@ -154,7 +154,7 @@ Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, dou
   L.nsrc = nsrc;
   L.k = k;
   L.vs = ((24 * V + 63) / 64) * 64;
-  R* u = wsT<R>(c, B_LINKS, 72 * V);
+  R* u = wsT<R>(c, B_LINKS, link_reals<R>() * V);
   L.u = u;
   run(c, OV_KIND_LAYOUT, 1, [&] { pack_links<R>(static_cast<const double*>(U), u, V, c->st); });
   launch_check();
@@ -549,7 +549,7 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   int slot = 1, j0 = k - 1, nrec = 0;
   for (int j = k - 2; j >= 0; --j) {
     if (slot == m) {
-      run(c, OV_KIND_FORCE, 1, [&] { force_flush(L, B, nullptr, m, j0, c->st); });
+      run(c, OV_KIND_FORCE, 4, [&] { force_flush(L, B, nullptr, m, j0, c->st); });
       slot = 0;
       j0 = j;
     }
@@ -573,7 +573,7 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
     std::swap(B.gw, B.gw_new);
     ++slot;
   }
-  run(c, OV_KIND_FORCE, 1, [&] { force_flush(L, B, nullptr, slot, j0, c->st); });
+  run(c, OV_KIND_FORCE, 4, [&] { force_flush(L, B, nullptr, slot, j0, c->st); });
   CK(cudaEventRecord(c->ev[5], c->st));
   run(c, OV_KIND_LAYOUT, 1, [&] { unpack_force(B.force, static_cast<double*>(dU), V, c->st); });
   launch_check();
