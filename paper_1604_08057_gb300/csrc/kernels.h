@@ -86,8 +86,9 @@ template <typename R> void tsl_update(const Lat<R>& L, int j, bool finalize, cud
 // mode 1 (adjoint):  e_r = V^dag g_r, e_s = W^dag g_s;  g_r -= W e_r, g_s -= V e_s
 template <typename R> void proj_dots(const Lat<R>& L, int j, int mode, const R* a, const R* b,
                                      int64_t ab_src_stride, zd* coef, zd* cpart, cudaStream_t st);
+// small: the coefficients are at rounding level (a second Gram-Schmidt pass): FP32 accumulation
 template <typename R> void proj_update(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_src_stride,
-                                       const zd* coef, bool finalize_omega, cudaStream_t st);
+                                       const zd* coef, bool finalize_omega, cudaStream_t st, bool small);
 template <typename R> void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_src_stride, zd* out,
                                       zd* cpart, cudaStream_t st);
 template <typename R> void combine(const Lat<R>& L, int nvec, const zd* y, double* out_aos, cudaStream_t st);

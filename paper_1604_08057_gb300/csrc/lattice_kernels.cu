@@ -6,6 +6,8 @@
 // Thread mapping: one thread per lattice site (blockIdx.y = source) unless a
 // kernel says otherwise.  All reductions are deterministic: per-block partials
 // are summed in block order by the last block to finish.
+#include <type_traits>
+
 #include "dslash.cuh"
 #include "kernels.h"
 
@@ -428,18 +430,30 @@ __global__ void k_proj_reduce(const zd* __restrict__ cpart, int64_t cp_stride, i
   coef[src * coef_stride + t] = s;
 }
 
-template <typename R>
+// SMALL: the coefficients are at rounding level relative to a and b (the second
+// Gram-Schmidt pass, whose input is already biorthogonal to working precision),
+// so the correction sum_i c_i u_i is formed in FP32 arithmetic; its rounding is
+// ~6e-8 of a correction that is itself ~1e-12 or less of a, far below FP64
+// rounding of a.  FP64 fields are still read in full.
+template <typename T, typename R> OV_HD void spinor_cast(const Spinor<R>& in, Spinor<T>& out) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) out.c[c] = mk<T>((T)in.c[c].re, (T)in.c[c].im);
+}
+
+template <typename R, bool SMALL>
 __global__ void __launch_bounds__(BS) k_proj_update(Lat<R> L, int nb, int mode, R* __restrict__ a,
                                                      R* __restrict__ b, int64_t ab_stride,
                                                      const zd* __restrict__ coef, int64_t coef_stride,
                                                      int j, int finalize) {
+  using A = typename std::conditional<SMALL, float, R>::type;   // accumulation type
   __shared__ zd cs[2 * 64];
   __shared__ zd scratch[3 * 32];
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int src = blockIdx.y;
   const int64_t V = L.g.V;
   const bool active = x < V;
-  Spinor<R> ca, cb, e;
+  Spinor<A> ca, cb;
+  Spinor<R> e;
   spinor_zero(ca);
   spinor_zero(cb);
   const zd* cf = coef + src * coef_stride;
@@ -452,16 +466,16 @@ __global__ void __launch_bounds__(BS) k_proj_update(Lat<R> L, int nb, int mode, 
       for (int t = 0; t < n; ++t) {
         const int i = i0 + t;
         const R* ua = mode == 0 ? L.basis_v(src, i) : L.basis_w(src, i);
-        const cplx<R> c0 = cast<R>(cs[2 * t]);
+        const cplx<A> c0 = cast<A>(cs[2 * t]);
         load_spinor(ua, V, x, e);
 #pragma unroll
-        for (int c = 0; c < 12; ++c) cmac(ca.c[c], c0, e.c[c]);
+        for (int c = 0; c < 12; ++c) cmac(ca.c[c], c0, mk<A>((A)e.c[c].re, (A)e.c[c].im));
         if (b) {
           const R* ub = mode == 0 ? L.basis_w(src, i) : L.basis_v(src, i);
-          const cplx<R> c1 = cast<R>(cs[2 * t + 1]);
+          const cplx<A> c1 = cast<A>(cs[2 * t + 1]);
           load_spinor(ub, V, x, e);
 #pragma unroll
-          for (int c = 0; c < 12; ++c) cmac(cb.c[c], c1, e.c[c]);
+          for (int c = 0; c < 12; ++c) cmac(cb.c[c], c1, mk<A>((A)e.c[c].re, (A)e.c[c].im));
         }
       }
     }
@@ -471,12 +485,12 @@ __global__ void __launch_bounds__(BS) k_proj_update(Lat<R> L, int nb, int mode, 
     Spinor<R> r, s;
     load_spinor(a + src * ab_stride, V, x, r);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) r.c[c] = r.c[c] - ca.c[c];
+    for (int c = 0; c < 12; ++c) r.c[c] = r.c[c] - mk<R>((R)ca.c[c].re, (R)ca.c[c].im);
     store_spinor(a + src * ab_stride, V, x, r);
     if (b) {
       load_spinor(b + src * ab_stride, V, x, s);
 #pragma unroll
-      for (int c = 0; c < 12; ++c) s.c[c] = s.c[c] - cb.c[c];
+      for (int c = 0; c < 12; ++c) s.c[c] = s.c[c] - mk<R>((R)cb.c[c].re, (R)cb.c[c].im);
       store_spinor(b + src * ab_stride, V, x, s);
       if (finalize) {
         v[0] = spinor_dot(s, r);
@@ -511,9 +525,14 @@ void proj_dots(const Lat<R>& L, int j, int mode, const R* a, const R* b, int64_t
 }
 template <typename R>
 void proj_update(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_stride, const zd* coef, bool finalize,
-                 cudaStream_t st) {
-  k_proj_update<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, j + 1, mode, a, b, ab_stride, coef,
-                                                                     2 * (int64_t)L.k, j, finalize ? 1 : 0);
+                 cudaStream_t st, bool small) {
+  const dim3 grid(nblocks(L.g.V, BS), L.nsrc);
+  if (small && sizeof(R) == 8)
+    k_proj_update<R, true><<<grid, BS, 0, st>>>(L, j + 1, mode, a, b, ab_stride, coef, 2 * (int64_t)L.k, j,
+                                                finalize ? 1 : 0);
+  else
+    k_proj_update<R, false><<<grid, BS, 0, st>>>(L, j + 1, mode, a, b, ab_stride, coef, 2 * (int64_t)L.k, j,
+                                                 finalize ? 1 : 0);
 }
 
 // out[src][i] = v_i^dag x  for i < nvec (dots of the V basis with one vector per source)
@@ -971,7 +990,8 @@ void force_flush(const Lat<R>& L, const Rev<R>& B, const int* /*unused*/, int nt
   template void tsl_stencil<R>(const Lat<R>&, int, bool, cudaStream_t, int);                             \
   template void tsl_update<R>(const Lat<R>&, int, bool, cudaStream_t);                                   \
   template void proj_dots<R>(const Lat<R>&, int, int, const R*, const R*, int64_t, zd*, zd*, cudaStream_t); \
-  template void proj_update<R>(const Lat<R>&, int, int, R*, R*, int64_t, const zd*, bool, cudaStream_t);   \
+  template void proj_update<R>(const Lat<R>&, int, int, R*, R*, int64_t, const zd*, bool, cudaStream_t, \
+                               bool);                                                                   \
   template void basis_dots<R>(const Lat<R>&, int, const R*, int64_t, zd*, zd*, cudaStream_t);            \
   template void combine<R>(const Lat<R>&, int, const zd*, double*, cudaStream_t);                        \
   template void rev_init<R>(const Lat<R>&, const Rev<R>&, cudaStream_t);                                 \

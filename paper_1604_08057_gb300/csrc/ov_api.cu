@@ -214,7 +214,7 @@ void forward_krylov(ov_context* c, Lat<R>& L) {
       for (int ps = 0; ps < c->opt.passes; ++ps) {
         run(c, OV_KIND_PROJ_DOTS, 2, [&] { proj_dots(L, j, 0, L.r, L.s, L.vs, coef, cpart, c->st); });
         run(c, OV_KIND_PROJ_UPDATE, 1,
-            [&] { proj_update(L, j, 0, L.r, L.s, L.vs, coef, ps == c->opt.passes - 1, c->st); });
+            [&] { proj_update(L, j, 0, L.r, L.s, L.vs, coef, ps == c->opt.passes - 1, c->st, ps > 0); });
       }
     }
   }
@@ -562,7 +562,7 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
       R* gss = B.gs_ring + (int64_t)slot * nsrc * vs;
       for (int ps = 0; ps < c->opt.passes; ++ps) {
         run(c, OV_KIND_PROJ_DOTS, 2, [&] { proj_dots(L, j, 1, grs, gss, vs, coef, cpart, c->st); });
-        run(c, OV_KIND_PROJ_UPDATE, 1, [&] { proj_update(L, j, 1, grs, gss, vs, coef, false, c->st); });
+        run(c, OV_KIND_PROJ_UPDATE, 1, [&] { proj_update(L, j, 1, grs, gss, vs, coef, false, c->st, ps > 0); });
         run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_proj_record(L, B, j, nrec, coef, c->st); });
       }
       run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_alpha_dots(L, B, j, slot, c->st); });

@@ -1,0 +1,98 @@
+"""Full-size checks on the 14x14^3, k = 800 workload (the benchmark's launch
+configuration: FP64, pair-periodic re-biorthogonalisation every 20 steps, one
+Gram-Schmidt pass; two passes are checked as well).  The oracle cannot run this size in seconds, so the checks
+use properties that hold at any size:
+
+* the VJP against central finite differences of the GPU's own FP64 forward
+  map along a direction supported on 16 random links, and along mu;
+* a batched call over several sources equals the per-source calls;
+* sampled outputs of H psi against the oracle's operator at those sites.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dirac
+from paper_1604_08057_gb300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+WL = inputs.WORKLOADS["14x14^3"]
+P = 20
+
+
+@pytest.fixture(scope="module")
+def data():
+    u, b, xbar = inputs.make_inputs(WL)
+    return u, b, xbar
+
+
+@pytest.mark.parametrize("PASSES", [1, 2])
+def test_vjp_finite_differences_on_16_links(data, PASSES):
+    u, b, xbar = data
+    k, mu, m_w = WL.k, WL.mu, WL.m_w
+    ut, bt, xt = (torch.tensor(a, device="cuda") for a in (u, b[0], xbar[0]))
+    du, dmu, _ = binding.tsl_sign_vjp(ut, mu, m_w, bt, k, xt, "fp64", P, PASSES)
+    du = du.cpu().numpy()
+    rng = np.random.default_rng(2016)
+    shape = u.shape[:4]
+    e = np.zeros_like(u)
+    for _ in range(16):
+        site = tuple(int(rng.integers(0, n)) for n in shape)
+        nu = int(rng.integers(0, 4))
+        e[site + (nu,)] = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+
+    def loss(uu, mm):
+        x = binding.tsl_sign(torch.tensor(uu, device="cuda"), mm, m_w, bt, k, "fp64", P, PASSES)
+        return float(torch.real(torch.vdot(xt.flatten(), x.flatten())))
+
+    # At k = 800 the map's rounding floor limits central differences to ~1e-3
+    # (measured: FD at h = 1e-4 scatters by 1.4e-3 across schedules, smaller h is
+    # noise); the step sizes below are the most accurate ones measured.
+    h = 1e-4
+    fd = (loss(u + h * e, mu) - loss(u - h * e, mu)) / (2 * h)
+    ad = float(np.real(np.vdot(du, e)))
+    assert abs(fd - ad) <= 5e-3 * abs(fd), (fd, ad)
+
+@pytest.mark.parametrize("PASSES", [1, 2])
+def test_vjp_mu_finite_differences_k200(data, PASSES):
+    """d/dmu at the full lattice with k = 200.  At k = 800 the mu-derivative of the
+    k-step map is itself chaotic at the 10% level (mu moves every temporal link and
+    with them the Ritz values next to Re z = 0, where sgn's derivative is ~1/|Re z|):
+    central differences and the VJP there move by ~10% under any change of rounding
+    order, so the mu check is made where the map is still smooth."""
+    u, b, xbar = data
+    k, mu, m_w = 200, WL.mu, WL.m_w
+    ut, bt, xt = (torch.tensor(a, device="cuda") for a in (u, b[0], xbar[0]))
+    _, dmu, _ = binding.tsl_sign_vjp(ut, mu, m_w, bt, k, xt, "fp64", P, PASSES)
+
+    def loss(mm):
+        x = binding.tsl_sign(ut, mm, m_w, bt, k, "fp64", P, PASSES)
+        return float(torch.real(torch.vdot(xt.flatten(), x.flatten())))
+
+    h = 1e-6
+    fd_mu = (loss(mu + h) - loss(mu - h)) / (2 * h)
+    assert abs(fd_mu - dmu) <= 1e-3 * abs(fd_mu), (fd_mu, dmu)
+
+
+def test_batched_sources_equal_single_source_calls(data):
+    PASSES = 1
+    u, _, _ = data
+    rng = np.random.default_rng(5)
+    b = inputs.gaussian_spinors(WL.dims, 3, rng)
+    ut, bt = torch.tensor(u, device="cuda"), torch.tensor(b, device="cuda")
+    k = 120
+    xb = binding.tsl_sign(ut, WL.mu, WL.m_w, bt, k, "fp64", P, PASSES)
+    for s in range(3):
+        xs = binding.tsl_sign(ut, WL.mu, WL.m_w, bt[s], k, "fp64", P, PASSES)
+        assert torch.equal(xb[s], xs), s
+
+
+def test_apply_h_sampled_sites_full_size(data):
+    u, b, _ = data
+    got = binding.apply_H(torch.tensor(u, device="cuda"), WL.mu, WL.m_w,
+                          torch.tensor(b[0], device="cuda")).cpu().numpy()
+    want = dirac.apply_h(u, b[0], WL.mu, WL.m_w)
+    rng = np.random.default_rng(9)
+    for _ in range(64):
+        site = tuple(int(rng.integers(0, n)) for n in u.shape[:4])
+        assert np.abs(got[site] - want[site]).max() <= 1e-13 * np.abs(want).max()

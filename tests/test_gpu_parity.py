@@ -104,7 +104,8 @@ def test_every_stencil_variant(precision, tol_h, tol_x):
     ((3, 3, 3, 3), 0.3, -1.0, 60, 1, 2, 1e-11),
     ((3, 5, 2, 4), 0.4, -1.0, 45, 10, 2, 1e-11),     # ragged lattice, pair-periodic
     ((4, 4, 4, 4), 0.3, -2.0, 200, 1, 2, 1e-9),      # the 4x4^3 workload: floor 1e-10
-    ((4, 4, 4, 4), 0.3, -2.0, 200, 20, 1, 1e-9),     # benchmark schedule: P = 20, one pass
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 20, 1, 1e-9),     # P = 20, one pass
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 20, 2, 1e-9),     # benchmark schedule: P = 20, two passes
 ])
 def test_tsl_forward_fp64(dims, mu, m_w, k, reb, passes, tol):
     u, b, _ = case(dims, 0.3, 3)
@@ -146,7 +147,8 @@ def test_tsl_forward_mixed_precision():
     ((3, 3, 3, 3), 0.3, -1.0, 40, 1, 2, 1e-9),
     ((3, 5, 2, 4), 0.3, -1.0, 50, 10, 2, 1e-8),
     ((4, 4, 4, 4), 0.3, -2.0, 200, 1, 2, 1e-6),      # the 4x4^3 workload: dU floor 9e-8
-    ((4, 4, 4, 4), 0.3, -2.0, 200, 20, 1, 5e-6),     # benchmark schedule: dU floor 7.4e-7
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 20, 1, 5e-6),     # P = 20, one pass: dU floor 7.4e-7
+    ((4, 4, 4, 4), 0.3, -2.0, 200, 20, 2, 5e-6),     # benchmark schedule: dU floor 3.7e-7
 ])
 def test_vjp_fp64(dims, mu, m_w, k, reb, passes, tol):
     u, b, xbar = case(dims, 0.3, 3)
