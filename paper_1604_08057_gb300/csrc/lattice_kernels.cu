@@ -18,6 +18,21 @@ constexpr int NB = 8;     // basis vectors per block in the projection dots
 
 static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Site of this thread.  MAP 0: consecutive sites.  MAP 1 ("plane" tiles): block b
+// owns the whole x-y plane b (Nx*Ny sites), so the +-x and +-y neighbours and their
+// links are read by threads of the same block and are served by L1.
+template <int MAP>
+__device__ __forceinline__ int64_t thread_site(const Geom& g) {
+  if (MAP == 0) return blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int plane = g.nx * g.ny;
+  return threadIdx.x < plane ? (int64_t)blockIdx.x * plane + threadIdx.x : g.V;
+}
+static inline bool plane_ok(const Geom& g, int max_threads) {
+  const int plane = g.nx * g.ny;
+  return plane >= 64 && (plane + 31) / 32 * 32 <= max_threads;
+}
+static inline unsigned plane_threads(const Geom& g) { return (unsigned)((g.nx * g.ny + 31) / 32 * 32); }
+
 // ---------------------------------------------------------------------------
 // layout conversion
 // ---------------------------------------------------------------------------
@@ -95,10 +110,10 @@ void unpack_force(const double* f, double* du, int64_t V, cudaStream_t st) {
 // H and H^dagger
 // ---------------------------------------------------------------------------
 // NS sources per thread share every link load; blockIdx.y indexes groups of NS sources
-template <typename R, int NS, int BSZ>
+template <typename R, int NS, int BSZ, int MAP>
 __global__ void __launch_bounds__(BSZ) k_apply_h(Lat<R> L, const R* __restrict__ in, R* __restrict__ out,
                                                  int dagger, int nsrc) {
-  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t x = thread_site<MAP>(L.g);
   const int s0 = blockIdx.y * NS;
   if (x >= L.g.V) return;
   const R f = dagger ? L.efinv : L.ef, fi = dagger ? L.ef : L.efinv;
@@ -117,30 +132,40 @@ __global__ void __launch_bounds__(BSZ) k_apply_h(Lat<R> L, const R* __restrict__
     if (s0 + i < nsrc) store_spinor(out + (int64_t)(s0 + i) * L.vs, L.g.V, x, o[i]);
 }
 
-// launch variants (sources per thread, threads per block); 0 is the default
-static const int kApplyVariants[][2] = {{1, 128}, {1, 64}, {1, 256}, {2, 64}, {2, 128}, {4, 64}, {4, 128}};
+// launch variants (sources per thread, threads per block, site map); 0 is the default.
+// Plane variants fall back to consecutive sites when an x-y plane has fewer than
+// 64 sites or more than the variant's thread bound.
+static const int kApplyVariants[][3] = {{1, 128, 0}, {1, 64, 0}, {1, 256, 0}, {2, 64, 0}, {2, 128, 0},
+                                        {4, 64, 0}, {4, 128, 0}, {1, 512, 1}, {2, 256, 1}};
 int apply_h_variants() { return (int)(sizeof(kApplyVariants) / sizeof(kApplyVariants[0])); }
 
-template <typename R, int NS, int BSZ>
+template <typename R, int NS, int BSZ, int MAP>
 static void launch_apply(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st) {
+  if (MAP == 1 && !plane_ok(L.g, BSZ)) {
+    launch_apply<R, NS, 128, 0>(L, in, out, dagger, st);
+    return;
+  }
+  const unsigned bs = MAP == 1 ? plane_threads(L.g) : BSZ;
+  const unsigned gx = MAP == 1 ? (unsigned)(L.g.V / (L.g.nx * L.g.ny)) : nblocks(L.g.V, BSZ);
   const int ns = L.nsrc < NS ? 1 : NS;   // a lone source never needs the wider variant
   if (ns == 1)
-    k_apply_h<R, 1, BSZ><<<dim3(nblocks(L.g.V, BSZ), L.nsrc), BSZ, 0, st>>>(L, in, out, dagger, L.nsrc);
+    k_apply_h<R, 1, BSZ, MAP><<<dim3(gx, L.nsrc), bs, 0, st>>>(L, in, out, dagger, L.nsrc);
   else
-    k_apply_h<R, NS, BSZ><<<dim3(nblocks(L.g.V, BSZ), (L.nsrc + NS - 1) / NS), BSZ, 0, st>>>(L, in, out, dagger,
-                                                                                           L.nsrc);
+    k_apply_h<R, NS, BSZ, MAP><<<dim3(gx, (L.nsrc + NS - 1) / NS), bs, 0, st>>>(L, in, out, dagger, L.nsrc);
 }
 
 template <typename R>
 void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st, int variant) {
   switch (variant) {
-    case 1: launch_apply<R, 1, 64>(L, in, out, dagger, st); break;
-    case 2: launch_apply<R, 1, 256>(L, in, out, dagger, st); break;
-    case 3: launch_apply<R, 2, 64>(L, in, out, dagger, st); break;
-    case 4: launch_apply<R, 2, 128>(L, in, out, dagger, st); break;
-    case 5: launch_apply<R, 4, 64>(L, in, out, dagger, st); break;
-    case 6: launch_apply<R, 4, 128>(L, in, out, dagger, st); break;
-    default: launch_apply<R, 1, 128>(L, in, out, dagger, st); break;
+    case 1: launch_apply<R, 1, 64, 0>(L, in, out, dagger, st); break;
+    case 2: launch_apply<R, 1, 256, 0>(L, in, out, dagger, st); break;
+    case 3: launch_apply<R, 2, 64, 0>(L, in, out, dagger, st); break;
+    case 4: launch_apply<R, 2, 128, 0>(L, in, out, dagger, st); break;
+    case 5: launch_apply<R, 4, 64, 0>(L, in, out, dagger, st); break;
+    case 6: launch_apply<R, 4, 128, 0>(L, in, out, dagger, st); break;
+    case 7: launch_apply<R, 1, 512, 1>(L, in, out, dagger, st); break;
+    case 8: launch_apply<R, 2, 256, 1>(L, in, out, dagger, st); break;
+    default: launch_apply<R, 1, 128, 0>(L, in, out, dagger, st); break;
   }
 }
 
@@ -234,10 +259,10 @@ void tsl_init(const Lat<R>& L, cudaStream_t st) {
 // TSL step j: v_j = sv r_{j-1}, w_j = sw s_{j-1} stored in the bases;
 // p = H v_j, q = H^dag w_j; alpha_j = w_j^dag p.
 // ---------------------------------------------------------------------------
-template <typename R, int PAIR, int BSZ>
+template <typename R, int PAIR, int BSZ, int MAP>
 __global__ void __launch_bounds__(BSZ) k_tsl_stencil(Lat<R> L, int j, int need_q) {
   __shared__ zd scratch[32];
-  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t x = thread_site<MAP>(L.g);
   const int src = blockIdx.y;
   const int64_t V = L.g.V;
   const R* rp = L.r + src * L.vs;
@@ -294,18 +319,32 @@ __global__ void __launch_bounds__(BSZ) k_tsl_stencil(Lat<R> L, int j, int need_q
     }
   }
 }
-static const int kPairVariants[][2] = {{1, 128}, {1, 64}, {0, 128}, {0, 64}, {0, 256}};
+static const int kPairVariants[][3] = {{1, 128, 0}, {1, 64, 0}, {0, 128, 0}, {0, 64, 0}, {0, 256, 0},
+                                       {1, 256, 1}, {0, 512, 1}};
 int tsl_stencil_variants() { return (int)(sizeof(kPairVariants) / sizeof(kPairVariants[0])); }
+
+template <typename R, int PAIR, int BSZ, int MAP>
+static void launch_pair(const Lat<R>& L, int j, int q, cudaStream_t st) {
+  if (MAP == 1 && !plane_ok(L.g, BSZ)) {
+    launch_pair<R, PAIR, 128, 0>(L, j, q, st);
+    return;
+  }
+  const unsigned bs = MAP == 1 ? plane_threads(L.g) : BSZ;
+  const unsigned gx = MAP == 1 ? (unsigned)(L.g.V / (L.g.nx * L.g.ny)) : nblocks(L.g.V, BSZ);
+  k_tsl_stencil<R, PAIR, BSZ, MAP><<<dim3(gx, L.nsrc), bs, 0, st>>>(L, j, q);
+}
 
 template <typename R>
 void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st, int variant) {
   const int q = need_q ? 1 : 0;
   switch (variant) {
-    case 1: k_tsl_stencil<R, 1, 64><<<dim3(nblocks(L.g.V, 64), L.nsrc), 64, 0, st>>>(L, j, q); break;
-    case 2: k_tsl_stencil<R, 0, 128><<<dim3(nblocks(L.g.V, 128), L.nsrc), 128, 0, st>>>(L, j, q); break;
-    case 3: k_tsl_stencil<R, 0, 64><<<dim3(nblocks(L.g.V, 64), L.nsrc), 64, 0, st>>>(L, j, q); break;
-    case 4: k_tsl_stencil<R, 0, 256><<<dim3(nblocks(L.g.V, 256), L.nsrc), 256, 0, st>>>(L, j, q); break;
-    default: k_tsl_stencil<R, 1, 128><<<dim3(nblocks(L.g.V, 128), L.nsrc), 128, 0, st>>>(L, j, q); break;
+    case 1: launch_pair<R, 1, 64, 0>(L, j, q, st); break;
+    case 2: launch_pair<R, 0, 128, 0>(L, j, q, st); break;
+    case 3: launch_pair<R, 0, 64, 0>(L, j, q, st); break;
+    case 4: launch_pair<R, 0, 256, 0>(L, j, q, st); break;
+    case 5: launch_pair<R, 1, 256, 1>(L, j, q, st); break;
+    case 6: launch_pair<R, 0, 512, 1>(L, j, q, st); break;
+    default: launch_pair<R, 1, 128, 0>(L, j, q, st); break;
   }
 }
 

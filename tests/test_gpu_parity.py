@@ -74,14 +74,15 @@ def test_apply_h_single_source_shape():
     assert rel(got, dirac.apply_h(u, b[0], 0.1, -1.0)) <= 1e-13
 
 
+@pytest.mark.parametrize("dims", [(3, 5, 2, 4), (12, 6, 2, 3)])   # the second has 72-site x-y planes
 @pytest.mark.parametrize("precision,tol_h,tol_x", [("fp64", 1e-13, 1e-11), ("mixed", 2e-6, None)])
-def test_every_stencil_variant(precision, tol_h, tol_x):
+def test_every_stencil_variant(dims, precision, tol_h, tol_x):
     """Each compiled launch variant of both stencil kernels gives the oracle's result."""
-    dims, mu, m_w, k = (3, 5, 2, 4), 0.3, -1.0, 20
+    mu, m_w, k = 0.3, -1.0, 20
     u, b, _ = case(dims, 0.3, 8, 5)
     ut, bt = T(u), T(b)
     rep = binding.autotune(ut, mu, m_w, nsrc=5, precision=precision)
-    assert len(rep["apply_us"]) >= 7 and len(rep["pair_us"]) >= 5
+    assert len(rep["apply_us"]) >= 9 and len(rep["pair_us"]) >= 7
     refs = [tsl.tsl_forward(u, b[s], mu, m_w, k) for s in range(2)]
     for v in range(len(rep["apply_us"])):
         binding.set_stencil_variants(v, 0, precision)
