@@ -122,6 +122,37 @@ def apply_dh_dmu(u, psi, mu, m_w):
     return apply_gamma5(-kappa * (np.exp(mu) * g_plus - np.exp(-mu) * g_minus))
 
 
+def apply_dh_dmu_dagger(u, psi, mu, m_w):
+    """(dH/dmu)^dagger psi = (d D_w/dmu)^dagger gamma5 psi, from the explicit adjoint of
+    the temporal hops: (G_4^+)^dag psi (y) = (1+gamma_4) U_4(y-t)^dag psi(y-t) and
+    (G_4^-)^dag psi (y) = (1-gamma_4) U_4(y) psi(y+t)."""
+    kappa = kappa_of(m_w)
+    nu = 3
+    u_nu = u[..., nu, :, :]
+    phi = apply_gamma5(psi)
+    gp_dag = spin_mul(ID4 + GAMMA[nu], colour_mul_dag(shift(u_nu, nu, -1), shift(phi, nu, -1)))
+    gm_dag = spin_mul(ID4 - GAMMA[nu], colour_mul(u_nu, shift(phi, nu, +1)))
+    return -kappa * (np.exp(mu) * gp_dag - np.exp(-mu) * gm_dag)
+
+
+def apply_dh(u, e, psi, mu, m_w, m_dir):
+    """Directional derivative d/dt H(U + t E, mu + t m) psi at t = 0 (Eq. WD_op is affine
+    in the links, so the link part is the hopping part of D_w with E in place of U)."""
+    out = m_dir * apply_dh_dmu(u, psi, mu, m_w) if m_dir else np.zeros_like(psi)
+    if e is not None:
+        out = out + apply_gamma5(apply_dw(e, psi, mu, m_w) - psi)
+    return out
+
+
+def apply_dh_dagger(u, e, psi, mu, m_w, m_dir):
+    """Adjoint of ``apply_dh`` from the explicit adjoint of each term."""
+    out = m_dir * apply_dh_dmu_dagger(u, psi, mu, m_w) if m_dir else np.zeros_like(psi)
+    if e is not None:
+        phi = apply_gamma5(psi)
+        out = out + (apply_dw_dagger(e, phi, mu, m_w) - phi)
+    return out
+
+
 def link_gradient(a: np.ndarray, b: np.ndarray, u: np.ndarray, mu: float, m_w: float):
     """Contract a sum of rank-one terms g_H = sum_j a_j b_j^dagger into (dU, dmu).
 

@@ -77,9 +77,9 @@ def _round32(a):
 
 
 def tsl_forward(u, b, mu, m_w, k, rebiorth=1, passes=2, emulate_fp32=False) -> TSLResult:
+    """TSL for H(mu) = gamma5 D_w(mu) built from links u."""
     rnd = _round32 if emulate_fp32 else _identity
     uu = rnd(np.asarray(u, dtype=np.complex128))
-    b = np.asarray(b, dtype=np.complex128)
 
     def h(psi):
         return rnd(dirac.apply_h(uu, psi, mu, m_w))
@@ -87,9 +87,18 @@ def tsl_forward(u, b, mu, m_w, k, rebiorth=1, passes=2, emulate_fp32=False) -> T
     def hdag(psi):
         return rnd(dirac.apply_h_dagger(uu, psi, mu, m_w))
 
+    return tsl_forward_op(h, hdag, b, k, rebiorth, passes, rnd)
+
+
+def tsl_forward_op(h, hdag, b, k, rebiorth=1, passes=2, rnd=_identity, w1=None) -> TSLResult:
+    """The TSL recurrence above for any linear map given by h(psi) and hdag(psi).
+
+    The left start vector is w_1 = v_1 unless ``w1`` is given (it must satisfy
+    w1^dagger v_1 = 1)."""
+    b = np.asarray(b, dtype=np.complex128)
     beta0 = float(np.linalg.norm(b))
     v = [rnd(b / beta0)]
-    w = [v[0].copy()]
+    w = [v[0].copy() if w1 is None else np.asarray(w1, dtype=np.complex128)]
     alpha = np.zeros(k, dtype=np.complex128)
     beta = np.zeros(k, dtype=np.complex128)
     delta = np.zeros(k, dtype=np.float64)
@@ -153,3 +162,30 @@ def eps_a(u, b, mu, m_w, k, **kw) -> float:
     x1 = sign_apply(u, b, mu, m_w, k, **kw)
     x2 = sign_apply(u, x1, mu, m_w, k, **kw)
     return float(np.linalg.norm(x2 - b) / (2.0 * np.linalg.norm(b)))
+
+
+def block_tsl(u, b, mu, m_w, k, e=None, m_dir=0.0, rebiorth=1, passes=2):
+    """Theorem 1 (Sec. 2, Eq. func_derivative_1) with the TSL on the block matrix
+
+        B = [[H, dH], [0, H]],   dH = d/dt H(U + t E, mu + t m),
+
+    applied to (0, b): the top half approximates (d sgn(H)) b, the bottom half sgn(H) b.
+    Block vectors are stacked arrays (2, ...); B^dagger = [[H^dag, 0], [dH^dag, H^dag]].
+
+    Left start vector (the paper does not state it): w_1 = (b, b)/||b||, so that
+    w_1^dagger v_1 = 1.  With w_1 = v_1 = (0, b)/||b|| the left Krylov space of
+    B^dagger never leaves the lower half, T_k reduces to the plain TSL's and the
+    upper half is not a derivative.  Returns (dx, x, TSLResult)."""
+    def bh(z):
+        top = dirac.apply_h(u, z[0], mu, m_w) + dirac.apply_dh(u, e, z[1], mu, m_w, m_dir)
+        return np.stack([top, dirac.apply_h(u, z[1], mu, m_w)])
+
+    def bhdag(z):
+        bot = dirac.apply_dh_dagger(u, e, z[0], mu, m_w, m_dir) + dirac.apply_h_dagger(u, z[1], mu, m_w)
+        return np.stack([dirac.apply_h_dagger(u, z[0], mu, m_w), bot])
+
+    b = np.asarray(b, dtype=np.complex128)
+    src = np.stack([np.zeros_like(b), b])
+    w1 = np.stack([b, b]) / np.linalg.norm(b)
+    res = tsl_forward_op(bh, bhdag, src, k, rebiorth, passes, w1=w1)
+    return res.x[0], res.x[1], res
