@@ -132,6 +132,19 @@ int ov_autotune(ov_context *ctx, const int32_t dims[4], const void *U, double mu
  * reusing a tuning result. */
 int ov_set_stencil_variants(ov_context *ctx, int32_t apply_variant, int32_t pair_variant);
 
+/* Directional derivative by Theorem 1 (Sec. 2, Eq. func_derivative_1): TSL
+ * with k steps on the block matrix B = [[H, dH], [0, H]] applied to (0, b),
+ *   dH = d/dt H(U + t E, mu + t m_dir) at t = 0,
+ * returns dx ~ (d sgn(H)) b (upper half) and x ~ sgn(H) b (lower half).  E is a
+ * device array shaped like U (complex128; NULL for a pure mu direction).  The
+ * left Krylov space starts from (b, b)/||b|| (the paper does not state it; with
+ * w_1 = v_1 = (0, b)/||b|| the left space stays in the lower half and the
+ * upper half is not a derivative).  Fields are twice as long as in
+ * ov_tsl_sign, and the re-biorthogonalisation options apply to them. */
+int ov_tsl_sign_jvp(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                    int32_t nsrc, const void *b, int32_t k, const void *E, double m_dir, void *dx,
+                    void *x, ov_tsl_info *info);
+
 /* Recurrence coefficients of source `src` from the last ov_tsl_sign or
  * ov_tsl_sign_vjp call on this context (k must equal that call's k), copied
  * to HOST arrays: alpha[2k] and beta[2k] interleaved complex, delta[k].

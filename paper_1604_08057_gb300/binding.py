@@ -56,7 +56,7 @@ class Info(ctypes.Structure):
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
-           "ov_strerror"]
+           "ov_tsl_sign_jvp", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
     lib.ov_tsl_sign_vjp.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, P, P,
                                     ctypes.POINTER(D), ctypes.POINTER(Info)]
     lib.ov_tsl_coefficients.argtypes = [P, I32, I32, P, P, P]
+    lib.ov_tsl_sign_jvp.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, P, ctypes.POINTER(Info)]
     lib.ov_profile_enable.argtypes = [P, I32]
     lib.ov_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D), I32]
     lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
@@ -185,6 +186,28 @@ def tsl_sign_vjp(u, mu, m_w, b, k, xbar, precision="fp64", rebiorth=1, passes=2,
         x = x[0]
     out = (du, dmu.value, x)
     return out + (info.as_dict(),) if return_info else out
+
+
+def tsl_sign_jvp(u, mu, m_w, b, k, e=None, m_dir=0.0, precision="fp64", rebiorth=1, passes=2,
+                 return_info=False):
+    """Theorem 1: (dx, x) with dx ~ d/dt sgn(H(U + tE, mu + t m_dir)) b, x ~ sgn(H) b."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    if e is not None:
+        _dims(e)
+        e = e.contiguous()
+    x = torch.empty_like(bb)
+    dx = torch.empty_like(bb)
+    info = Info()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_tsl_sign_jvp(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
+                               _ptr(e) if e is not None else None, float(m_dir), _ptr(dx), _ptr(x),
+                               ctypes.byref(info)), "ov_tsl_sign_jvp")
+    if single:
+        dx, x = dx[0], x[0]
+    return (dx, x, info.as_dict()) if return_info else (dx, x)
 
 
 def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2):

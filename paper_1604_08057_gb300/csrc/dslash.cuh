@@ -247,6 +247,55 @@ OV_HD void force_half(const Spinor<R>& ax, const Spinor<R>& bxf, const Spinor<R>
   force_half_bwd<NU>(axf, bx, cb, G, Gd, with_d);
 }
 
+// Loader of one half of a block field: psi(off + s) in a field of Vf sites
+template <typename R>
+struct FieldLoadOff {
+  const R* f;
+  int64_t Vf, off;
+  OV_HD void operator()(int64_t s, Spinor<R>& o) const { load_spinor_ro(f, Vf, off + s, o); }
+};
+
+// Directional derivative of H along links E (ue, may be null) and mu (m):
+//   dH psi = gamma5 [ -kappa sum_nu (f_nu (1+g_nu) E_nu(x) psi(x+nu) + f_nu^-1 (1-g_nu) E_nu(x-nu)^dag psi(x-nu))
+//                     - kappa m (ft (1+g_4) U_4(x) psi(x+t) - ftinv (1-g_4) U_4(x-t)^dag psi(x-t)) ]
+// (Eq. WD_op is affine in the links).  (dH)^dagger is the same with ft and ftinv
+// exchanged and m -> -m.
+template <typename R, typename LD>
+OV_HD void dh_site_ld(const LD& ld, const R* ue, const R* u, const Geom& g, int64_t s, R kappa, R ft, R ftinv,
+                      R m, Spinor<R>& out) {
+  int c[4];
+  site_coords(g, s, c);
+  Spinor<R> acc;
+  spinor_zero(acc);
+  if (ue) {
+    hop_dir<0>(acc, ld, ue, g, s, c, ft, ftinv);
+    hop_dir<1>(acc, ld, ue, g, s, c, ft, ftinv);
+    hop_dir<2>(acc, ld, ue, g, s, c, ft, ftinv);
+    hop_dir<3>(acc, ld, ue, g, s, c, ft, ftinv);
+  }
+  if (m != R(0)) {
+    Spinor<R> nb;
+    Half<R> h, uh;
+    Mat3<R> lk;
+    const int64_t sf = neighbour(g, s, c, 3, +1);
+    ld(sf, nb);
+    spin_project<3, +1>(nb, h);
+    load_link(u, g.V, s, 3, lk);
+    link_mul(lk, h, uh);
+    spin_reconstruct_add<3, +1>(acc, uh, m * ft);
+    const int64_t sb = neighbour(g, s, c, 3, -1);
+    ld(sb, nb);
+    spin_project<3, -1>(nb, h);
+    load_link(u, g.V, sb, 3, lk);
+    link_dag_mul(lk, h, uh);
+    spin_reconstruct_add<3, -1>(acc, uh, -m * ftinv);
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) out.c[i] = -kappa * acc.c[i];
+#pragma unroll
+  for (int i = 6; i < 12; ++i) out.c[i] = kappa * acc.c[i];
+}
+
 // gamma5 (1 + sgn*gamma_nu) b, all four spins (used by the force contraction)
 template <int NU, int SGN, typename R>
 OV_HD void g5_proj_full(const Spinor<R>& b, Spinor<R>& o) {

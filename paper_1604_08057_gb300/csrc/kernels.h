@@ -42,6 +42,13 @@ struct Lat {
   zd* part;                  // reduction partials
   unsigned* cnt;             // last-block counters [src][16]
   int64_t part_stride;       // zd per source in `part`
+  // block mode (Theorem-1 block matrix [[H, dH], [0, H]]): every field holds the
+  // upper half at sites [0, V) and the lower half at [V, 2V) of a 2V-site field;
+  // g.V is then 2V (element-wise kernels), gl is the lattice itself.
+  int block;
+  Geom gl;
+  const R* ue;               // links of the direction E (internal layout) or null
+  R mdir;                    // mu direction
   OV_HD R* basis_v(int src, int j) const { return bv + ((int64_t)src * k + j) * vs; }
   OV_HD R* basis_w(int src, int j) const { return bw + ((int64_t)src * k + j) * vs; }
 };
@@ -70,6 +77,9 @@ struct Rev {
 
 // ---- lattice launchers (precision R = double or float) ----
 template <typename R> void pack_spinors(const double* src_aos, R* dst, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
+// pack V sites into sites [off, off + V) of fields of Vf sites
+template <typename R> void pack_spinors_off(const double* src_aos, R* dst, int nsrc, int64_t V, int64_t Vf,
+                                            int64_t off, int64_t vs, cudaStream_t st);
 template <typename R> void unpack_spinors(const R* src, double* dst_aos, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
 template <typename R> void pack_links(const double* src_aos, R* dst, int64_t V, cudaStream_t st);
 // launch variants of the two stencil kernels (chosen by the autotuner; 0 = default)

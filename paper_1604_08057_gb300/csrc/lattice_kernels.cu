@@ -49,6 +49,19 @@ __global__ void k_pack_spinors(const double* __restrict__ aos, R* __restrict__ d
 }
 
 template <typename R>
+__global__ void k_pack_spinors_off(const double* __restrict__ aos, R* __restrict__ dst, int64_t V, int64_t Vf,
+                                   int64_t off, int64_t vs) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  if (x >= V) return;
+  const double2* in = reinterpret_cast<const double2*>(aos) + ((int64_t)src * V + x) * 12;
+  Spinor<R> o;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) { double2 t = in[c]; o.c[c] = mk<R>((R)t.x, (R)t.y); }
+  store_spinor(dst + src * vs, Vf, off + x, o);
+}
+
+template <typename R>
 __global__ void k_unpack_spinors(const R* __restrict__ f, double* __restrict__ aos, int64_t V, int64_t vs) {
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int src = blockIdx.y;
@@ -93,6 +106,11 @@ __global__ void k_unpack_force(const double* __restrict__ f, double* __restrict_
 template <typename R>
 void pack_spinors(const double* aos, R* dst, int nsrc, int64_t V, int64_t vs, cudaStream_t st) {
   k_pack_spinors<R><<<dim3(nblocks(V, BS), nsrc), BS, 0, st>>>(aos, dst, V, vs);
+}
+template <typename R>
+void pack_spinors_off(const double* aos, R* dst, int nsrc, int64_t V, int64_t Vf, int64_t off, int64_t vs,
+                      cudaStream_t st) {
+  k_pack_spinors_off<R><<<dim3(nblocks(V, BS), nsrc), BS, 0, st>>>(aos, dst, V, Vf, off, vs);
 }
 template <typename R>
 void unpack_spinors(const R* f, double* aos, int nsrc, int64_t V, int64_t vs, cudaStream_t st) {
@@ -319,6 +337,78 @@ __global__ void __launch_bounds__(BSZ) k_tsl_stencil(Lat<R> L, int j, int need_q
     }
   }
 }
+// Block TSL step (Theorem 1): with r = (r_u, r_l), s = (s_u, s_l) in 2V-site fields,
+//   v_j = sv r, w_j = sw s,
+//   p = sv (H r_u + dH r_l, H r_l),   q = sw (H^dag s_u, dH^dag s_u + H^dag s_l),
+//   alpha_j = w_j^dag p  (over both halves).  One thread per lattice site.
+template <typename R>
+__global__ void __launch_bounds__(BS) k_tsl_stencil_block(Lat<R> L, int j, int need_q) {
+  __shared__ zd scratch[32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t Vr = L.gl.V, Vf = L.g.V;
+  const R* rp = L.r + src * L.vs;
+  const R* sp = L.s + src * L.vs;
+  zd v[1] = {mk(0.0, 0.0)};
+  if (x < Vr && L.sc[src].err == 0) {
+    const cplx<R> sv = cast<R>(L.sc[src].sv), sw = cast<R>(L.sc[src].sw);
+    Spinor<R> a;
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      load_spinor(rp, Vf, hf * Vr + x, a);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) a.c[c] = sv * a.c[c];
+      store_spinor(L.basis_v(src, j), Vf, hf * Vr + x, a);
+      load_spinor(sp, Vf, hf * Vr + x, a);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) a.c[c] = sw * a.c[c];
+      store_spinor(L.basis_w(src, j), Vf, hf * Vr + x, a);
+    }
+    {
+      const FieldLoadOff<R> ld[2] = {FieldLoadOff<R>{rp, Vf, 0}, FieldLoadOff<R>{rp, Vf, Vr}};
+      const R ft[2] = {L.ef, L.ef}, fti[2] = {L.efinv, L.efinv};
+      Spinor<R> hh[2], d;
+      h_site_multi<2>(ld, L.u, L.gl, x, L.kappa, ft, fti, hh);
+      dh_site_ld(ld[1], L.ue, L.u, L.gl, x, L.kappa, L.ef, L.efinv, L.mdir, d);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) hh[0].c[c] = sv * (hh[0].c[c] + d.c[c]);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) hh[1].c[c] = sv * hh[1].c[c];
+      store_spinor(L.p + src * L.vs, Vf, x, hh[0]);
+      store_spinor(L.p + src * L.vs, Vf, Vr + x, hh[1]);
+      load_spinor(L.basis_w(src, j), Vf, x, a);
+      v[0] = spinor_dot(a, hh[0]);
+      load_spinor(L.basis_w(src, j), Vf, Vr + x, a);
+      v[0] = v[0] + spinor_dot(a, hh[1]);
+    }
+    if (need_q) {
+      const FieldLoadOff<R> ld[2] = {FieldLoadOff<R>{sp, Vf, 0}, FieldLoadOff<R>{sp, Vf, Vr}};
+      const R ft[2] = {L.efinv, L.efinv}, fti[2] = {L.ef, L.ef};
+      Spinor<R> hh[2], d;
+      h_site_multi<2>(ld, L.u, L.gl, x, L.kappa, ft, fti, hh);
+      dh_site_ld(ld[0], L.ue, L.u, L.gl, x, L.kappa, L.efinv, L.ef, -L.mdir, d);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) hh[0].c[c] = sw * hh[0].c[c];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) hh[1].c[c] = sw * (hh[1].c[c] + d.c[c]);
+      store_spinor(L.q + src * L.vs, Vf, x, hh[0]);
+      store_spinor(L.q + src * L.vs, Vf, Vr + x, hh[1]);
+    }
+  }
+  block_sum<1>(v, scratch);
+  zd* part = L.part + src * L.part_stride;
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (arrive_last(L.cnt + src * 16 + 1, gridDim.x)) {
+    zd s1[1];
+    sum_partials<1>(part, gridDim.x, s1, scratch);
+    if (threadIdx.x == 0) {
+      SrcScal& sc = L.sc[src];
+      if (!finite_z(s1[0])) flag_error(sc, ERRB_NONFINITE, j);
+      L.alpha[(int64_t)src * L.k + j] = s1[0];
+    }
+  }
+}
+
 static const int kPairVariants[][3] = {{1, 128, 0}, {1, 64, 0}, {0, 128, 0}, {0, 64, 0}, {0, 256, 0},
                                        {1, 256, 1}, {0, 512, 1}};
 int tsl_stencil_variants() { return (int)(sizeof(kPairVariants) / sizeof(kPairVariants[0])); }
@@ -337,6 +427,10 @@ static void launch_pair(const Lat<R>& L, int j, int q, cudaStream_t st) {
 template <typename R>
 void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st, int variant) {
   const int q = need_q ? 1 : 0;
+  if (L.block) {
+    k_tsl_stencil_block<R><<<dim3(nblocks(L.gl.V, BS), L.nsrc), BS, 0, st>>>(L, j, q);
+    return;
+  }
   switch (variant) {
     case 1: launch_pair<R, 1, 64, 0>(L, j, q, st); break;
     case 2: launch_pair<R, 0, 128, 0>(L, j, q, st); break;
@@ -1022,6 +1116,8 @@ void force_flush(const Lat<R>& L, const Rev<R>& B, const int* /*unused*/, int nt
 // explicit instantiations
 #define OV_INST(R)                                                                                        \
   template void pack_spinors<R>(const double*, R*, int, int64_t, int64_t, cudaStream_t);                 \
+  template void pack_spinors_off<R>(const double*, R*, int, int64_t, int64_t, int64_t, int64_t,            \
+                                    cudaStream_t);                                                       \
   template void unpack_spinors<R>(const R*, double*, int, int64_t, int64_t, cudaStream_t);               \
   template void pack_links<R>(const double*, R*, int64_t, cudaStream_t);                                 \
   template void apply_h<R>(const Lat<R>&, const R*, R*, int, cudaStream_t, int);                         \

@@ -17,7 +17,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, NBUF
 };
 
 struct Status {
@@ -114,7 +114,11 @@ void* ws(ov_context* c, int id, size_t bytes, bool zero = false) {
       throw Status{OV_ERR_OOM};
     }
     c->cap[id] = nb;
-    zero = true;   // counters and accumulators start at zero
+    // The whole capacity starts at zero, not only the bytes asked for now: ticket
+    // counters rely on it when a later call (more sources) uses more of the buffer
+    // without reallocating it.
+    CK(cudaMemsetAsync(c->buf[id], 0, nb, c->st));
+    return c->buf[id];
   }
   if (zero) CK(cudaMemsetAsync(c->buf[id], 0, bytes, c->st));
   return c->buf[id];
@@ -139,11 +143,13 @@ Geom make_geom(const int32_t dims[4]) {
   return g;
 }
 
+// fm = 2 sets up block mode: fields of 2V sites (upper and lower halves)
 template <typename R>
 Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc, int k,
-             bool basis) {
+             bool basis, int fm = 1) {
   Lat<R> L{};
   L.g = make_geom(dims);
+  L.gl = L.g;
   if (nsrc < 1 || nsrc > 4096) throw Status{OV_ERR_INVALID_ARG};
   if (!(std::isfinite(mu) && std::isfinite(m_w)) || 2.0 * m_w + 8.0 == 0.0) throw Status{OV_ERR_INVALID_ARG};
   check_ptr(U);
@@ -158,6 +164,12 @@ Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, dou
   L.u = u;
   run(c, OV_KIND_LAYOUT, 1, [&] { pack_links<R>(static_cast<const double*>(U), u, V, c->st); });
   launch_check();
+  if (fm == 2) {
+    L.block = 1;
+    L.g.V = 2 * V;
+    L.vs = ((48 * V + 63) / 64) * 64;
+  }
+  const int64_t Vf = L.g.V;
   if (basis) {
     L.bv = wsT<R>(c, B_BV, (int64_t)nsrc * k * L.vs);
     L.bw = wsT<R>(c, B_BW, (int64_t)nsrc * k * L.vs);
@@ -170,7 +182,7 @@ Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, dou
   L.alpha = wsT<zd>(c, B_ALPHA, (int64_t)nsrc * k);
   L.beta = wsT<zd>(c, B_BETA, (int64_t)nsrc * k);
   L.delta = wsT<double>(c, B_DELTA, (int64_t)nsrc * k);
-  const int64_t nblk = (V + 127) / 128;
+  const int64_t nblk = (Vf + 127) / 128;
   L.part_stride = 8 * (nblk < 64 ? 64 : nblk);
   L.part = wsT<zd>(c, B_PART, nsrc * L.part_stride);
   L.cnt = wsT<unsigned>(c, B_CNT, (int64_t)nsrc * 16);
@@ -356,6 +368,67 @@ int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   CK(cudaEventRecord(c->ev[2], c->st));
   run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
   launch_check();
+  CK(cudaEventRecord(c->ev[3], c->st));
+  CK(cudaStreamSynchronize(c->st));
+  prof_collect(c);
+  if (info) {
+    info->newton_iters = iters;
+    info->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
+    info->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
+    info->t_ms[2] = elapsed(c->ev[2], c->ev[3]);
+  }
+  return OV_OK;
+}
+
+// Theorem 1: TSL on B = [[H, dH], [0, H]] from (0, b) with left start (b, b)/||b||
+template <typename R>
+int tsl_jvp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                 const void* b, int k, const void* E, double m_dir, void* dx, void* x, ov_tsl_info* info) {
+  check_ptr(b);
+  check_ptr(x);
+  check_ptr(dx);
+  if (E) check_ptr(E);
+  if (!std::isfinite(m_dir)) throw Status{OV_ERR_INVALID_ARG};
+  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true, 2);
+  const int64_t V = L.gl.V, Vf = L.g.V;
+  if (E) {
+    R* ue = wsT<R>(c, B_ELINKS, link_reals<R>() * V);
+    run(c, OV_KIND_LAYOUT, 1, [&] { pack_links<R>(static_cast<const double*>(E), ue, V, c->st); });
+    L.ue = ue;
+  }
+  L.mdir = (R)m_dir;
+  const double* bd = static_cast<const double*>(b);
+  CK(cudaMemsetAsync(L.r, 0, sizeof(R) * nsrc * L.vs, c->st));
+  run(c, OV_KIND_LAYOUT, 3, [&] {
+    pack_spinors_off<R>(bd, L.r, nsrc, V, Vf, V, L.vs, c->st);   // r = (0, b)
+    pack_spinors_off<R>(bd, L.s, nsrc, V, Vf, 0, L.vs, c->st);   // s = (b, b)
+    pack_spinors_off<R>(bd, L.s, nsrc, V, Vf, V, L.vs, c->st);
+  });
+  CK(cudaEventRecord(c->ev[0], c->st));
+  forward_krylov(c, L);
+  CK(cudaEventRecord(c->ev[1], c->st));
+  auto hsc = read_scalars(c, L.sc, nsrc);
+  int kr = k;
+  int st = scalar_status(hsc, &kr, k);
+  c->last_k = k;
+  c->last_nsrc = nsrc;
+  if (info) info->k_reached = kr;
+  if (st != OV_OK) return st;
+  zd* y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
+  int iters = 0;
+  st = sign_all(c, L, hsc, y, &iters);
+  if (st != OV_OK) return st;
+  CK(cudaEventRecord(c->ev[2], c->st));
+  double* out = wsT<double>(c, B_BLOCKOUT, (int64_t)nsrc * Vf * 24);
+  run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, out, c->st); });
+  launch_check();
+  const size_t half = (size_t)V * 24 * sizeof(double);
+  for (int src = 0; src < nsrc; ++src) {
+    CK(cudaMemcpyAsync(static_cast<char*>(dx) + src * half, out + (int64_t)src * Vf * 24, half,
+                       cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(static_cast<char*>(x) + src * half, out + (int64_t)src * Vf * 24 + V * 24, half,
+                       cudaMemcpyDeviceToDevice, c->st));
+  }
   CK(cudaEventRecord(c->ev[3], c->st));
   CK(cudaStreamSynchronize(c->st));
   prof_collect(c);
@@ -798,6 +871,17 @@ int ov_set_stencil_variants(ov_context* c, int32_t apply_variant, int32_t pair_v
   c->tuned_apply[c->opt.precision] = apply_variant;
   c->tuned_pair[c->opt.precision] = pair_variant;
   return OV_OK;
+}
+
+int ov_tsl_sign_jvp(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                    const void* b, int32_t k, const void* E, double m_dir, void* dx, void* x, ov_tsl_info* info) {
+  if (!c || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? tsl_jvp_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, E, m_dir, dx, x, info)
+               : tsl_jvp_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, E, m_dir, dx, x, info);
+  });
 }
 
 int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, double* beta, double* delta) {

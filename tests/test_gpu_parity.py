@@ -130,6 +130,24 @@ def test_tsl_forward_batched_sources_and_k2():
             assert rel(x[s], ref.x) <= 1e-11, (k, s, rel(x[s], ref.x))
 
 
+def test_growing_source_count_on_one_context():
+    """A call with more sources than the context has seen reuses workspace buffers
+    whose capacity already covers it: their unused part must start at zero (ticket
+    counters).  Device memory is dirtied first so that stale bytes would show."""
+    junk = torch.full((64 << 20,), -1, dtype=torch.int32, device=DEV)
+    del junk
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    dims, mu, m_w = (3, 5, 2, 4), 0.3, -1.0
+    u, b, _ = case(dims, 0.3, 12, 3)
+    reb, passes = 7, 1                     # options no other test uses: a fresh context
+    for nsrc, k in ((1, 24), (3, 24), (2, 30)):
+        x = binding.tsl_sign(T(u), mu, m_w, T(b[:nsrc]), k, rebiorth=reb, passes=passes).cpu().numpy()
+        for s in range(nsrc):
+            ref = tsl.tsl_forward(u, b[s], mu, m_w, k, rebiorth=reb, passes=passes)
+            assert rel(x[s], ref.x) <= 1e-11, (nsrc, s, rel(x[s], ref.x))
+
+
 def test_tsl_forward_mixed_precision():
     """FP32 vectors: compared with the FP64 oracle to 2x the error of the oracle's own FP32 emulation."""
     dims, mu, m_w, k = (3, 3, 3, 3), 0.3, -1.0, 60
@@ -216,3 +234,38 @@ def test_invalid_arguments_and_breakdown():
     with pytest.raises(binding.OVError) as e:
         binding.tsl_sign(T(uf), 0.0, -1.0, T(bf), 5, rebiorth=0)
     assert e.value.status == -3
+
+
+# ---------------------------------------------------------------------------
+# Theorem 1: TSL on the block matrix [[H, dH], [0, H]]
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,m_w,k,reb,with_e,m_dir,tol", [
+    ((3, 3, 3, 3), -1.0, 60, 1, True, 0.7, 1e-10),
+    ((3, 5, 2, 4), -1.0, 50, 10, True, 0.0, 1e-10),
+    ((3, 3, 2, 3), -1.0, 40, 1, False, 1.0, 1e-10),     # mu direction only
+    ((4, 4, 4, 4), -2.0, 120, 1, True, 0.3, 1e-7),      # the 4x4^3 physics point
+])
+def test_block_tsl_jvp_fp64(dims, m_w, k, reb, with_e, m_dir, tol):
+    rng = np.random.default_rng(71)
+    u = inputs.su3_links(dims, 0.3, rng)
+    b = inputs.gaussian_spinors(dims, 2, rng)
+    e = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape) if with_e else None
+    mu = 0.3
+    dx, x = binding.tsl_sign_jvp(T(u), mu, m_w, T(b), k, T(e) if with_e else None, m_dir, rebiorth=reb)
+    dx, x = dx.cpu().numpy(), x.cpu().numpy()
+    for s in range(2):
+        rdx, rx, _ = tsl.block_tsl(u, b[s], mu, m_w, k, e, m_dir, rebiorth=reb)
+        assert rel(dx[s], rdx) <= tol, (s, rel(dx[s], rdx))
+        assert rel(x[s], rx) <= tol, (s, rel(x[s], rx))
+
+
+def test_block_tsl_jvp_mixed_well_conditioned():
+    dims, m_w, k, mu = (3, 3, 3, 3), -1.0, 60, 0.3
+    rng = np.random.default_rng(72)
+    u = inputs.su3_links(dims, 0.3, rng)
+    b = inputs.gaussian_spinors(dims, 1, rng)[0]
+    e = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape)
+    dx, x = binding.tsl_sign_jvp(T(u), mu, m_w, T(b), k, T(e), 0.5, precision="mixed")
+    rdx, rx, _ = tsl.block_tsl(u, b, mu, m_w, k, e, 0.5)
+    assert rel(dx.cpu().numpy(), rdx) <= 1e-4
+    assert rel(x.cpu().numpy(), rx) <= 1e-4
