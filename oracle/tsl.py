@@ -164,28 +164,51 @@ def eps_a(u, b, mu, m_w, k, **kw) -> float:
     return float(np.linalg.norm(x2 - b) / (2.0 * np.linalg.norm(b)))
 
 
-def block_tsl(u, b, mu, m_w, k, e=None, m_dir=0.0, rebiorth=1, passes=2):
-    """Theorem 1 (Sec. 2, Eq. func_derivative_1) with the TSL on the block matrix
+def block_tsl_start(u, top, bottom, mu, m_w, k, e=None, m_dir=0.0, rebiorth=1, passes=2):
+    """The TSL on the block matrix of Theorem 1 (Sec. 2, Eq. func_derivative_1)
 
         B = [[H, dH], [0, H]],   dH = d/dt H(U + t E, mu + t m),
 
-    applied to (0, b): the top half approximates (d sgn(H)) b, the bottom half sgn(H) b.
-    Block vectors are stacked arrays (2, ...); B^dagger = [[H^dag, 0], [dH^dag, H^dag]].
+    started from the block vector (top, bottom); returns the two halves of the
+    approximation of sgn(B) (top, bottom) and the TSLResult.  Block vectors are
+    stacked arrays (2, ...); B^dagger = [[H^dag, 0], [dH^dag, H^dag]].
 
-    Left start vector (the paper does not state it): w_1 = (b, b)/||b||, so that
-    w_1^dagger v_1 = 1.  With w_1 = v_1 = (0, b)/||b|| the left Krylov space of
-    B^dagger never leaves the lower half, T_k reduces to the plain TSL's and the
-    upper half is not a derivative.  Returns (dx, x, TSLResult)."""
+    Left start vector (the paper does not state it): w_1 proportional to
+    (top + bottom, bottom), scaled so that w_1^dagger v_1 = 1.  For (0, b) this is
+    (b, b)/||b||.  With w_1 = v_1 = (0, b)/||b|| the left Krylov space of B^dagger
+    never leaves the lower half, T_k reduces to the plain TSL's and the upper half
+    is not a derivative.  Re(s^dagger r) >= (||top||^2 + ||bottom||^2)/2 for
+    s = (top + bottom, bottom), r = (top, bottom), so the start never breaks down."""
     def bh(z):
-        top = dirac.apply_h(u, z[0], mu, m_w) + dirac.apply_dh(u, e, z[1], mu, m_w, m_dir)
-        return np.stack([top, dirac.apply_h(u, z[1], mu, m_w)])
+        top_ = dirac.apply_h(u, z[0], mu, m_w) + dirac.apply_dh(u, e, z[1], mu, m_w, m_dir)
+        return np.stack([top_, dirac.apply_h(u, z[1], mu, m_w)])
 
     def bhdag(z):
         bot = dirac.apply_dh_dagger(u, e, z[0], mu, m_w, m_dir) + dirac.apply_h_dagger(u, z[1], mu, m_w)
         return np.stack([dirac.apply_h_dagger(u, z[0], mu, m_w), bot])
 
-    b = np.asarray(b, dtype=np.complex128)
-    src = np.stack([np.zeros_like(b), b])
-    w1 = np.stack([b, b]) / np.linalg.norm(b)
-    res = tsl_forward_op(bh, bhdag, src, k, rebiorth, passes, w1=w1)
+    top = np.asarray(top, dtype=np.complex128)
+    bottom = np.asarray(bottom, dtype=np.complex128)
+    r = np.stack([top, bottom])
+    sl = np.stack([top + bottom, bottom])
+    beta0 = np.linalg.norm(r)
+    w1 = sl * (beta0 / np.conj(np.vdot(sl, r)))
+    res = tsl_forward_op(bh, bhdag, r, k, rebiorth, passes, w1=w1)
     return res.x[0], res.x[1], res
+
+
+def block_tsl(u, b, mu, m_w, k, e=None, m_dir=0.0, rebiorth=1, passes=2):
+    """Theorem 1 applied to (0, b): the top half approximates (d sgn(H)) b along
+    (E, m), the bottom half sgn(H) b.  Returns (dx, x, TSLResult)."""
+    b = np.asarray(b, dtype=np.complex128)
+    return block_tsl_start(u, np.zeros_like(b), b, mu, m_w, k, e, m_dir, rebiorth, passes)
+
+
+def eps_b(u, b, mu, m_w, k, e=None, m_dir=0.0, **kw) -> float:
+    """A-posteriori error estimate of the derivative (Sec. 4.1, Eq. bA_error_est):
+    ||sgn(B)^2 (0, b) - (0, b)|| / (2 ||b||), each sign by its own block TSL run."""
+    dx, x, _ = block_tsl(u, b, mu, m_w, k, e, m_dir, **kw)
+    zt, zb, _ = block_tsl_start(u, dx, x, mu, m_w, k, e, m_dir, **kw)
+    b = np.asarray(b, dtype=np.complex128)
+    num = np.sqrt(np.linalg.norm(zt) ** 2 + np.linalg.norm(zb - b) ** 2)
+    return float(num / (2.0 * np.linalg.norm(b)))

@@ -79,3 +79,40 @@ def test_block_tsl_left_start_reading():
     _, _, res = tsl.block_tsl(u, b, mu, m_w, k, e, 0.5)
     plain = tsl.tsl_forward(u, b, mu, m_w, k)
     assert np.abs(res.alpha - plain.alpha).max() > 1e-3
+
+
+@pytest.mark.parametrize("m_w", [-1.0, -2.0])
+def test_block_tsl_from_a_general_start_is_exact_at_full_dimension(m_w):
+    """sgn(B) (t, l) = (sgn(H) t + L_sgn(H, dH) l, sgn(H) l) (Theorem 1) at k = 2n."""
+    dims = (2, 2, 2, 2)
+    u, b, e, rng = _setup(dims, 65)
+    t = inputs.gaussian_spinors(dims, 1, rng)[0]
+    mu, m = 0.3, 0.7
+    hm = dense_from_apply(lambda p: dirac.apply_h(u, p, mu, m_w), b.shape)
+    dhm = dense_from_apply(lambda p: dirac.apply_dh(u, e, p, mu, m_w, m), b.shape)
+    s = sign_eig(hm)
+    want_top = s @ t.ravel() + frechet_sign_daleckii_krein(hm, dhm) @ b.ravel()
+    want_bot = s @ b.ravel()
+    zt, zb, _ = tsl.block_tsl_start(u, t, b, mu, m_w, 2 * b.size, e, m)
+    assert np.linalg.norm(zt.ravel() - want_top) <= 1e-8 * np.linalg.norm(want_top)
+    assert np.linalg.norm(zb.ravel() - want_bot) <= 1e-8 * np.linalg.norm(want_bot)
+
+
+def test_eps_b_vanishes_at_full_dimension_and_decreases_with_k():
+    dims = (2, 2, 2, 2)
+    u, b, e, _ = _setup(dims, 66)
+    mu, m_w, m = 0.3, -1.0, 0.7
+    eps = [tsl.eps_b(u, b, mu, m_w, k, e, m) for k in (40, 120, 2 * b.size)]
+    assert eps[0] > eps[1] > eps[2] and eps[2] < 1e-9, eps
+
+
+def test_eps_b_reduces_to_eps_a_without_a_direction():
+    """With dH = 0 the block matrix is diag(H, H): started from (0, b) the right
+    space stays in the lower half and T_k is the plain TSL's, so the block estimate
+    of Eq. bA_error_est equals eps_A of Eq. error_est."""
+    dims = (2, 2, 2, 2)
+    u, b, _, _ = _setup(dims, 67)
+    mu, m_w, k = 0.3, -1.0, 50
+    ea = tsl.eps_a(u, b, mu, m_w, k)
+    eb = tsl.eps_b(u, b, mu, m_w, k, None, 0.0)
+    assert ea > 1e-6 and abs(eb - ea) <= 1e-9 * ea, (ea, eb)
