@@ -132,18 +132,42 @@ int ov_autotune(ov_context *ctx, const int32_t dims[4], const void *U, double mu
  * reusing a tuning result. */
 int ov_set_stencil_variants(ov_context *ctx, int32_t apply_variant, int32_t pair_variant);
 
-/* Directional derivative by Theorem 1 (Sec. 2, Eq. func_derivative_1): TSL
- * with k steps on the block matrix B = [[H, dH], [0, H]] applied to (0, b),
- *   dH = d/dt H(U + t E, mu + t m_dir) at t = 0,
- * returns dx ~ (d sgn(H)) b (upper half) and x ~ sgn(H) b (lower half).  E is a
- * device array shaped like U (complex128; NULL for a pure mu direction).  The
- * left Krylov space starts from (b, b)/||b|| (the paper does not state it; with
- * w_1 = v_1 = (0, b)/||b|| the left space stays in the lower half and the
- * upper half is not a derivative).  Fields are twice as long as in
- * ov_tsl_sign, and the re-biorthogonalisation options apply to them. */
+/* Theorem 1 (Sec. 2, Eq. func_derivative_1): k-step TSL on the block matrix
+ *   B = [[H, dH], [0, H]],   dH = d/dt H(U + t E, mu + t m_dir) at t = 0,
+ * started from the block vector (top, bottom); out_top and out_bottom receive
+ * the two halves of the approximation of sgn(B) (top, bottom), which are
+ *   sgn(H) top + (d sgn(H)) bottom   and   sgn(H) bottom.
+ * top, bottom, out_top, out_bottom: device arrays of nsrc spinor fields each
+ * (complex128, user layout); top may be NULL (zero).  E: device array shaped
+ * like U (complex128; NULL for a pure mu direction).  The left Krylov space
+ * starts from w_1 proportional to (top + bottom, bottom) with w_1^dag v_1 = 1
+ * (the paper does not state it; with w_1 = v_1 = (0, b)/||b|| the left space
+ * stays in the lower half and the upper half is not a derivative).  Internal
+ * fields are twice as long as in ov_tsl_sign; the re-biorthogonalisation
+ * options apply to them.  Errors as ov_tsl_sign. */
+int ov_block_tsl_sign(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                      int32_t nsrc, const void *top, const void *bottom, int32_t k, const void *E,
+                      double m_dir, void *out_top, void *out_bottom, ov_tsl_info *info);
+
+/* Directional derivative by Theorem 1: ov_block_tsl_sign from (0, b), so
+ * dx ~ (d sgn(H)) b along (E, m_dir) and x ~ sgn(H) b. */
 int ov_tsl_sign_jvp(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
                     int32_t nsrc, const void *b, int32_t k, const void *E, double m_dir, void *dx,
                     void *x, ov_tsl_info *info);
+
+/* A-posteriori error estimates of Sec. 4.1.  The sign is applied twice, each
+ * time by its own k-step TSL (the second starts from the first's result), and
+ * eps[src] (host array of nsrc doubles) receives per source
+ *   ov_tsl_eps:        ||sgn(H)^2 b - b|| / (2 ||b||)                (Eq. error_est)
+ *   ov_block_tsl_eps:  ||sgn(B)^2 (0, b) - (0, b)|| / (2 ||b||)       (Eq. bA_error_est)
+ * with B, E and m_dir as in ov_block_tsl_sign.  The norms are reduced on the
+ * device in FP64.  info: k_reached is the smaller, newton_iters the larger of
+ * the two runs, t_ms their sums.  Errors as ov_tsl_sign. */
+int ov_tsl_eps(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w, int32_t nsrc,
+               const void *b, int32_t k, double *eps, ov_tsl_info *info);
+int ov_block_tsl_eps(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                     int32_t nsrc, const void *b, int32_t k, const void *E, double m_dir, double *eps,
+                     ov_tsl_info *info);
 
 /* Recurrence coefficients of source `src` from the last ov_tsl_sign or
  * ov_tsl_sign_vjp call on this context (k must equal that call's k), copied

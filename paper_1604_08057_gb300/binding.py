@@ -56,7 +56,7 @@ class Info(ctypes.Structure):
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
-           "ov_tsl_sign_jvp", "ov_strerror"]
+           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -81,6 +81,9 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(D), ctypes.POINTER(Info)]
     lib.ov_tsl_coefficients.argtypes = [P, I32, I32, P, P, P]
     lib.ov_tsl_sign_jvp.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, P, ctypes.POINTER(Info)]
+    lib.ov_block_tsl_sign.argtypes = [P, dims_t, P, D, D, I32, P, P, I32, P, D, P, P, ctypes.POINTER(Info)]
+    lib.ov_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, ctypes.POINTER(Info)]
+    lib.ov_block_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, ctypes.POINTER(Info)]
     lib.ov_profile_enable.argtypes = [P, I32]
     lib.ov_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D), I32]
     lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
@@ -208,6 +211,69 @@ def tsl_sign_jvp(u, mu, m_w, b, k, e=None, m_dir=0.0, precision="fp64", rebiorth
     if single:
         dx, x = dx[0], x[0]
     return (dx, x, info.as_dict()) if return_info else (dx, x)
+
+
+def block_tsl_sign(u, mu, m_w, top, bottom, k, e=None, m_dir=0.0, precision="fp64", rebiorth=1, passes=2,
+                   return_info=False):
+    """Theorem 1 from a general block start: the halves of sgn(B) (top, bottom),
+    B = [[H, dH], [0, H]]; top may be None (zero)."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(bottom, u)
+    tt = None
+    if top is not None:
+        tt, single_t = _spinors(top, u)
+        if tt.shape != bb.shape:
+            raise ValueError("top and bottom must have the same shape")
+    if e is not None:
+        _dims(e)
+        e = e.contiguous()
+    zt = torch.empty_like(bb)
+    zb = torch.empty_like(bb)
+    info = Info()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_block_tsl_sign(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0],
+                                 _ptr(tt) if tt is not None else None, _ptr(bb), int(k),
+                                 _ptr(e) if e is not None else None, float(m_dir), _ptr(zt), _ptr(zb),
+                                 ctypes.byref(info)), "ov_block_tsl_sign")
+    if single:
+        zt, zb = zt[0], zb[0]
+    return (zt, zb, info.as_dict()) if return_info else (zt, zb)
+
+
+def tsl_eps(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2):
+    """eps_A = ||sgn(H)^2 b - b|| / (2 ||b||) per source (Sec. 4.1, Eq. error_est)."""
+    import numpy as np
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    eps = np.zeros(bb.shape[0], dtype=np.float64)
+    info = Info()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_tsl_eps(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
+                          eps.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info)), "ov_tsl_eps")
+    return float(eps[0]) if single else eps
+
+
+def block_tsl_eps(u, mu, m_w, b, k, e=None, m_dir=0.0, precision="fp64", rebiorth=1, passes=2):
+    """eps_B = ||sgn(B)^2 (0, b) - (0, b)|| / (2 ||b||) per source (Sec. 4.1, Eq. bA_error_est)."""
+    import numpy as np
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    if e is not None:
+        _dims(e)
+        e = e.contiguous()
+    eps = np.zeros(bb.shape[0], dtype=np.float64)
+    info = Info()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_block_tsl_eps(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
+                                _ptr(e) if e is not None else None, float(m_dir),
+                                eps.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info)), "ov_block_tsl_eps")
+    return float(eps[0]) if single else eps
 
 
 def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2):

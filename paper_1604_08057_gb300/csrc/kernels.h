@@ -78,8 +78,8 @@ struct Rev {
 // ---- lattice launchers (precision R = double or float) ----
 template <typename R> void pack_spinors(const double* src_aos, R* dst, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
 // pack V sites into sites [off, off + V) of fields of Vf sites
-template <typename R> void pack_spinors_off(const double* src_aos, R* dst, int nsrc, int64_t V, int64_t Vf,
-                                            int64_t off, int64_t vs, cudaStream_t st);
+template <typename R> void pack_block_start(const double* top_aos, const double* bot_aos, R* r, R* s, int nsrc,
+                                            int64_t V, int64_t vs, cudaStream_t st);
 template <typename R> void unpack_spinors(const R* src, double* dst_aos, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
 template <typename R> void pack_links(const double* src_aos, R* dst, int64_t V, cudaStream_t st);
 // launch variants of the two stencil kernels (chosen by the autotuner; 0 = default)
@@ -102,6 +102,8 @@ template <typename R> void proj_update(const Lat<R>& L, int j, int mode, R* a, R
 template <typename R> void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_src_stride, zd* out,
                                       zd* cpart, cudaStream_t st);
 template <typename R> void combine(const Lat<R>& L, int nvec, const zd* y, double* out_aos, cudaStream_t st);
+void eps_norms(const double* a_top, const double* a_bot, const double* b, int nsrc, int64_t n, double* out,
+               cudaStream_t st);
 
 // reverse sweep
 template <typename R> void rev_init(const Lat<R>& L, const Rev<R>& B, cudaStream_t st);

@@ -48,17 +48,30 @@ __global__ void k_pack_spinors(const double* __restrict__ aos, R* __restrict__ d
   store_spinor(dst + src * vs, V, x, o);
 }
 
+// Block start of the Theorem-1 TSL: r = (t, l) and s = (t + l, l) for every
+// source, in 2V-site fields (upper half at sites 0..V-1).  t may be null (zero).
 template <typename R>
-__global__ void k_pack_spinors_off(const double* __restrict__ aos, R* __restrict__ dst, int64_t V, int64_t Vf,
-                                   int64_t off, int64_t vs) {
+__global__ void k_pack_block_start(const double* __restrict__ top, const double* __restrict__ bot,
+                                   R* __restrict__ r, R* __restrict__ s, int64_t V, int64_t vs) {
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int src = blockIdx.y;
   if (x >= V) return;
-  const double2* in = reinterpret_cast<const double2*>(aos) + ((int64_t)src * V + x) * 12;
-  Spinor<R> o;
+  const int64_t Vf = 2 * V;
+  const double2* lb = reinterpret_cast<const double2*>(bot) + ((int64_t)src * V + x) * 12;
+  const double2* tp = top ? reinterpret_cast<const double2*>(top) + ((int64_t)src * V + x) * 12 : nullptr;
+  Spinor<R> rt, st, lo;
 #pragma unroll
-  for (int c = 0; c < 12; ++c) { double2 t = in[c]; o.c[c] = mk<R>((R)t.x, (R)t.y); }
-  store_spinor(dst + src * vs, Vf, off + x, o);
+  for (int c = 0; c < 12; ++c) {
+    const double2 l = lb[c];
+    const double2 t = tp ? tp[c] : make_double2(0.0, 0.0);
+    lo.c[c] = mk<R>((R)l.x, (R)l.y);
+    rt.c[c] = mk<R>((R)t.x, (R)t.y);
+    st.c[c] = mk<R>((R)(t.x + l.x), (R)(t.y + l.y));
+  }
+  store_spinor(r + src * vs, Vf, x, rt);
+  store_spinor(r + src * vs, Vf, V + x, lo);
+  store_spinor(s + src * vs, Vf, x, st);
+  store_spinor(s + src * vs, Vf, V + x, lo);
 }
 
 template <typename R>
@@ -108,9 +121,9 @@ void pack_spinors(const double* aos, R* dst, int nsrc, int64_t V, int64_t vs, cu
   k_pack_spinors<R><<<dim3(nblocks(V, BS), nsrc), BS, 0, st>>>(aos, dst, V, vs);
 }
 template <typename R>
-void pack_spinors_off(const double* aos, R* dst, int nsrc, int64_t V, int64_t Vf, int64_t off, int64_t vs,
+void pack_block_start(const double* top, const double* bot, R* r, R* s, int nsrc, int64_t V, int64_t vs,
                       cudaStream_t st) {
-  k_pack_spinors_off<R><<<dim3(nblocks(V, BS), nsrc), BS, 0, st>>>(aos, dst, V, Vf, off, vs);
+  k_pack_block_start<R><<<dim3(nblocks(V, BS), nsrc), BS, 0, st>>>(top, bot, r, s, V, vs);
 }
 template <typename R>
 void unpack_spinors(const R* f, double* aos, int nsrc, int64_t V, int64_t vs, cudaStream_t st) {
@@ -239,21 +252,29 @@ __device__ void omega_finalize(const Lat<R>& L, int src, int j, zd om, double rr
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(BS) k_tsl_init(Lat<R> L) {
-  __shared__ zd scratch[32];
+  __shared__ zd scratch[2 * 32];
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int src = blockIdx.y;
-  zd v[1] = {mk(0.0, 0.0)};
+  zd v[2] = {mk(0.0, 0.0), mk(0.0, 0.0)};
   if (x < L.g.V) {
     Spinor<R> b;
     load_spinor(L.r + src * L.vs, L.g.V, x, b);
     v[0] = spinor_dot(b, b);
+    if (L.block) {
+      Spinor<R> a;
+      load_spinor(L.s + src * L.vs, L.g.V, x, a);
+      v[1] = spinor_dot(a, b);
+    }
   }
-  block_sum<1>(v, scratch);
+  block_sum<2>(v, scratch);
   zd* part = L.part + src * L.part_stride;
-  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = v[0];
+    part[gridDim.x + blockIdx.x] = v[1];
+  }
   if (arrive_last(L.cnt + src * 16 + 0, gridDim.x)) {
-    zd s[1];
-    sum_partials<1>(part, gridDim.x, s, scratch);
+    zd s[2];
+    sum_partials<2>(part, gridDim.x, s, scratch);
     if (threadIdx.x == 0) {
       SrcScal& sc = L.sc[src];
       sc.err = 0;
@@ -262,7 +283,8 @@ __global__ void __launch_bounds__(BS) k_tsl_init(Lat<R> L) {
       sc.beta0 = b0;
       if (!(b0 > 0.0) || !isfinite(b0)) flag_error(sc, ERRB_NONFINITE, 0);
       sc.sv = mk(1.0 / b0, 0.0);
-      sc.sw = mk(1.0 / b0, 0.0);
+      // w_1 = s sw with w_1^dag v_1 = 1: sw = beta_0 / conj(s^dag r); s = r in plain mode
+      sc.sw = L.block ? zdiv(mk(b0, 0.0), conj(s[1])) : mk(1.0 / b0, 0.0);
       L.beta[(int64_t)src * L.k] = mk(0.0, 0.0);
       L.delta[(int64_t)src * L.k] = 0.0;
     }
@@ -1114,9 +1136,41 @@ void force_flush(const Lat<R>& L, const Rev<R>& B, const int* /*unused*/, int nt
 }
 
 // explicit instantiations
+// ---------------------------------------------------------------------------
+// Error estimates (Sec. 4.1, Eqs. error_est and bA_error_est): per source
+//   out[3 src + 0] = ||a_top||^2,  out[3 src + 1] = ||a_bot - b||^2,  out[3 src + 2] = ||b||^2
+// over interleaved complex128 fields of n doubles per source (a_top may be null).
+// One block per source, fixed strides and tree: deterministic.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_eps_norms(const double* __restrict__ a_top, const double* __restrict__ a_bot,
+                                                   const double* __restrict__ b, int64_t n, double* __restrict__ out) {
+  __shared__ zd scratch[2 * 32];
+  const int src = blockIdx.x;
+  const double* at = a_top ? a_top + (int64_t)src * n : nullptr;
+  const double* ab = a_bot + (int64_t)src * n;
+  const double* bb = b + (int64_t)src * n;
+  zd v[2] = {mk(0.0, 0.0), mk(0.0, 0.0)};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double t = at ? at[i] : 0.0, d = ab[i] - bb[i], q = bb[i];
+    v[0].re = fma(t, t, v[0].re);
+    v[0].im = fma(d, d, v[0].im);
+    v[1].re = fma(q, q, v[1].re);
+  }
+  block_sum<2>(v, scratch);
+  if (threadIdx.x == 0) {
+    out[3 * src + 0] = v[0].re;
+    out[3 * src + 1] = v[0].im;
+    out[3 * src + 2] = v[1].re;
+  }
+}
+void eps_norms(const double* a_top, const double* a_bot, const double* b, int nsrc, int64_t n, double* out,
+               cudaStream_t st) {
+  k_eps_norms<<<nsrc, 512, 0, st>>>(a_top, a_bot, b, n, out);
+}
+
 #define OV_INST(R)                                                                                        \
   template void pack_spinors<R>(const double*, R*, int, int64_t, int64_t, cudaStream_t);                 \
-  template void pack_spinors_off<R>(const double*, R*, int, int64_t, int64_t, int64_t, int64_t,            \
+  template void pack_block_start<R>(const double*, const double*, R*, R*, int, int64_t, int64_t,          \
                                     cudaStream_t);                                                       \
   template void unpack_spinors<R>(const R*, double*, int, int64_t, int64_t, cudaStream_t);               \
   template void pack_links<R>(const double*, R*, int64_t, cudaStream_t);                                 \

@@ -17,7 +17,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
 };
 
 struct Status {
@@ -380,13 +380,17 @@ int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   return OV_OK;
 }
 
-// Theorem 1: TSL on B = [[H, dH], [0, H]] from (0, b) with left start (b, b)/||b||
+// Theorem 1: TSL on B = [[H, dH], [0, H]] from (top, bottom) (top may be null:
+// zero) with left start proportional to (top + bottom, bottom); writes the two
+// halves of the result.
 template <typename R>
-int tsl_jvp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
-                 const void* b, int k, const void* E, double m_dir, void* dx, void* x, ov_tsl_info* info) {
-  check_ptr(b);
-  check_ptr(x);
-  check_ptr(dx);
+int block_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+               const void* top, const void* bottom, int k, const void* E, double m_dir, void* out_top,
+               void* out_bottom, ov_tsl_info* info) {
+  check_ptr(bottom);
+  check_ptr(out_top);
+  check_ptr(out_bottom);
+  if (top) check_ptr(top);
   if (E) check_ptr(E);
   if (!std::isfinite(m_dir)) throw Status{OV_ERR_INVALID_ARG};
   Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true, 2);
@@ -397,12 +401,9 @@ int tsl_jvp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
     L.ue = ue;
   }
   L.mdir = (R)m_dir;
-  const double* bd = static_cast<const double*>(b);
-  CK(cudaMemsetAsync(L.r, 0, sizeof(R) * nsrc * L.vs, c->st));
-  run(c, OV_KIND_LAYOUT, 3, [&] {
-    pack_spinors_off<R>(bd, L.r, nsrc, V, Vf, V, L.vs, c->st);   // r = (0, b)
-    pack_spinors_off<R>(bd, L.s, nsrc, V, Vf, 0, L.vs, c->st);   // s = (b, b)
-    pack_spinors_off<R>(bd, L.s, nsrc, V, Vf, V, L.vs, c->st);
+  run(c, OV_KIND_LAYOUT, 1, [&] {
+    pack_block_start<R>(static_cast<const double*>(top), static_cast<const double*>(bottom), L.r, L.s, nsrc, V,
+                        L.vs, c->st);
   });
   CK(cudaEventRecord(c->ev[0], c->st));
   forward_krylov(c, L);
@@ -424,9 +425,9 @@ int tsl_jvp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   launch_check();
   const size_t half = (size_t)V * 24 * sizeof(double);
   for (int src = 0; src < nsrc; ++src) {
-    CK(cudaMemcpyAsync(static_cast<char*>(dx) + src * half, out + (int64_t)src * Vf * 24, half,
+    CK(cudaMemcpyAsync(static_cast<char*>(out_top) + src * half, out + (int64_t)src * Vf * 24, half,
                        cudaMemcpyDeviceToDevice, c->st));
-    CK(cudaMemcpyAsync(static_cast<char*>(x) + src * half, out + (int64_t)src * Vf * 24 + V * 24, half,
+    CK(cudaMemcpyAsync(static_cast<char*>(out_bottom) + src * half, out + (int64_t)src * Vf * 24 + V * 24, half,
                        cudaMemcpyDeviceToDevice, c->st));
   }
   CK(cudaEventRecord(c->ev[3], c->st));
@@ -438,6 +439,57 @@ int tsl_jvp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
     info->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
     info->t_ms[2] = elapsed(c->ev[2], c->ev[3]);
   }
+  return OV_OK;
+}
+
+// A-posteriori estimates of Sec. 4.1: the sign applied twice, each time by its
+// own k-step TSL, then ||sgn^2 b - b|| / (2 ||b||) per source (Eq. error_est),
+// or for the block matrix from (0, b) (Eq. bA_error_est) when block is set.
+void merge_info(ov_tsl_info* acc, const ov_tsl_info& one) {
+  if (!acc) return;
+  if (one.k_reached < acc->k_reached) acc->k_reached = one.k_reached;
+  if (one.newton_iters > acc->newton_iters) acc->newton_iters = one.newton_iters;
+  for (int i = 0; i < 8; ++i) acc->t_ms[i] += one.t_ms[i];
+}
+
+template <typename R>
+int eps_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc, const void* b,
+             int k, bool block, const void* E, double m_dir, double* eps, ov_tsl_info* info) {
+  check_ptr(b);
+  if (!eps) throw Status{OV_ERR_INVALID_ARG};
+  const Geom g = make_geom(dims);
+  if (nsrc < 1 || nsrc > 4096) throw Status{OV_ERR_INVALID_ARG};
+  const int64_t n = g.V * 24;   // doubles per source
+  double* t1 = block ? wsT<double>(c, B_EPS1T, nsrc * n) : nullptr;
+  double* b1 = wsT<double>(c, B_EPS1B, nsrc * n);
+  double* t2 = block ? wsT<double>(c, B_EPS2T, nsrc * n) : nullptr;
+  double* b2 = wsT<double>(c, B_EPS2B, nsrc * n);
+  double* nrm = wsT<double>(c, B_EPSN, 3 * (int64_t)nsrc);
+  if (info) info->k_reached = k;
+  ov_tsl_info one{};
+  int st;
+  if (block) {
+    st = block_impl<R>(c, dims, U, mu, m_w, nsrc, nullptr, b, k, E, m_dir, t1, b1, &one);
+    merge_info(info, one);
+    if (st != OV_OK) return st;
+    one = ov_tsl_info{};
+    st = block_impl<R>(c, dims, U, mu, m_w, nsrc, t1, b1, k, E, m_dir, t2, b2, &one);
+  } else {
+    st = tsl_sign_impl<R>(c, dims, U, mu, m_w, nsrc, b, k, b1, &one);
+    merge_info(info, one);
+    if (st != OV_OK) return st;
+    one = ov_tsl_info{};
+    st = tsl_sign_impl<R>(c, dims, U, mu, m_w, nsrc, b1, k, b2, &one);
+  }
+  merge_info(info, one);
+  if (st != OV_OK) return st;
+  run(c, OV_KIND_COMBINE, 1, [&] { eps_norms(t2, b2, static_cast<const double*>(b), nsrc, n, nrm, c->st); });
+  launch_check();
+  std::vector<double> h(3 * (size_t)nsrc);
+  CK(cudaMemcpyAsync(h.data(), nrm, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int src = 0; src < nsrc; ++src)
+    eps[src] = std::sqrt(h[3 * src] + h[3 * src + 1]) / (2.0 * std::sqrt(h[3 * src + 2]));
   return OV_OK;
 }
 
@@ -873,14 +925,42 @@ int ov_set_stencil_variants(ov_context* c, int32_t apply_variant, int32_t pair_v
   return OV_OK;
 }
 
-int ov_tsl_sign_jvp(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
-                    const void* b, int32_t k, const void* E, double m_dir, void* dx, void* x, ov_tsl_info* info) {
+int ov_block_tsl_sign(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                      const void* top, const void* bottom, int32_t k, const void* E, double m_dir, void* out_top,
+                      void* out_bottom, ov_tsl_info* info) {
   if (!c || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
   if (info) std::memset(info, 0, sizeof(*info));
   return guarded([&] {
     return c->opt.precision == OV_MIXED
-               ? tsl_jvp_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, E, m_dir, dx, x, info)
-               : tsl_jvp_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, E, m_dir, dx, x, info);
+               ? block_impl<float>(c, dims, U, mu, m_w, nsrc, top, bottom, k, E, m_dir, out_top, out_bottom, info)
+               : block_impl<double>(c, dims, U, mu, m_w, nsrc, top, bottom, k, E, m_dir, out_top, out_bottom, info);
+  });
+}
+
+int ov_tsl_sign_jvp(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                    const void* b, int32_t k, const void* E, double m_dir, void* dx, void* x, ov_tsl_info* info) {
+  return ov_block_tsl_sign(c, dims, U, mu, m_w, nsrc, nullptr, b, k, E, m_dir, dx, x, info);
+}
+
+int ov_tsl_eps(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+               const void* b, int32_t k, double* eps, ov_tsl_info* info) {
+  if (!c || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? eps_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, false, nullptr, 0.0, eps, info)
+               : eps_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, false, nullptr, 0.0, eps, info);
+  });
+}
+
+int ov_block_tsl_eps(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                     const void* b, int32_t k, const void* E, double m_dir, double* eps, ov_tsl_info* info) {
+  if (!c || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? eps_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, true, E, m_dir, eps, info)
+               : eps_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, true, E, m_dir, eps, info);
   });
 }
 

@@ -259,6 +259,57 @@ def test_block_tsl_jvp_fp64(dims, m_w, k, reb, with_e, m_dir, tol):
         assert rel(x[s], rx) <= tol, (s, rel(x[s], rx))
 
 
+@pytest.mark.parametrize("dims,k,reb", [((3, 5, 2, 4), 50, 10), ((3, 3, 3, 3), 60, 1)])
+def test_block_tsl_from_general_start_fp64(dims, k, reb):
+    rng = np.random.default_rng(73)
+    u = inputs.su3_links(dims, 0.3, rng)
+    top = inputs.gaussian_spinors(dims, 2, rng)
+    bot = inputs.gaussian_spinors(dims, 2, rng)
+    e = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape)
+    mu, m_w, m = 0.3, -1.0, 0.4
+    zt, zb = binding.block_tsl_sign(T(u), mu, m_w, T(top), T(bot), k, T(e), m, rebiorth=reb)
+    zt, zb = zt.cpu().numpy(), zb.cpu().numpy()
+    for s in range(2):
+        rt, rb, _ = tsl.block_tsl_start(u, top[s], bot[s], mu, m_w, k, e, m, rebiorth=reb)
+        assert rel(zt[s], rt) <= 1e-10, (s, rel(zt[s], rt))
+        assert rel(zb[s], rb) <= 1e-10, (s, rel(zb[s], rb))
+
+
+@pytest.mark.parametrize("dims,m_w,k,reb,passes,tol", [
+    ((3, 3, 3, 3), -1.0, 40, 1, 2, 1e-6),
+    ((4, 4, 4, 4), -2.0, 200, 1, 2, 1e-3),      # the 4x4^3 physics point: agreement to 1e-3
+])
+def test_eps_a_matches_oracle(dims, m_w, k, reb, passes, tol):
+    u, b, _ = case(dims, 0.3, 14, 2)
+    mu = 0.3
+    got = binding.tsl_eps(T(u), mu, m_w, T(b), k, rebiorth=reb, passes=passes)
+    for s in range(2):
+        want = tsl.eps_a(u, b[s], mu, m_w, k, rebiorth=reb, passes=passes)
+        assert abs(got[s] - want) <= tol * want, (s, got[s], want)
+
+
+def test_eps_b_matches_oracle():
+    dims, mu, m_w, k, m = (3, 3, 2, 3), 0.3, -1.0, 40, 0.5
+    rng = np.random.default_rng(74)
+    u = inputs.su3_links(dims, 0.3, rng)
+    b = inputs.gaussian_spinors(dims, 2, rng)
+    e = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape)
+    got = binding.block_tsl_eps(T(u), mu, m_w, T(b), k, T(e), m)
+    for s in range(2):
+        want = tsl.eps_b(u, b[s], mu, m_w, k, e, m)
+        assert abs(got[s] - want) <= 1e-6 * want, (s, got[s], want)
+
+
+def test_eps_b_without_direction_equals_eps_a():
+    """dH = 0: the block estimate reduces to eps_A (the same closed form the oracle is pinned by)."""
+    dims, mu, m_w, k = (3, 5, 2, 4), 0.3, -1.0, 50
+    u, b, _ = case(dims, 0.3, 15, 2)
+    ea = binding.tsl_eps(T(u), mu, m_w, T(b), k)
+    eb = binding.block_tsl_eps(T(u), mu, m_w, T(b), k, None, 0.0)
+    assert np.all(ea > 1e-6)
+    assert np.all(np.abs(eb - ea) <= 1e-9 * ea), (ea, eb)
+
+
 def test_block_tsl_jvp_mixed_well_conditioned():
     dims, m_w, k, mu = (3, 3, 3, 3), -1.0, 60, 0.3
     rng = np.random.default_rng(72)
