@@ -155,6 +155,20 @@ def algorithmic_bytes(kind, k, V, nsrc, e, period, passes):
     return None
 
 
+def job_seconds_per_unit(ms_local, steps, world, device="cpu"):
+    """(ms of the timed region, whole-job seconds per unit).  The region's time is
+    the MAX over ranks; every rank runs one replica of the workload per step, so
+    the job processes steps x world units in that time."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ms / 1e3 / (steps * world)
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -204,13 +218,7 @@ def run_ours(args, rank, world, local_rank):
     launches = binding.launch_count(ctx) - l0
     prof = binding.profile_read(ctx, reset=True)
     binding.profile_enable(ctx, False)
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = ms_total / 1e3 / (args.steps * world)
+    ms_total, value = job_seconds_per_unit(e0.elapsed_time(e1), args.steps, world, dev)
 
     # roofline of the dominant lattice kernel (HBM-bound by design)
     e = 4 if args.precision == "mixed" else 8
@@ -231,13 +239,26 @@ def run_ours(args, rank, world, local_rank):
     if args.precision == "fp64" and dom in ("proj_dots", "proj_update"):
         # 4 FP64 FMA (8 flop) per complex element streamed from a basis vector
         flops = bytes_dom / 16 * 8
-        peak64 = fp64_peak(dev)
         achieved = flops / (prof[dom][1] / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak64 / 1e3, 3),
-                    "unit": "TFLOP/s", "frac": round(achieved / (peak64 / 1e3), 3),
-                    "peak_source": "measured in this run: cuBLAS float64 GEMM n=4096",
-                    "traffic": None, "hbm_view": {"achieved_GB_s": round(gbs, 1), "peak": hbm,
-                                                   "frac": round(gbs / hbm, 3)}, **per_launch}
+        # FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA (4 flop) per
+        # SM per clock (1.25 TFLOP/s nominal at 2070 MHz), at the median SM clock sampled
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        peak_alu = 152 * 4 * sm_mhz * 1e6 / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak_alu, 4),
+                    "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 3),
+                    "peak_source": f"derived: 152 SMs x 4 FP64 flop/clk x {sm_mhz:.0f} MHz (sampled)",
+                    "fp64_gemm_measured_tflops": round(fp64_peak(dev) / 1e3, 3),
+                    "hbm_view": {"achieved_GB_s": round(gbs, 1), "peak": hbm, "frac": round(gbs / hbm, 3)},
+                    **per_launch}
+        if dom == "proj_dots":
+            # ncu: DRAM bytes of a two-sided k_proj_dots launch = 1.085 x its algorithmic
+            # bytes (14x14^3, k = 120, nb = 101); traffic grows with the fields streamed
+            roofline["traffic"] = int(PROJ_DOTS_TRAFFIC_RATIO * per_launch["algorithmic_bytes_per_launch"])
+            roofline["traffic_source"] = ("ncu dram bytes of one k_proj_dots launch at 14x14^3, k=120, nb=101 "
+                                          f"(ratio {PROJ_DOTS_TRAFFIC_RATIO} to algorithmic), scaled to this "
+                                          "launch average")
+        else:
+            roofline["traffic"] = None
     else:
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(gbs / hbm, 3), "peak_source": peak_src, "traffic": None, **per_launch}
@@ -265,8 +286,11 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+PROJ_DOTS_TRAFFIC_RATIO = 1.085
+
+
 def fp64_peak(dev, n=4096, reps=3):
-    """FP64 ALU peak for the roofline of FP64-bound kernels: a cuBLAS float64 GEMM."""
+    """cuBLAS float64 GEMM rate (context for the FP64 ALU roofline), GFLOP/s."""
     import torch
     a = torch.randn(n, n, dtype=torch.float64, device=dev)
     b = torch.randn(n, n, dtype=torch.float64, device=dev)
