@@ -155,6 +155,32 @@ def algorithmic_bytes(kind, k, V, nsrc, e, period, passes):
     return None
 
 
+H_FLOP_PER_SITE = 1368   # one Wilson H application on half spinors (8 hops + diagonal)
+
+
+def algorithmic_flops(kind, k, V, nsrc, period, passes):
+    """Algorithmic FP64 flops of one ov_tsl_sign_vjp call for the ALU-bound kinds.
+
+    Gram-Schmidt kinds: 4 FMA (8 flop) per complex element and basis vector.
+    rev_stencil, per site and step: H^dag g_p and H (conj(g_alpha) v_j + g_s)
+    (2 x 1368), the seven single complex combinations of fields it adds (g_p,
+    the H input, xbar, g_r, g_s and the two previous-step terms: 7 x 12 x 8),
+    and 2 x 12 x 8 per recorded Gram-Schmidt projection still to be applied."""
+    e64 = 8
+    if kind in ("proj_dots", "proj_update"):
+        basis = 2 * passes * nsrc * 24 * e64 * V * sum(2 * (j + 1) for j in rebiorth_steps(k, period))
+        return basis / 16 * 8
+    if kind == "rev_stencil":
+        reb = set(rebiorth_steps(k, period))
+        nrec, acc = 0, 0
+        for j in range(k - 1, -1, -1):
+            if j < k - 1 and j in reb:
+                nrec += 1
+            acc += 2 * 12 * 8 * nrec
+        return nsrc * V * (k * (2 * H_FLOP_PER_SITE + 7 * 12 * 8) + acc)
+    return None
+
+
 def job_seconds_per_unit(ms_local, steps, world, device="cpu"):
     """(ms of the timed region, whole-job seconds per unit).  The region's time is
     the MAX over ranks; every rank runs one replica of the workload per step, so
@@ -236,9 +262,8 @@ def run_ours(args, rank, world, local_rank):
     gbs = bytes_dom / (prof[dom][1] / 1e3) / 1e9
     per_launch = {"launches": prof[dom][0], "avg_launch_us": round(1e3 * prof[dom][1] / max(1, prof[dom][0]), 2),
                   "algorithmic_bytes_per_launch": int(bytes_dom / max(1, prof[dom][0]))}
-    if args.precision == "fp64" and dom in ("proj_dots", "proj_update"):
-        # 4 FP64 FMA (8 flop) per complex element streamed from a basis vector
-        flops = bytes_dom / 16 * 8
+    if args.precision == "fp64" and dom in ("proj_dots", "proj_update", "rev_stencil"):
+        flops = algorithmic_flops(dom, k, V, nsrc, args.rebiorth, args.passes) * args.steps
         achieved = flops / (prof[dom][1] / 1e3) / 1e12
         # FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA (4 flop) per
         # SM per clock (1.25 TFLOP/s nominal at 2070 MHz), at the median SM clock sampled

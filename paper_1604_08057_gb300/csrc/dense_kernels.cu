@@ -3,6 +3,10 @@
 // in-place Gauss-Jordan inversion with partial pivoting, GEMM, and the
 // scaled Newton update X <- (g X + s X^{-1}/g)/2 with deterministic norms.
 // Matrices are row-major, element (i, j) at i*k + j.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
 #include "kernels.h"
 
 namespace ov {
@@ -79,139 +83,122 @@ void dense_extract_tri(const zd* e, int k, zd* ga, zd* gb, double* gd, cudaStrea
 // the pivot is the unused row p_kk with the largest |X[p][kk]|; row p_kk is
 // normalised and column kk is eliminated from every other row (the inverse is
 // built in place, column kk receiving -X[i][kk]/pivot).  One launch per step,
-// reading X_in and writing X_out (ping-pong), so no block sees a row that
-// another block has already rewritten.  The pivot search of step kk+1 is
-// fused into step kk as per-block candidates.  At the end
+// one block per row, reading X_in and writing X_out (ping-pong), so no block
+// sees a row that another block has already rewritten.  Each thread owns a
+// fixed set of columns and reads only those entries of its row and of the
+// pivot row: no shared memory, no block-wide barrier.  The pivot of step kk+1
+// is chosen during step kk by a 64-bit atomicMax over packed keys
+//   (top 52 bits of the FP64 |X[i][kk+1]|^2) << 12 | (4095 - i),
+// so the largest modulus wins and, among keys equal in those bits, the lowest
+// row; the maximum does not depend on the order of arrival.  At the end
 //   inv(A)[i][j] = X[p_i][q_j],  q = p^{-1}.
 // ---------------------------------------------------------------------------
-constexpr int GJ_THREADS = 256;
-constexpr int GJ_ROWS = 4;
-constexpr int GJ_JPT = 4;   // columns per thread held in registers (k <= 1024)
+constexpr int GJ_THREADS = 128;
+constexpr int GJ_JPT = 8;   // columns per thread held in registers (k <= 1024)
 
-struct Cand { double v; int i; };
-
-__device__ __forceinline__ Cand cand_max(Cand a, Cand b) {
-  return (b.v > a.v || (b.v == a.v && b.i < a.i)) ? b : a;
+__device__ __forceinline__ unsigned long long gj_key(double nrm, int i) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(nrm);
+  return ((b >> 12) << 12) | (unsigned long long)(4095 - i);
 }
-__device__ __forceinline__ Cand block_cand_max(Cand c, Cand* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    Cand d;
-    d.v = __shfl_down_sync(0xffffffffu, c.v, o);
-    d.i = __shfl_down_sync(0xffffffffu, c.i, o);
-    c = cand_max(c, d);
+__device__ __forceinline__ void gj_offer(unsigned long long* key, double nrm, int i, int* err) {
+  if (!(nrm >= 0.0)) {   // NaN entry: no pivot can be trusted
+    atomicOr(err, ERRB_SINGULAR);
+    return;
   }
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) c = cand_max(c, sh[w]);
-    sh[0] = c;
-  }
-  __syncthreads();
-  const Cand r = sh[0];
-  __syncthreads();
-  return r;
+  atomicMax(key, gj_key(nrm, i));
 }
 
-// candidates for column 0; clears the used-row flags
-__global__ void __launch_bounds__(GJ_THREADS) k_gj_init(const zd* __restrict__ x, int k, Cand* cand, int* used) {
-  __shared__ Cand sh[GJ_THREADS / 32];
-  const int r0 = blockIdx.x * GJ_ROWS;
-  Cand c{-1.0, 0x7fffffff};
-  for (int t = threadIdx.x; t < GJ_ROWS; t += blockDim.x) {
-    const int i = r0 + t;
-    if (i < k) {
-      used[i] = 0;
-      c = cand_max(c, Cand{norm2(x[(int64_t)i * k]), i});
+// used-row flags cleared and the candidates of column 0 offered (keys zeroed beforehand)
+__global__ void k_gj_init(const zd* __restrict__ x, int k, unsigned long long* keys, int* used, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  used[i] = 0;
+  gj_offer(keys, norm2(x[(int64_t)i * k]), i, err);
+}
+
+template <int JPT>
+__global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict__ xin, zd* __restrict__ xout, int k,
+                                                        int kk, unsigned long long* keys, int* used, int* prows,
+                                                        double* logdet, int* err) {
+  const int i = blockIdx.x;   // the block's row
+  const zd* xr = xin + (int64_t)i * k;
+  zd* yr = xout + (int64_t)i * k;
+  // the row's own entries do not depend on the pivot: issue them first
+  zd xv[JPT > 0 ? JPT : 1];
+  if (JPT > 0) {
+#pragma unroll
+    for (int q = 0; q < JPT; ++q) {
+      const int j = threadIdx.x + q * GJ_THREADS;
+      xv[q] = j < k ? xr[j] : mk(0.0, 0.0);
     }
   }
-  c = block_cand_max(c, sh);
-  if (threadIdx.x == 0) cand[blockIdx.x] = c;
-}
-
-__global__ void __launch_bounds__(GJ_THREADS) k_gj_step(const zd* __restrict__ xin, zd* __restrict__ xout, int k,
-                                                        int kk, const Cand* __restrict__ cin, Cand* cout, int* used,
-                                                        int* prows, double* logdet, int* err) {
-  extern __shared__ zd prow[];
-  __shared__ Cand sh[GJ_THREADS / 32];
-  // pivot of column kk from the candidates of the previous step
-  Cand c{-1.0, 0x7fffffff};
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) c = cand_max(c, cin[b]);
-  c = block_cand_max(c, sh);
-  // a NaN column leaves no valid candidate: keep the indices in range and flag it
-  const bool bad = c.i < 0 || c.i >= k;
-  const int p = bad ? kk : c.i;
-  if (bad && blockIdx.x == 0 && threadIdx.x == 0) *err |= ERRB_SINGULAR;
-  const zd piv = xin[(int64_t)p * k + kk];
-  const zd inv = zdiv(mk(1.0, 0.0), piv);
-  for (int j = threadIdx.x; j < k; j += blockDim.x) prow[j] = (j == kk) ? inv : xin[(int64_t)p * k + j] * inv;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const double a = sqrt(norm2(piv));
-    if (!(a > 0.0) || !isfinite(a)) *err |= ERRB_SINGULAR;
-    *logdet += log(a);
-    prows[kk] = p;
+  const zd fr = xr[kk];
+  const int row_used = used[i];
+  const unsigned long long key = keys[kk];
+  const int cand = 4095 - (int)(key & 4095ull);
+  const bool bad = key == 0ull || cand < 0 || cand >= k;
+  const int p = bad ? kk : cand;
+  const zd* pr = xin + (int64_t)p * k;
+  const zd piv = pr[kk];
+  // 1/pivot and the row factor m = X[i][kk]/pivot, once per warp
+  zd inv = mk(0.0, 0.0), m = mk(0.0, 0.0);
+  if ((threadIdx.x & 31) == 0) {
+    inv = zdiv(mk(1.0, 0.0), piv);
+    m = fr * inv;
   }
-  __syncthreads();
-  const int r0 = blockIdx.x * GJ_ROWS;
-  const int nrow = min(GJ_ROWS, k - r0);
-  Cand nc{-1.0, 0x7fffffff};
-  if (k <= GJ_THREADS * GJ_JPT) {
-    // all loads of the block's rows are issued before any arithmetic
-    zd xv[GJ_ROWS][GJ_JPT], fr[GJ_ROWS];
+  inv.re = __shfl_sync(0xffffffffu, inv.re, 0);
+  inv.im = __shfl_sync(0xffffffffu, inv.im, 0);
+  m.re = __shfl_sync(0xffffffffu, m.re, 0);
+  m.im = __shfl_sync(0xffffffffu, m.im, 0);
+  const bool offer = i != p && !row_used && kk + 1 < k;
+  if (JPT > 0) {
+    zd pv[JPT > 0 ? JPT : 1];
 #pragma unroll
-    for (int r = 0; r < GJ_ROWS; ++r) {
-      const int i = r0 + r;
-      fr[r] = r < nrow ? xin[(int64_t)i * k + kk] : mk(0.0, 0.0);
-#pragma unroll
-      for (int q = 0; q < GJ_JPT; ++q) {
-        const int j = threadIdx.x + q * GJ_THREADS;
-        xv[r][q] = (r < nrow && j < k) ? xin[(int64_t)i * k + j] : mk(0.0, 0.0);
-      }
+    for (int q = 0; q < JPT; ++q) {
+      const int j = threadIdx.x + q * GJ_THREADS;
+      pv[q] = j < k ? pr[j] : mk(0.0, 0.0);
     }
 #pragma unroll
-    for (int r = 0; r < GJ_ROWS; ++r) {
-      const int i = r0 + r;
-      if (r >= nrow) break;
-#pragma unroll
-      for (int q = 0; q < GJ_JPT; ++q) {
-        const int j = threadIdx.x + q * GJ_THREADS;
-        if (j >= k) break;
-        zd v;
-        if (i == p) {
-          v = prow[j];
-        } else if (j == kk) {
-          v = -(fr[r] * prow[kk]);
-        } else {
-          v = xv[r][q];
-          cmsub(v, fr[r], prow[j]);
-        }
-        xout[(int64_t)i * k + j] = v;
-        if (j == kk + 1 && i != p && !used[i]) nc = cand_max(nc, Cand{norm2(v), i});
+    for (int q = 0; q < JPT; ++q) {
+      const int j = threadIdx.x + q * GJ_THREADS;
+      if (j >= k) break;
+      zd v;
+      if (i == p) {
+        v = (j == kk) ? inv : pv[q] * inv;
+      } else if (j == kk) {
+        v = mk(-m.re, -m.im);
+      } else {
+        v = xv[q];
+        cmsub(v, m, pv[q]);
       }
+      yr[j] = v;
+      if (j == kk + 1 && offer) gj_offer(keys + kk + 1, norm2(v), i, err);
     }
   } else {
-    for (int r = 0; r < nrow; ++r) {
-      const int i = r0 + r;
-      const zd f = xin[(int64_t)i * k + kk];
-      const zd* xr = xin + (int64_t)i * k;
-      zd* yr = xout + (int64_t)i * k;
-      for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        zd v;
-        if (i == p) {
-          v = prow[j];
-        } else if (j == kk) {
-          v = -(f * prow[kk]);
-        } else {
-          v = xr[j];
-          cmsub(v, f, prow[j]);
-        }
-        yr[j] = v;
-        if (j == kk + 1 && i != p && !used[i]) nc = cand_max(nc, Cand{norm2(v), i});
+    for (int j = threadIdx.x; j < k; j += GJ_THREADS) {
+      zd v;
+      if (i == p) {
+        v = (j == kk) ? inv : pr[j] * inv;
+      } else if (j == kk) {
+        v = mk(-m.re, -m.im);
+      } else {
+        v = xr[j];
+        cmsub(v, m, pr[j]);
       }
+      yr[j] = v;
+      if (j == kk + 1 && offer) gj_offer(keys + kk + 1, norm2(v), i, err);
     }
   }
-  nc = block_cand_max(nc, sh);
-  if (threadIdx.x == 0) cout[blockIdx.x] = nc;
-  if (p >= r0 && p < r0 + nrow && threadIdx.x == 0) used[p] = 1;
+  if (threadIdx.x == 0) {
+    if (bad && i == 0) atomicOr(err, ERRB_SINGULAR);
+    if (i == p) {
+      const double a = sqrt(norm2(piv));
+      if (!(a > 0.0) || !isfinite(a)) atomicOr(err, ERRB_SINGULAR);
+      *logdet += log(a);
+      prows[kk] = p;
+      used[p] = 1;
+    }
+  }
 }
 
 __global__ void k_gj_invperm(const int* __restrict__ prows, int* q, int k) {
@@ -226,28 +213,78 @@ __global__ void k_gj_gather(const zd* __restrict__ x, zd* __restrict__ out, cons
   out[t] = x[(int64_t)prows[i] * k + q[j]];
 }
 
-void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, Cand2* cand,
-                   double* logdet, int* err, cudaStream_t st) {
-  Cand* cd = reinterpret_cast<Cand*>(cand);
-  const unsigned nb = nblk(k, GJ_ROWS);
-  const size_t smem = (size_t)k * sizeof(zd);
-  static bool attr = false;
-  if (smem > 48 * 1024 && !attr) {
-    cudaFuncSetAttribute(k_gj_step, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr = true;
-  }
-  k_gj_init<<<nb, GJ_THREADS, 0, st>>>(a, k, cd, used);
+static void gj_launch_all(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int* used,
+                          unsigned long long* keys, double* logdet, int* err, cudaStream_t st) {
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)(k + 1), st);
+  k_gj_init<<<nblk(k, 128), 128, 0, st>>>(a, k, keys, used, err);
   const zd* in = a;
   zd* bufs[2] = {w0, w1};
   for (int kk = 0; kk < k; ++kk) {
     zd* out = bufs[kk & 1];
-    k_gj_step<<<nb, GJ_THREADS, smem, st>>>(in, out, k, kk, cd + (kk & 1) * nb, cd + ((kk + 1) & 1) * nb, used,
-                                            ipiv, logdet, err);
+    if (k <= GJ_THREADS * GJ_JPT)
+      k_gj_step<GJ_JPT><<<k, GJ_THREADS, 0, st>>>(in, out, k, kk, keys, used, ipiv, logdet, err);
+    else
+      k_gj_step<0><<<k, GJ_THREADS, 0, st>>>(in, out, k, kk, keys, used, ipiv, logdet, err);
     in = out;
   }
   int* q = used;   // the flags are no longer needed
   k_gj_invperm<<<nblk(k, 128), 128, 0, st>>>(ipiv, q, k);
   k_gj_gather<<<nblk((int64_t)k * k, 256), 256, 0, st>>>(in, ainv, ipiv, q, k);
+}
+
+// The k + 4 launches of one inversion are captured once per (k, buffers) as a
+// CUDA graph and replayed on the caller's stream: the steps are short, so the
+// per-launch overhead of k back-to-back launches is a large part of their time.
+namespace {
+struct GjGraph {
+  const void* ptrs[9];
+  int k, dev;
+  cudaGraphExec_t exec;
+};
+std::mutex g_gj_mutex;
+std::vector<GjGraph> g_gj_graphs;
+}  // namespace
+
+void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, unsigned long long* keys,
+                   double* logdet, int* err, cudaStream_t st) {
+  const void* ptrs[9] = {a, ainv, w0, w1, ipiv, used, keys, logdet, err};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_gj_mutex);
+  for (const GjGraph& g : g_gj_graphs) {
+    if (g.k == k && g.dev == dev && std::equal(ptrs, ptrs + 9, g.ptrs)) {
+      cudaGraphLaunch(g.exec, st);
+      return;
+    }
+  }
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    gj_launch_all(a, ainv, w0, w1, k, ipiv, used, keys, logdet, err, cap);
+    ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess && graph &&
+         cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (cap) cudaStreamDestroy(cap);
+  if (!ok) {   // capture unavailable: launch directly
+    cudaGetLastError();
+    gj_launch_all(a, ainv, w0, w1, k, ipiv, used, keys, logdet, err, st);
+    return;
+  }
+  if (g_gj_graphs.size() >= 64) {
+    cudaGraphExecDestroy(g_gj_graphs.front().exec);
+    g_gj_graphs.erase(g_gj_graphs.begin());
+  }
+  GjGraph g;
+  std::copy(ptrs, ptrs + 9, g.ptrs);
+  g.k = k;
+  g.dev = dev;
+  g.exec = exec;
+  g_gj_graphs.push_back(g);
+  cudaGraphLaunch(exec, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -125,8 +125,7 @@ void dense_zero(zd* A, int64_t n, cudaStream_t st);
 // Ainv = A^{-1} by Gauss-Jordan with partial pivoting (A is not modified; w0, w1 are
 // k x k work buffers; ipiv, used: k ints; cand: 2 * ceil(k/4) entries);
 // logdet[0] += sum log|pivot| = log|det A|
-struct Cand2 { double v; int i; int pad; };
-void dense_inverse(const zd* A, zd* Ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, Cand2* cand,
+void dense_inverse(const zd* A, zd* Ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, unsigned long long* keys,
                    double* logdet, int* err, cudaStream_t st);
 void dense_gemm(const zd* A, const zd* B, zd* C, int k, cudaStream_t st);   // C = A B
 // C = op(A) op(B), op = conjugate transpose when the flag is set

@@ -527,19 +527,26 @@ void tsl_update(const Lat<R>& L, int j, bool finalize, cudaStream_t st) {
 // mode 1 (adjoint):  DA = V, UA = W, DB = W, UB = V   (a = g_r, b = g_s)
 // coef layout: [src][2*i + side];  cpart: [src][2*i + side][site block]
 // ---------------------------------------------------------------------------
+// sites per thread of the projection dots: 4 once there are enough basis
+// vectors to fill the GPU with site blocks x basis blocks, else 1
+static inline int proj_spt(int nb) { return nb >= NB ? 4 : 1; }
+
+// Each thread accumulates `spt` sites (strided by the block size, so loads stay
+// coalesced) before the block reduction, which then costs 1/spt per site.
 template <typename R>
 __global__ void __launch_bounds__(BS) k_proj_dots(Lat<R> L, int nb, int mode, const R* __restrict__ a,
                                                    const R* __restrict__ b, int64_t ab_stride,
-                                                   zd* __restrict__ cpart, int64_t cp_stride) {
+                                                   zd* __restrict__ cpart, int64_t cp_stride, int spt) {
   __shared__ zd scratch[2 * NB * 32];
-  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int src = blockIdx.z;
   const int i0 = blockIdx.y * NB;
   const int64_t V = L.g.V;
   SiteDot<R> acc[2 * NB];
 #pragma unroll
   for (int t = 0; t < 2 * NB; ++t) acc[t].zero();
-  if (x < V) {
+  for (int q = 0; q < spt; ++q) {
+    const int64_t x = (blockIdx.x * (int64_t)spt + q) * blockDim.x + threadIdx.x;
+    if (x >= V) break;
     Spinor<R> va, vb, e;
     load_spinor(a + src * ab_stride, V, x, va);
     if (b) load_spinor(b + src * ab_stride, V, x, vb);
@@ -671,10 +678,11 @@ template <typename R>
 void proj_dots(const Lat<R>& L, int j, int mode, const R* a, const R* b, int64_t ab_stride, zd* coef,
                zd* cpart, cudaStream_t st) {
   const int nb = j + 1;
-  const unsigned nsb = nblocks(L.g.V, BS);
+  const int spt = proj_spt(nb);
+  const unsigned nsb = nblocks(L.g.V, BS * spt);
   const int64_t cp_stride = (int64_t)2 * L.k * nsb;
   k_proj_dots<R><<<dim3(nsb, nblocks(nb, NB), L.nsrc), BS, 0, st>>>(L, nb, mode, a, b, ab_stride, cpart,
-                                                                     cp_stride);
+                                                                     cp_stride, spt);
   k_proj_reduce<<<dim3(nblocks(2 * nb, 128), L.nsrc), 128, 0, st>>>(cpart, cp_stride, nsb, nb, coef,
                                                                       2 * (int64_t)L.k);
 }
@@ -694,11 +702,12 @@ void proj_update(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_stride
 template <typename R>
 void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_stride, zd* out, zd* cpart,
                 cudaStream_t st) {
-  const unsigned nsb = nblocks(L.g.V, BS);
+  const int spt = proj_spt(nvec);
+  const unsigned nsb = nblocks(L.g.V, BS * spt);
   const int64_t cp_stride = (int64_t)2 * L.k * nsb;
   // mode 1 makes side A dot the V basis
   k_proj_dots<R><<<dim3(nsb, nblocks(nvec, NB), L.nsrc), BS, 0, st>>>(L, nvec, 1, x, nullptr, x_stride,
-                                                                       cpart, cp_stride);
+                                                                       cpart, cp_stride, spt);
   k_proj_reduce<<<dim3(nblocks(2 * nvec, 128), L.nsrc), 128, 0, st>>>(cpart, cp_stride, nsb, nvec, out,
                                                                         2 * (int64_t)L.k);
 }

@@ -254,7 +254,7 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
   zd* t2 = e ? wsT<zd>(c, B_TMP2, n) : nullptr;
   int* ipiv = wsT<int>(c, B_IPIV, k);
   int* used = wsT<int>(c, B_COL, k);
-  Cand2* cand = wsT<Cand2>(c, B_PROW, 2 * ((k + 3) / 4) + 8);
+  unsigned long long* keys = wsT<unsigned long long>(c, B_PROW, k + 1);
   zd* w0 = wsT<zd>(c, B_W0, n);
   zd* w1 = wsT<zd>(c, B_W1, n);
   double* dstat = wsT<double>(c, B_DSTAT, 4);   // [0] diff^2, [1] norm^2, [2] log|det|
@@ -267,7 +267,7 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
   for (it = 1; it <= 100; ++it) {
     CK(cudaMemsetAsync(dstat, 0, 3 * sizeof(double), c->st));
     run(c, OV_KIND_DENSE, (int64_t)k + 3, [&] {
-      dense_inverse(a[cur], ai, w0, w1, k, ipiv, used, cand, dstat + 2, err_dev, c->st);
+      dense_inverse(a[cur], ai, w0, w1, k, ipiv, used, keys, dstat + 2, err_dev, c->st);
     });
     if (rec) {
       const int slot = it - 1;
