@@ -59,6 +59,7 @@ struct Rev {
   R* gv; R* gw;              // complete gradients of v_{j+1}, w_{j+1}: [src][vs]
   R* gv_new; R* gw_new;      // gradients being formed for v_j, w_j
   R* gr_ring; R* gs_ring; R* gp_ring;   // [m][src][vs]
+  R* hin;                    // conj(g_alpha) v_j + g_s of the current step: [src][vs]
   int m;                     // ring length
   const R* xbar;             // [src][vs]
   const zd* y;               // [src][k]
@@ -77,7 +78,7 @@ struct Rev {
 
 // ---- lattice launchers (precision R = double or float) ----
 template <typename R> void pack_spinors(const double* src_aos, R* dst, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
-// pack V sites into sites [off, off + V) of fields of Vf sites
+// Theorem-1 block start: r = (top, bot), s = (top + bot, bot) in fields of 2V sites (top may be null)
 template <typename R> void pack_block_start(const double* top_aos, const double* bot_aos, R* r, R* s, int nsrc,
                                             int64_t V, int64_t vs, cudaStream_t st);
 template <typename R> void unpack_spinors(const R* src, double* dst_aos, int nsrc, int64_t V, int64_t vs, cudaStream_t st);
@@ -111,6 +112,7 @@ template <typename R> void rev_dots(const Lat<R>& L, const Rev<R>& B, int j, cud
 template <typename R> void rev_form(const Lat<R>& L, const Rev<R>& B, int j, int slot, bool with_dots, cudaStream_t st);
 template <typename R> void rev_proj_record(const Lat<R>& L, const Rev<R>& B, int j, int m_index, const zd* coef, cudaStream_t st);
 template <typename R> void rev_alpha_dots(const Lat<R>& L, const Rev<R>& B, int j, int slot, cudaStream_t st);
+template <typename R> void rev_combine(const Lat<R>& L, const Rev<R>& B, int j, int slot, cudaStream_t st);
 template <typename R> void rev_stencil(const Lat<R>& L, const Rev<R>& B, int j, int slot, int prev_slot,
                                        int nrec, cudaStream_t st);
 template <typename R> void force_flush(const Lat<R>& L, const Rev<R>& B, const int* steps_dev, int nterms,

@@ -944,33 +944,49 @@ void rev_init(const Lat<R>& L, const Rev<R>& B, cudaStream_t st) {
   k_rev_init<<<nblocks(L.nsrc, 32), 32, 0, st>>>(L.sc, B.gaT, L.k, L.nsrc);
 }
 
-// Combination loader: a1 F1(s) + a2 F2(s) (either field may be null)
+// R3a: the two stencil inputs of step j, formed once per site
+//   g_p = g_r + g_alpha w_j  (into the ring, for the force too),   h_in = conj(g_alpha) v_j + g_s
+// (g_r, g_s are absent at the last step j = k - 1).
 template <typename R>
-struct Comb2 {
-  const R* f1; cplx<R> a1;
-  const R* f2; cplx<R> a2;
-  int64_t V;
-  __device__ __forceinline__ void operator()(int64_t s, Spinor<R>& o) const {
-    Spinor<R> t;
-    spinor_zero(o);
-    if (f1) {
-      load_spinor(f1, V, s, t);
+__global__ void __launch_bounds__(BS) k_rev_combine(Lat<R> L, Rev<R> B, int j, int slot) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  const int64_t V = L.g.V;
+  if (x >= V) return;
+  const cplx<R> ga = cast<R>(L.sc[src].g_alpha);
+  const bool carry = j < L.k - 1;
+  Spinor<R> a, e;
+  load_spinor(L.basis_w(src, j), V, x, e);
+  if (carry) {
+    load_spinor(B.ring(B.gr_ring, slot, src), V, x, a);
 #pragma unroll
-      for (int c = 0; c < 12; ++c) cmac(o.c[c], a1, t.c[c]);
-    }
-    if (f2) {
-      load_spinor(f2, V, s, t);
+    for (int c = 0; c < 12; ++c) cmac(a.c[c], ga, e.c[c]);
+  } else {
 #pragma unroll
-      for (int c = 0; c < 12; ++c) cmac(o.c[c], a2, t.c[c]);
-    }
+    for (int c = 0; c < 12; ++c) a.c[c] = ga * e.c[c];
   }
-};
+  store_spinor(B.ring(B.gp_ring, slot, src), V, x, a);
+  const cplx<R> gac = conj(ga);
+  load_spinor(L.basis_v(src, j), V, x, e);
+  if (carry) {
+    load_spinor(B.ring(B.gs_ring, slot, src), V, x, a);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) cmac(a.c[c], gac, e.c[c]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) a.c[c] = gac * e.c[c];
+  }
+  store_spinor(B.hin + src * L.vs, V, x, a);
+}
+template <typename R>
+void rev_combine(const Lat<R>& L, const Rev<R>& B, int j, int slot, cudaStream_t st) {
+  k_rev_combine<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j, slot);
+}
 
-// R3: complete gradients of v_j and w_j
-//   g_p = g_r + g_alpha w_j,  g_q = g_s
+// R3b: complete gradients of v_j and w_j
 //   Gv_j = -conj(beta_{j+1}) g_r' - conj(alpha_j) g_r + conj(y_j) xbar + H^dag g_p + acc_v
-//   Gw_j = -delta_{j+1} g_s' - alpha_j g_s + H (conj(g_alpha) v_j + g_s) + acc_w
-// (primes: the previous step's g_r, g_s).  g_p goes to the ring for the force.
+//   Gw_j = -delta_{j+1} g_s' - alpha_j g_s + H h_in + acc_w
+// (primes: the previous step's g_r, g_s; g_p and h_in from R3a).
 template <typename R>
 __global__ void __launch_bounds__(BS) k_rev_stencil(Lat<R> L, Rev<R> B, int j, int slot, int prev_slot,
                                                      int nrec) {
@@ -978,30 +994,14 @@ __global__ void __launch_bounds__(BS) k_rev_stencil(Lat<R> L, Rev<R> B, int j, i
   const int src = blockIdx.y;
   const int64_t V = L.g.V;
   if (x >= V) return;
-  const SrcScal& sc = L.sc[src];
   const int64_t o = (int64_t)src * L.k + j;
-  const cplx<R> ga = cast<R>(sc.g_alpha);
   const cplx<R> al = cast<R>(L.alpha[o]);
   const cplx<R> yj = cast<R>(B.y[(int64_t)src * L.k + j]);
   const R* gr = slot >= 0 && j < L.k - 1 ? B.ring(B.gr_ring, slot, src) : nullptr;
   const R* gs = slot >= 0 && j < L.k - 1 ? B.ring(B.gs_ring, slot, src) : nullptr;
-  const R* wj = L.basis_w(src, j);
-  const R* vj = L.basis_v(src, j);
-  const cplx<R> one = mk<R>(1, 0);
   Spinor<R> hv, hw, t;
-  // H^dag g_p
-  {
-    Comb2<R> ld{gr, one, wj, ga, V};
-    h_site_ld(ld, L.u, L.g, x, L.kappa, L.efinv, L.ef, hv);
-    Spinor<R> gp;
-    ld(x, gp);
-    store_spinor(B.ring(B.gp_ring, slot, src), V, x, gp);
-  }
-  // H (conj(g_alpha) v_j + g_s)
-  {
-    Comb2<R> ld{vj, conj(ga), gs, one, V};
-    h_site_ld(ld, L.u, L.g, x, L.kappa, L.ef, L.efinv, hw);
-  }
+  h_site_ld(FieldLoad<R>{B.ring(B.gp_ring, slot, src), V}, L.u, L.g, x, L.kappa, L.efinv, L.ef, hv);
+  h_site_ld(FieldLoad<R>{B.hin + src * L.vs, V}, L.u, L.g, x, L.kappa, L.ef, L.efinv, hw);
   load_spinor(B.xbar + src * L.vs, V, x, t);
 #pragma unroll
   for (int c = 0; c < 12; ++c) cmac(hv.c[c], conj(yj), t.c[c]);
@@ -1197,6 +1197,7 @@ void eps_norms(const double* a_top, const double* a_bot, const double* b, int ns
   template void rev_form<R>(const Lat<R>&, const Rev<R>&, int, int, bool, cudaStream_t);                 \
   template void rev_proj_record<R>(const Lat<R>&, const Rev<R>&, int, int, const zd*, cudaStream_t);     \
   template void rev_alpha_dots<R>(const Lat<R>&, const Rev<R>&, int, int, cudaStream_t);                 \
+  template void rev_combine<R>(const Lat<R>&, const Rev<R>&, int, int, cudaStream_t);                    \
   template void rev_stencil<R>(const Lat<R>&, const Rev<R>&, int, int, int, int, cudaStream_t);          \
   template void force_flush<R>(const Lat<R>&, const Rev<R>&, const int*, int, int, cudaStream_t);
 

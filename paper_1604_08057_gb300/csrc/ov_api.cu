@@ -17,7 +17,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
 };
 
 struct Status {
@@ -651,6 +651,7 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   B.gr_ring = wsT<R>(c, B_GR, (int64_t)m * nsrc * vs);
   B.gs_ring = wsT<R>(c, B_GS, (int64_t)m * nsrc * vs);
   B.gp_ring = wsT<R>(c, B_GP, (int64_t)m * nsrc * vs);
+  B.hin = wsT<R>(c, B_HIN, (int64_t)nsrc * vs);
   B.xbar = xb;
   B.y = y;
   B.gaT = gaT;
@@ -668,6 +669,7 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   B.dmu_cnt = wsT<unsigned>(c, B_DMUCNT, 4);
   zd* coef = wsT<zd>(c, B_COEF, (int64_t)nsrc * 2 * k);
   run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_init(L, B, c->st); });
+  run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_combine(L, B, k - 1, 0, c->st); });
   run(c, OV_KIND_REV_STENCIL, 1, [&] { rev_stencil(L, B, k - 1, 0, -1, 0, c->st); });
   std::swap(B.gv, B.gv_new);
   std::swap(B.gw, B.gw_new);
@@ -693,6 +695,7 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
       run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_alpha_dots(L, B, j, slot, c->st); });
       ++nrec;
     }
+    run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_combine(L, B, j, slot, c->st); });
     run(c, OV_KIND_REV_STENCIL, 1, [&] { rev_stencil(L, B, j, slot, prev, nrec, c->st); });
     std::swap(B.gv, B.gv_new);
     std::swap(B.gw, B.gw_new);
