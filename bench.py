@@ -54,8 +54,9 @@ def parse_args():
     ap.add_argument("--passes", type=int, default=1)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
     ap.add_argument("--cpu-k", type=int, default=4, help="Lanczos steps of the oracle sample")
-    ap.add_argument("--leg", default="all", choices=["all", "stencil"],
-                    help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling)")
+    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch"],
+                    help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling); "
+                         "batch: the uneven batch of 32 problems (forward + VJP) through ov_tsl_batch")
     return ap.parse_args()
 
 
@@ -365,6 +366,37 @@ def e2e_leg(args, ut, bt, xt, wl, k):
             "d2h_bytes_per_step": int(d2h), "steps": steps}
 
 
+def batch_leg(args, workers=(1, 4), nprob=32):
+    """Uneven batch: 32 problems on 8^4, 6x12^3 and 14^4 lattices with mu in
+    {0.1, 0.3, 0.5} and k in 300..1000, forward + VJP each, through
+    ov_tsl_batch; one warm-up and one timed batch per worker count."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    links, probs = inputs.uneven_batch(nprob)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ut = {d: torch.tensor(u, device=dev) for d, u in links.items()}
+    problems = [dict(u=ut[p["dims"]], mu=p["mu"], m_w=p["m_w"], b=torch.tensor(p["b"], device=dev), k=p["k"],
+                     xbar=torch.tensor(p["xbar"], device=dev)) for p in probs]
+    ctx = binding.context(args.precision, args.rebiorth, args.passes)
+    out = {"problems": nprob, "k_total": int(sum(p["k"] for p in probs)),
+           "lattices": ["8x8x8x8", "12x12x12x6", "14x14x14x14"], "work": "forward + VJP per problem"}
+    for nw in workers:
+        binding.tsl_batch(problems, nworkers=nw, precision=args.precision, rebiorth=args.rebiorth,
+                          passes=args.passes, check=False)
+        torch.cuda.synchronize()
+        l0 = binding.launch_count(ctx)
+        t0 = time.perf_counter()
+        res = binding.tsl_batch(problems, nworkers=nw, precision=args.precision, rebiorth=args.rebiorth,
+                                passes=args.passes, check=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = [r["status"] for r in res]
+        out[f"workers_{nw}"] = {"s": round(dt, 3), "s_per_problem": round(dt / nprob, 4),
+                                "gpu_launches": binding.launch_count(ctx) - l0,
+                                "ok": sum(1 for x in st if x == 0), "statuses": sorted(set(st))}
+    return out
+
+
 def stencil_leg(args, ut, wl, hbm, peak_src, nsrc=32, reps=20):
     """ov_apply_H on nsrc sources sharing the links (working set > L2): live kernel time."""
     import torch
@@ -500,6 +532,12 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
+    if args.leg == "batch":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"leg": "uneven_batch", "precision": args.precision, "rebiorth_period": args.rebiorth,
+                          "gs_passes": args.passes, **batch_leg(args)}))
+        return
     if args.leg == "stencil":
         import torch
         torch.cuda.set_device(local_rank)

@@ -111,6 +111,37 @@ int ov_tsl_sign_vjp(ov_context *ctx, const int32_t dims[4], const void *U, doubl
                     double m_w, int32_t nsrc, const void *b, int32_t k, const void *xbar,
                     void *x, void *dU, double *dmu, ov_tsl_info *info);
 
+/* One problem of an uneven batch: the arguments of ov_tsl_sign (xbar = NULL)
+ * or of ov_tsl_sign_vjp (xbar != NULL) for one lattice, mu and k, and its
+ * outputs: info and status (OV_OK or the call's error code). */
+typedef struct {
+  int32_t dims[4];
+  const void *U;
+  double mu, m_w;
+  int32_t nsrc;
+  const void *b;
+  int32_t k;
+  const void *xbar;           /* NULL: forward only */
+  void *x;                    /* forward result (may be NULL with xbar) */
+  void *dU;                   /* with xbar: link gradient */
+  double *dmu;                /* with xbar: host double */
+  ov_tsl_info info;           /* out */
+  int32_t status;             /* out */
+} ov_problem;
+
+/* Uneven batch (problems on different lattices, mu and k; not in the paper,
+ * which treats one problem at a time): the problems run concurrently on
+ * nworkers (1..16) worker contexts, each with its own stream and workspace,
+ * owned by ctx and kept for later batches; a problem runs exactly as the
+ * corresponding single call on a context with ctx's options and tuned stencil
+ * variants, so its results equal that call's bit for bit.  The most expensive
+ * problems (V k^2 nsrc, VJP twice the forward) are started first.  Work on
+ * ctx's stream before the call is ordered before the problems, and the
+ * problems before later work on it.  Each worker context allocates workspace
+ * for the largest problem it runs.  Returns OV_OK, or the status of the first
+ * failed problem in batch order (every problem's status is in probs[i].status). */
+int ov_tsl_batch(ov_context *ctx, int32_t nprob, ov_problem *probs, int32_t nworkers);
+
 /* Launch-shape autotuner.  Times every compiled variant of the two stencil
  * kernels -- ov_apply_H (sources per thread x threads per block) and the
  * TSL step's H/H^dagger pair (both products sharing each link load in one

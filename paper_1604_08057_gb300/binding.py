@@ -53,10 +53,17 @@ class Info(ctypes.Structure):
                 "newton_iters_adj": self.newton_iters_adj, "t_ms": list(self.t_ms)}
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 4), ("U", ctypes.c_void_p), ("mu", ctypes.c_double),
+                ("m_w", ctypes.c_double), ("nsrc", ctypes.c_int32), ("b", ctypes.c_void_p), ("k", ctypes.c_int32),
+                ("xbar", ctypes.c_void_p), ("x", ctypes.c_void_p), ("dU", ctypes.c_void_p),
+                ("dmu", ctypes.c_void_p), ("info", Info), ("status", ctypes.c_int32)]
+
+
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
-           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_strerror"]
+           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -82,6 +89,7 @@ def load(path: str = LIB_PATH):
     lib.ov_tsl_coefficients.argtypes = [P, I32, I32, P, P, P]
     lib.ov_tsl_sign_jvp.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, P, ctypes.POINTER(Info)]
     lib.ov_block_tsl_sign.argtypes = [P, dims_t, P, D, D, I32, P, P, I32, P, D, P, P, ctypes.POINTER(Info)]
+    lib.ov_tsl_batch.argtypes = [P, I32, ctypes.POINTER(Problem), I32]
     lib.ov_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, ctypes.POINTER(Info)]
     lib.ov_block_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, ctypes.POINTER(Info)]
     lib.ov_profile_enable.argtypes = [P, I32]
@@ -274,6 +282,50 @@ def block_tsl_eps(u, mu, m_w, b, k, e=None, m_dir=0.0, precision="fp64", rebiort
                                 _ptr(e) if e is not None else None, float(m_dir),
                                 eps.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info)), "ov_block_tsl_eps")
     return float(eps[0]) if single else eps
+
+
+def tsl_batch(problems, nworkers=4, precision="fp64", rebiorth=1, passes=2, check=True):
+    """Uneven batch: each problem is a dict with u, mu, m_w, b, k and optionally
+    xbar (then the VJP is computed).  Returns one dict per problem with x and,
+    with xbar, dU and dmu; plus info and status."""
+    lib = load()
+    n = len(problems)
+    arr = (Problem * max(n, 1))()
+    keep, outs = [], []
+    for i, pr in enumerate(problems):
+        u = pr["u"].contiguous()
+        dims = _dims(u)
+        bb, single = _spinors(pr["b"], u)
+        xb = None
+        if pr.get("xbar") is not None:
+            xb, _ = _spinors(pr["xbar"], u)
+            if xb.shape != bb.shape:
+                raise ValueError("xbar must have the shape of b")
+        x = torch.empty_like(bb)
+        du = torch.empty_like(u) if xb is not None else None
+        dmu = ctypes.c_double(0.0)
+        p = arr[i]
+        for d in range(4):
+            p.dims[d] = dims[d]
+        p.U, p.mu, p.m_w, p.nsrc = u.data_ptr(), float(pr["mu"]), float(pr["m_w"]), bb.shape[0]
+        p.b, p.k = bb.data_ptr(), int(pr["k"])
+        p.xbar = xb.data_ptr() if xb is not None else None
+        p.x = x.data_ptr()
+        p.dU = du.data_ptr() if du is not None else None
+        p.dmu = ctypes.addressof(dmu) if xb is not None else None
+        keep.append((u, bb, xb, dmu))
+        outs.append((x, du, dmu, single))
+    ctx = context(precision, rebiorth, passes)
+    status = lib.ov_tsl_batch(ctx, n, arr, int(nworkers))
+    res = []
+    for i, (x, du, dmu, single) in enumerate(outs):
+        r = {"x": x[0] if single else x, "status": arr[i].status, "info": arr[i].info.as_dict()}
+        if du is not None:
+            r["dU"], r["dmu"] = du, dmu.value
+        res.append(r)
+    if check:
+        _check(status, "ov_tsl_batch")
+    return res
 
 
 def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2):

@@ -2,6 +2,9 @@
 // host-side driver that enqueues the kernels of the forward two-sided Lanczos
 // recurrence, the k x k sign, the reverse sweep and the force contraction.
 #include <cmath>
+#include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -68,6 +71,8 @@ struct ov_context {
   int64_t launches = 0;
   int tuned_apply[2] = {0, 0};  // per precision (OV_FP64, OV_MIXED)
   int tuned_pair[2] = {0, 0};
+  bool owns_stream = false;     // worker contexts of ov_tsl_batch own theirs
+  std::vector<ov_context*> workers;
 };
 
 namespace {
@@ -821,6 +826,8 @@ int ov_context_create(ov_context** ctx, const ov_options* opt, void* stream) {
 
 int ov_context_destroy(ov_context* c) {
   if (!c) return OV_ERR_INVALID_ARG;
+  for (ov_context* w : c->workers) ov_context_destroy(w);
+  c->workers.clear();
   cudaStreamSynchronize(c->st);
   for (int i = 0; i < NBUF; ++i)
     if (c->buf[i]) cudaFree(c->buf[i]);
@@ -833,6 +840,7 @@ int ov_context_destroy(ov_context* c) {
     }
     delete c->prof;
   }
+  if (c->owns_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
   return OV_OK;
 }
@@ -965,6 +973,93 @@ int ov_block_tsl_eps(ov_context* c, const int32_t dims[4], const void* U, double
                ? eps_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, true, E, m_dir, eps, info)
                : eps_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, true, E, m_dir, eps, info);
   });
+}
+
+int ov_tsl_batch(ov_context* c, int32_t nprob, ov_problem* probs, int32_t nworkers) {
+  if (!c || nprob < 0 || (nprob > 0 && !probs) || nworkers < 1 || nworkers > 16) return OV_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < nprob; ++i) probs[i].status = OV_OK;
+  if (nprob == 0) return OV_OK;
+  const int nw = std::min<int>(nworkers, nprob);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return OV_ERR_CUDA;
+  }
+  while ((int)c->workers.size() < nw) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return OV_ERR_CUDA;
+    }
+    ov_context* w = nullptr;
+    const int st = ov_context_create(&w, &c->opt, s);
+    if (st != OV_OK) {
+      cudaStreamDestroy(s);
+      return st;
+    }
+    w->owns_stream = true;
+    c->workers.push_back(w);
+  }
+  // most work first (V k^2 per source; the VJP about twice the forward)
+  std::vector<int> order(nprob);
+  std::vector<double> cost(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    const ov_problem& p = probs[i];
+    const double V = (double)p.dims[0] * p.dims[1] * p.dims[2] * p.dims[3];
+    cost[i] = V * (double)p.k * p.k * std::max(1, p.nsrc) * (p.xbar ? 2.0 : 1.0);
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  // the caller's stream orders the inputs before the workers and the workers before later work
+  cudaEvent_t start = nullptr;
+  std::vector<cudaEvent_t> done(nw, nullptr);
+  if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(start, c->st) != cudaSuccess) {
+    cudaGetLastError();
+    if (start) cudaEventDestroy(start);
+    return OV_ERR_CUDA;
+  }
+  std::vector<int64_t> l0(nw);
+  for (int w = 0; w < nw; ++w) {
+    ov_context* wc = c->workers[w];
+    wc->opt = c->opt;
+    std::copy(c->tuned_apply, c->tuned_apply + 2, wc->tuned_apply);
+    std::copy(c->tuned_pair, c->tuned_pair + 2, wc->tuned_pair);
+    cudaStreamWaitEvent(wc->st, start, 0);
+    l0[w] = wc->launches;
+  }
+  std::atomic<int> next{0};
+  auto work = [&](ov_context* wc) {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int n = next.fetch_add(1);
+      if (n >= nprob) break;
+      ov_problem& p = probs[order[n]];
+      p.status = p.xbar ? ov_tsl_sign_vjp(wc, p.dims, p.U, p.mu, p.m_w, p.nsrc, p.b, p.k, p.xbar, p.x, p.dU,
+                                          p.dmu, &p.info)
+                        : ov_tsl_sign(wc, p.dims, p.U, p.mu, p.m_w, p.nsrc, p.b, p.k, p.x, &p.info);
+    }
+  };
+  std::vector<std::thread> threads;
+  for (int w = 1; w < nw; ++w) threads.emplace_back(work, c->workers[w]);
+  work(c->workers[0]);
+  for (auto& t : threads) t.join();
+  int status = OV_OK;
+  for (int w = 0; w < nw; ++w) {
+    ov_context* wc = c->workers[w];
+    c->launches += wc->launches - l0[w];
+    if (cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(done[w], wc->st) == cudaSuccess)
+      cudaStreamWaitEvent(c->st, done[w], 0);
+    else if (status == OV_OK)
+      status = OV_ERR_CUDA;
+  }
+  cudaEventDestroy(start);
+  for (auto e : done)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  for (int32_t i = 0; i < nprob && status == OV_OK; ++i) status = probs[i].status;
+  return status;
 }
 
 int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, double* beta, double* delta) {

@@ -44,3 +44,31 @@ def test_strerror_without_gpu():
     lib = binding.load(build.build())
     assert lib.ov_strerror(-3).decode().startswith("Lanczos breakdown")
     assert lib.ov_strerror(0).decode() == "success"
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """Sizes and field offsets of the ABI structs as gcc lays them out from ov.h
+    equal those of the binding's ctypes mirrors."""
+    import shutil
+    import subprocess
+    import pytest
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    structs = {"ov_options": binding.Options, "ov_tsl_info": binding.Info,
+               "ov_tune_report": binding.TuneReport, "ov_problem": binding.Problem}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ov.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)

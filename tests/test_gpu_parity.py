@@ -320,3 +320,36 @@ def test_block_tsl_jvp_mixed_well_conditioned():
     rdx, rx, _ = tsl.block_tsl(u, b, mu, m_w, k, e, 0.5)
     assert rel(dx.cpu().numpy(), rdx) <= 1e-4
     assert rel(x.cpu().numpy(), rx) <= 1e-4
+
+
+# ---------------------------------------------------------------------------
+# uneven batch
+# ---------------------------------------------------------------------------
+def test_uneven_batch_equals_single_calls():
+    specs = [((3, 3, 3, 3), 0.3, 40, False, 1), ((3, 5, 2, 4), 0.1, 50, True, 2), ((4, 4, 4, 4), 0.5, 60, True, 1)]
+    probs = []
+    for n, (dims, mu, k, vjp_, nsrc) in enumerate(specs):
+        u, b, xbar = case(dims, 0.3, 20 + n, nsrc)
+        bb = b if nsrc > 1 else b[0]
+        xb = (xbar if nsrc > 1 else xbar[0]) if vjp_ else None
+        probs.append(dict(u=T(u), mu=mu, m_w=-1.0, b=T(bb), k=k, xbar=T(xb) if xb is not None else None))
+    res = binding.tsl_batch(probs, nworkers=3, rebiorth=10, passes=2)
+    for pr, r in zip(probs, res):
+        assert r["status"] == 0
+        if pr["xbar"] is None:
+            x = binding.tsl_sign(pr["u"], pr["mu"], pr["m_w"], pr["b"], pr["k"], rebiorth=10, passes=2)
+            assert torch.equal(r["x"], x)
+        else:
+            du, dmu, x = binding.tsl_sign_vjp(pr["u"], pr["mu"], pr["m_w"], pr["b"], pr["k"], pr["xbar"],
+                                              rebiorth=10, passes=2)
+            assert torch.equal(r["x"], x) and torch.equal(r["dU"], du) and r["dmu"] == dmu
+
+
+def test_uneven_batch_reports_each_problem_status():
+    u, b, _ = case((3, 3, 3, 3), 0.3, 23, 1)
+    good = dict(u=T(u), mu=0.3, m_w=-1.0, b=T(b[0]), k=30)
+    bad = dict(u=T(u), mu=0.3, m_w=-1.0, b=T(b[0]), k=1)      # k < 2: invalid
+    res = binding.tsl_batch([good, bad, good], nworkers=2, check=False)
+    assert [r["status"] for r in res] == [0, -1, 0]
+    assert torch.equal(res[0]["x"], res[2]["x"])
+    assert torch.equal(res[0]["x"], binding.tsl_sign(good["u"], 0.3, -1.0, good["b"], 30))
