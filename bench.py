@@ -277,7 +277,7 @@ def run_ours(args, rank, world, local_rank):
                     "hbm_view": {"achieved_GB_s": round(gbs, 1), "peak": hbm, "frac": round(gbs / hbm, 3)},
                     **per_launch}
         if dom == "proj_dots":
-            # ncu: DRAM bytes of a two-sided k_proj_dots launch = 1.085 x its algorithmic
+            # ncu: DRAM bytes of a two-sided k_proj_dots launch = 1.050 x its algorithmic
             # bytes (14x14^3, k = 120, nb = 101); traffic grows with the fields streamed
             roofline["traffic"] = int(PROJ_DOTS_TRAFFIC_RATIO * per_launch["algorithmic_bytes_per_launch"])
             roofline["traffic_source"] = ("ncu dram bytes of one k_proj_dots launch at 14x14^3, k=120, nb=101 "
@@ -312,7 +312,7 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-PROJ_DOTS_TRAFFIC_RATIO = 1.085
+PROJ_DOTS_TRAFFIC_RATIO = 1.050
 
 
 def fp64_peak(dev, n=4096, reps=3):
