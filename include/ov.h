@@ -62,7 +62,13 @@ typedef struct {
   int32_t precision;   /* OV_FP64 or OV_MIXED */
   int32_t rebiorth;    /* 0: none; 1: every step; P > 1: at the two steps j = 0, 1 (mod P) */
   int32_t passes;      /* classical Gram-Schmidt passes per re-biorthogonalisation (1 or 2) */
-  int32_t reserved[5];
+  int32_t segment;     /* 0: keep all k basis vectors in device memory.  S > 0: two-pass TSL
+                        * (Sec. 4.1) with segment replay: the recurrence keeps a window of
+                        * S + 2 basis vectors, checkpoints its state every S steps, and
+                        * recomputes each segment bit for bit when x = V_k y, g_y = V_k^dag xbar
+                        * and the reverse sweep need its vectors.  Requires rebiorth = 0 (every
+                        * projection reads the whole basis); not for the block TSL. */
+  int32_t reserved[4];
 } ov_options;
 
 typedef struct {

@@ -34,7 +34,7 @@ class OVError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
-                ("passes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class TuneReport(ctypes.Structure):
@@ -109,14 +109,15 @@ def _check(status: int, what: str):
         raise OVError(status, what)
 
 
-def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=None):
-    """A cached library context for (device, current stream, options)."""
+def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=None, segment: int = 0):
+    """A cached library context for (device, current stream, options).  segment > 0
+    selects the two-pass TSL with checkpoints every `segment` steps (rebiorth = 0)."""
     lib = load()
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     stream = torch.cuda.current_stream(dev).cuda_stream
-    key = (dev.index, stream, precision, rebiorth, passes)
+    key = (dev.index, stream, precision, rebiorth, passes, segment)
     if key not in _contexts:
-        opt = Options(_PREC[precision], rebiorth, passes)
+        opt = Options(_PREC[precision], rebiorth, passes, segment)
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             _check(lib.ov_context_create(ctypes.byref(h), ctypes.byref(opt), ctypes.c_void_p(stream)),
@@ -160,7 +161,7 @@ def apply_H(u, mu, m_w, psi, dagger=False, precision="fp64"):
     return out[0] if single else out
 
 
-def tsl_sign(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2, return_info=False):
+def tsl_sign(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2, return_info=False, segment=0):
     """x ~ sgn(H(mu)) b by k-step two-sided Lanczos (per source)."""
     lib = load()
     dims = _dims(u)
@@ -168,7 +169,7 @@ def tsl_sign(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2, return_in
     bb, single = _spinors(b, u)
     x = torch.empty_like(bb)
     info = Info()
-    ctx = context(precision, rebiorth, passes)
+    ctx = context(precision, rebiorth, passes, segment=segment)
     _check(lib.ov_tsl_sign(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
                            _ptr(x), ctypes.byref(info)), "ov_tsl_sign")
     x = x[0] if single else x
@@ -176,7 +177,7 @@ def tsl_sign(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2, return_in
 
 
 def tsl_sign_vjp(u, mu, m_w, b, k, xbar, precision="fp64", rebiorth=1, passes=2, want_x=True,
-                 return_info=False):
+                 return_info=False, segment=0):
     """(dU, dmu, x) for L = sum_src Re <xbar, x>."""
     lib = load()
     dims = _dims(u)
@@ -189,7 +190,7 @@ def tsl_sign_vjp(u, mu, m_w, b, k, xbar, precision="fp64", rebiorth=1, passes=2,
     du = torch.empty_like(u)
     dmu = ctypes.c_double(0.0)
     info = Info()
-    ctx = context(precision, rebiorth, passes)
+    ctx = context(precision, rebiorth, passes, segment=segment)
     _check(lib.ov_tsl_sign_vjp(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
                                _ptr(xb), _ptr(x) if x is not None else None, _ptr(du),
                                ctypes.byref(dmu), ctypes.byref(info)), "ov_tsl_sign_vjp")
@@ -250,7 +251,7 @@ def block_tsl_sign(u, mu, m_w, top, bottom, k, e=None, m_dir=0.0, precision="fp6
     return (zt, zb, info.as_dict()) if return_info else (zt, zb)
 
 
-def tsl_eps(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2):
+def tsl_eps(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2, segment=0):
     """eps_A = ||sgn(H)^2 b - b|| / (2 ||b||) per source (Sec. 4.1, Eq. error_est)."""
     import numpy as np
     lib = load()
@@ -259,7 +260,7 @@ def tsl_eps(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2):
     bb, single = _spinors(b, u)
     eps = np.zeros(bb.shape[0], dtype=np.float64)
     info = Info()
-    ctx = context(precision, rebiorth, passes)
+    ctx = context(precision, rebiorth, passes, segment=segment)
     _check(lib.ov_tsl_eps(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
                           eps.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info)), "ov_tsl_eps")
     return float(eps[0]) if single else eps
@@ -284,7 +285,7 @@ def block_tsl_eps(u, mu, m_w, b, k, e=None, m_dir=0.0, precision="fp64", rebiort
     return float(eps[0]) if single else eps
 
 
-def tsl_batch(problems, nworkers=4, precision="fp64", rebiorth=1, passes=2, check=True):
+def tsl_batch(problems, nworkers=4, precision="fp64", rebiorth=1, passes=2, check=True, segment=0):
     """Uneven batch: each problem is a dict with u, mu, m_w, b, k and optionally
     xbar (then the VJP is computed).  Returns one dict per problem with x and,
     with xbar, dU and dmu; plus info and status."""
@@ -315,7 +316,7 @@ def tsl_batch(problems, nworkers=4, precision="fp64", rebiorth=1, passes=2, chec
         p.dmu = ctypes.addressof(dmu) if xb is not None else None
         keep.append((u, bb, xb, dmu))
         outs.append((x, du, dmu, single))
-    ctx = context(precision, rebiorth, passes)
+    ctx = context(precision, rebiorth, passes, segment=segment)
     status = lib.ov_tsl_batch(ctx, n, arr, int(nworkers))
     res = []
     for i, (x, du, dmu, single) in enumerate(outs):
@@ -328,11 +329,11 @@ def tsl_batch(problems, nworkers=4, precision="fp64", rebiorth=1, passes=2, chec
     return res
 
 
-def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2):
+def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2, segment=0):
     """(alpha, beta, delta) of the last TSL call on the matching context (host numpy)."""
     import numpy as np
     lib = load()
-    ctx = context(precision, rebiorth, passes)
+    ctx = context(precision, rebiorth, passes, segment=segment)
     a = np.zeros(k, dtype=np.complex128)
     b = np.zeros(k, dtype=np.complex128)
     d = np.zeros(k, dtype=np.float64)

@@ -32,8 +32,8 @@ struct Lat {
   const R* u;                // internal links (link_reals<R>() * V reals)
   int nsrc, k;
   int64_t vs;                // reals per lattice vector (padded)
-  R* bv;                     // basis V: [src][k][vs]
-  R* bw;                     // basis W: [src][k][vs]
+  R* bv;                     // basis V: [src][kcap][vs]
+  R* bw;                     // basis W: [src][kcap][vs]
   R* p; R* q; R* r; R* s;    // per-source scratch vectors [src][vs]
   SrcScal* sc;               // [src]
   zd* alpha;                 // [src][k]
@@ -49,8 +49,10 @@ struct Lat {
   Geom gl;
   const R* ue;               // links of the direction E (internal layout) or null
   R mdir;                    // mu direction
-  OV_HD R* basis_v(int src, int j) const { return bv + ((int64_t)src * k + j) * vs; }
-  OV_HD R* basis_w(int src, int j) const { return bw + ((int64_t)src * k + j) * vs; }
+  // basis window: vectors jbase .. jbase + kcap - 1 (all k from 0 unless segments are replayed)
+  int kcap, jbase;
+  OV_HD R* basis_v(int src, int j) const { return bv + ((int64_t)src * kcap + (j - jbase)) * vs; }
+  OV_HD R* basis_w(int src, int j) const { return bw + ((int64_t)src * kcap + (j - jbase)) * vs; }
 };
 
 // reverse-sweep buffers
@@ -102,7 +104,13 @@ template <typename R> void proj_update(const Lat<R>& L, int j, int mode, R* a, R
                                        const zd* coef, bool finalize_omega, cudaStream_t st, bool small);
 template <typename R> void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_src_stride, zd* out,
                                       zd* cpart, cudaStream_t st);
+// out[src][2 (j - j0)] = v_j^dag x  for j0 <= j < j0 + nvec
+template <typename R> void basis_dots_range(const Lat<R>& L, int j0, int nvec, const R* x, int64_t x_src_stride,
+                                            zd* out, zd* cpart, cudaStream_t st);
 template <typename R> void combine(const Lat<R>& L, int nvec, const zd* y, double* out_aos, cudaStream_t st);
+// out (+)= sum_{j0 <= j < j0 + nvec} y_j v_j  (accumulate when acc is set)
+template <typename R> void combine_range(const Lat<R>& L, int j0, int nvec, const zd* y, double* out_aos, bool acc,
+                                         cudaStream_t st);
 void eps_norms(const double* a_top, const double* a_bot, const double* b, int nsrc, int64_t n, double* out,
                cudaStream_t st);
 

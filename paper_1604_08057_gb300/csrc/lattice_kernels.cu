@@ -536,7 +536,7 @@ static inline int proj_spt(int nb) { return nb >= NB ? 4 : 1; }
 template <typename R>
 __global__ void __launch_bounds__(BS) k_proj_dots(Lat<R> L, int nb, int mode, const R* __restrict__ a,
                                                    const R* __restrict__ b, int64_t ab_stride,
-                                                   zd* __restrict__ cpart, int64_t cp_stride, int spt) {
+                                                   zd* __restrict__ cpart, int64_t cp_stride, int spt, int ioff) {
   __shared__ zd scratch[2 * NB * 32];
   const int src = blockIdx.z;
   const int i0 = blockIdx.y * NB;
@@ -554,12 +554,12 @@ __global__ void __launch_bounds__(BS) k_proj_dots(Lat<R> L, int nb, int mode, co
     for (int t = 0; t < NB; ++t) {
       const int i = i0 + t;
       if (i < nb) {
-        const R* da = mode == 0 ? L.basis_w(src, i) : L.basis_v(src, i);
+        const R* da = mode == 0 ? L.basis_w(src, ioff + i) : L.basis_v(src, ioff + i);
         load_spinor(da, V, x, e);
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[2 * t].add(e.c[c], va.c[c]);
         if (b) {
-          const R* db = mode == 0 ? L.basis_v(src, i) : L.basis_w(src, i);
+          const R* db = mode == 0 ? L.basis_v(src, ioff + i) : L.basis_w(src, ioff + i);
           load_spinor(db, V, x, e);
 #pragma unroll
           for (int c = 0; c < 12; ++c) acc[2 * t + 1].add(e.c[c], vb.c[c]);
@@ -682,7 +682,7 @@ void proj_dots(const Lat<R>& L, int j, int mode, const R* a, const R* b, int64_t
   const unsigned nsb = nblocks(L.g.V, BS * spt);
   const int64_t cp_stride = (int64_t)2 * L.k * nsb;
   k_proj_dots<R><<<dim3(nsb, nblocks(nb, NB), L.nsrc), BS, 0, st>>>(L, nb, mode, a, b, ab_stride, cpart,
-                                                                     cp_stride, spt);
+                                                                     cp_stride, spt, 0);
   k_proj_reduce<<<dim3(nblocks(2 * nb, 128), L.nsrc), 128, 0, st>>>(cpart, cp_stride, nsb, nb, coef,
                                                                       2 * (int64_t)L.k);
 }
@@ -700,39 +700,48 @@ void proj_update(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_stride
 
 // out[src][i] = v_i^dag x  for i < nvec (dots of the V basis with one vector per source)
 template <typename R>
-void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_stride, zd* out, zd* cpart,
-                cudaStream_t st) {
+void basis_dots_range(const Lat<R>& L, int j0, int nvec, const R* x, int64_t x_stride, zd* out, zd* cpart,
+                      cudaStream_t st) {
   const int spt = proj_spt(nvec);
   const unsigned nsb = nblocks(L.g.V, BS * spt);
   const int64_t cp_stride = (int64_t)2 * L.k * nsb;
   // mode 1 makes side A dot the V basis
   k_proj_dots<R><<<dim3(nsb, nblocks(nvec, NB), L.nsrc), BS, 0, st>>>(L, nvec, 1, x, nullptr, x_stride,
-                                                                       cpart, cp_stride, spt);
+                                                                       cpart, cp_stride, spt, j0);
   k_proj_reduce<<<dim3(nblocks(2 * nvec, 128), L.nsrc), 128, 0, st>>>(cpart, cp_stride, nsb, nvec, out,
                                                                         2 * (int64_t)L.k);
+}
+template <typename R>
+void basis_dots(const Lat<R>& L, int nvec, const R* x, int64_t x_stride, zd* out, zd* cpart, cudaStream_t st) {
+  basis_dots_range(L, 0, nvec, x, x_stride, out, cpart, st);
 }
 
 // x[src] = sum_i y_i v_i, written as interleaved complex128 [src][V][12]
 template <typename R>
-__global__ void __launch_bounds__(BS) k_combine(Lat<R> L, int nvec, const zd* __restrict__ y,
-                                                 double* __restrict__ out) {
+__global__ void __launch_bounds__(BS) k_combine(Lat<R> L, int j0, int nvec, const zd* __restrict__ y,
+                                                 double* __restrict__ out, int accumulate) {
   __shared__ zd ys[64];
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int src = blockIdx.y;
   const int64_t V = L.g.V;
+  double2* o = reinterpret_cast<double2*>(out) + ((int64_t)src * V + x) * 12;
   zd acc[12];
 #pragma unroll
   for (int c = 0; c < 12; ++c) acc[c] = mk(0.0, 0.0);
+  if (accumulate && x < V) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) acc[c] = mk(o[c].x, o[c].y);
+  }
   for (int i0 = 0; i0 < nvec; i0 += 32) {
     const int n = min(32, nvec - i0);
     __syncthreads();
-    if (threadIdx.x < n) ys[threadIdx.x] = y[(int64_t)src * L.k + i0 + threadIdx.x];
+    if (threadIdx.x < n) ys[threadIdx.x] = y[(int64_t)src * L.k + j0 + i0 + threadIdx.x];
     __syncthreads();
     if (x < V) {
       Spinor<R> part, e;
       spinor_zero(part);
       for (int t = 0; t < n; ++t) {
-        load_spinor(L.basis_v(src, i0 + t), V, x, e);
+        load_spinor(L.basis_v(src, j0 + i0 + t), V, x, e);
         const cplx<R> yc = cast<R>(ys[t]);
 #pragma unroll
         for (int c = 0; c < 12; ++c) cmac(part.c[c], yc, e.c[c]);
@@ -742,14 +751,17 @@ __global__ void __launch_bounds__(BS) k_combine(Lat<R> L, int nvec, const zd* __
     }
   }
   if (x < V) {
-    double2* o = reinterpret_cast<double2*>(out) + ((int64_t)src * V + x) * 12;
 #pragma unroll
     for (int c = 0; c < 12; ++c) o[c] = make_double2(acc[c].re, acc[c].im);
   }
 }
 template <typename R>
+void combine_range(const Lat<R>& L, int j0, int nvec, const zd* y, double* out, bool acc, cudaStream_t st) {
+  k_combine<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, j0, nvec, y, out, acc ? 1 : 0);
+}
+template <typename R>
 void combine(const Lat<R>& L, int nvec, const zd* y, double* out, cudaStream_t st) {
-  k_combine<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, nvec, y, out);
+  combine_range(L, 0, nvec, y, out, false, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1192,6 +1204,8 @@ void eps_norms(const double* a_top, const double* a_bot, const double* b, int ns
                                bool);                                                                   \
   template void basis_dots<R>(const Lat<R>&, int, const R*, int64_t, zd*, zd*, cudaStream_t);            \
   template void combine<R>(const Lat<R>&, int, const zd*, double*, cudaStream_t);                        \
+  template void combine_range<R>(const Lat<R>&, int, int, const zd*, double*, bool, cudaStream_t);       \
+  template void basis_dots_range<R>(const Lat<R>&, int, int, const R*, int64_t, zd*, zd*, cudaStream_t); \
   template void rev_init<R>(const Lat<R>&, const Rev<R>&, cudaStream_t);                                 \
   template void rev_dots<R>(const Lat<R>&, const Rev<R>&, int, cudaStream_t);                            \
   template void rev_form<R>(const Lat<R>&, const Rev<R>&, int, int, bool, cudaStream_t);                 \

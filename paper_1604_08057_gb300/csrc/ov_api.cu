@@ -2,6 +2,7 @@
 // host-side driver that enqueues the kernels of the forward two-sided Lanczos
 // recurrence, the k x k sign, the reverse sweep and the force contraction.
 #include <cmath>
+#include <cstddef>
 #include <algorithm>
 #include <atomic>
 #include <thread>
@@ -20,7 +21,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
 };
 
 struct Status {
@@ -151,7 +152,7 @@ Geom make_geom(const int32_t dims[4]) {
 // fm = 2 sets up block mode: fields of 2V sites (upper and lower halves)
 template <typename R>
 Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc, int k,
-             bool basis, int fm = 1) {
+             bool basis, int fm = 1, int kcap = 0) {
   Lat<R> L{};
   L.g = make_geom(dims);
   L.gl = L.g;
@@ -175,9 +176,11 @@ Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, dou
     L.vs = ((48 * V + 63) / 64) * 64;
   }
   const int64_t Vf = L.g.V;
+  L.kcap = kcap > 0 ? kcap : k;
+  L.jbase = 0;
   if (basis) {
-    L.bv = wsT<R>(c, B_BV, (int64_t)nsrc * k * L.vs);
-    L.bw = wsT<R>(c, B_BW, (int64_t)nsrc * k * L.vs);
+    L.bv = wsT<R>(c, B_BV, (int64_t)nsrc * L.kcap * L.vs);
+    L.bw = wsT<R>(c, B_BW, (int64_t)nsrc * L.kcap * L.vs);
   }
   L.p = wsT<R>(c, B_P, nsrc * L.vs);
   L.q = wsT<R>(c, B_Q, nsrc * L.vs);
@@ -235,6 +238,107 @@ void forward_krylov(ov_context* c, Lat<R>& L) {
       }
     }
   }
+  launch_check();
+}
+
+// ---------------------------------------------------------------------------
+// Two-pass TSL with segment replay (options.segment = S > 0, no
+// re-biorthogonalisation).  Segments are aligned to the top: [k - S, k),
+// [k - 2S, k - S), ..., the lowest one possibly shorter.  The basis window holds
+// v_{j0-1} .. v_{j1} of the current segment [j0, j1).  At every segment start
+// the recurrence state (r, s, v_{j0-1}, w_{j0-1} and the per-source scalars) is
+// checkpointed; replaying a segment from its checkpoint runs the same kernels
+// on the same data, so it reproduces its vectors and coefficients bit for bit.
+// ---------------------------------------------------------------------------
+struct SegPlan {
+  int S = 0;
+  std::vector<int> lo, hi;   // ascending segments [lo[t], hi[t])
+};
+SegPlan seg_plan(int k, int S) {
+  SegPlan p;
+  p.S = S;
+  std::vector<int> b;
+  for (int x = k; x > 0; x -= S) b.push_back(x);
+  b.push_back(0);
+  for (int t = (int)b.size() - 1; t > 0; --t) {
+    p.lo.push_back(b[t]);
+    p.hi.push_back(b[t - 1]);
+  }
+  return p;
+}
+
+template <typename R>
+struct SegStore {
+  R *r, *s, *v, *w;   // [segment][src][vs]
+  SrcScal* sc;        // [segment][src]
+};
+template <typename R>
+SegStore<R> seg_store(ov_context* c, const Lat<R>& L, int nseg) {
+  const int64_t n = (int64_t)nseg * L.nsrc * L.vs;
+  return SegStore<R>{wsT<R>(c, B_CKR, n), wsT<R>(c, B_CKS, n), wsT<R>(c, B_CKV, n), wsT<R>(c, B_CKW, n),
+                     wsT<SrcScal>(c, B_CKSC, (int64_t)nseg * L.nsrc)};
+}
+// copy the window's first vector (v_{jbase}, w_{jbase}) of every source to or from a checkpoint
+template <typename R>
+void window_slot(ov_context* c, const Lat<R>& L, int slot, R* v, R* w, bool to_window) {
+  const size_t pitch = sizeof(R) * L.kcap * L.vs, width = sizeof(R) * L.vs;
+  R* bv = L.bv + (int64_t)slot * L.vs;
+  R* bw = L.bw + (int64_t)slot * L.vs;
+  if (to_window) {
+    CK(cudaMemcpy2DAsync(bv, pitch, v, width, width, L.nsrc, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpy2DAsync(bw, pitch, w, width, width, L.nsrc, cudaMemcpyDeviceToDevice, c->st));
+  } else {
+    CK(cudaMemcpy2DAsync(v, width, bv, pitch, width, L.nsrc, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpy2DAsync(w, width, bw, pitch, width, L.nsrc, cudaMemcpyDeviceToDevice, c->st));
+  }
+}
+// steps j0 .. j1-1 without re-biorthogonalisation; with `next`, also the stencil of
+// step j1, which writes v_{j1} and w_{j1} into the window
+template <typename R>
+void seg_steps(ov_context* c, Lat<R>& L, int j0, int j1, bool next) {
+  const int k = L.k;
+  const int jend = next ? j1 + 1 : j1;
+  for (int j = j0; j < jend; ++j) {
+    run(c, OV_KIND_STENCIL_PAIR, 1, [&] { tsl_stencil(L, j, j < k - 1, c->st, c->tuned_pair[c->opt.precision]); });
+    if (j == k - 1 || j == j1) break;
+    run(c, OV_KIND_UPDATE, 1, [&] { tsl_update(L, j, true, c->st); });
+  }
+}
+// pass 1: the recurrence over all segments, checkpointing each segment start
+template <typename R>
+void seg_forward(ov_context* c, Lat<R>& L, const SegPlan& P, const SegStore<R>& K) {
+  const int64_t fs = (int64_t)L.nsrc * L.vs;
+  run(c, OV_KIND_UPDATE, 1, [&] { tsl_init(L, c->st); });
+  for (size_t t = 0; t < P.lo.size(); ++t) {
+    const int j0 = P.lo[t];
+    if (t > 0) {
+      // v_{j0-1} moves from the end of the previous window to its first slot
+      window_slot(c, L, j0 - L.jbase - 1, K.v + (int64_t)t * fs, K.w + (int64_t)t * fs, false);
+      L.jbase = j0 - 1;
+      window_slot(c, L, 0, K.v + (int64_t)t * fs, K.w + (int64_t)t * fs, true);
+    } else {
+      L.jbase = j0 - 1;
+    }
+    CK(cudaMemcpyAsync(K.r + t * fs, L.r, sizeof(R) * fs, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(K.s + t * fs, L.s, sizeof(R) * fs, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(K.sc + t * L.nsrc, L.sc, sizeof(SrcScal) * L.nsrc, cudaMemcpyDeviceToDevice, c->st));
+    seg_steps(c, L, j0, P.hi[t], false);
+  }
+  launch_check();
+}
+// replay segment t from its checkpoint (with `next`: also v_{j1}, w_{j1})
+template <typename R>
+void seg_replay(ov_context* c, Lat<R>& L, const SegPlan& P, const SegStore<R>& K, int t, bool next) {
+  const int64_t fs = (int64_t)L.nsrc * L.vs;
+  const int j0 = P.lo[t];
+  L.jbase = j0 - 1;
+  if (t > 0) window_slot(c, L, 0, K.v + (int64_t)t * fs, K.w + (int64_t)t * fs, true);
+  CK(cudaMemcpyAsync(L.r, K.r + t * fs, sizeof(R) * fs, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(L.s, K.s + t * fs, sizeof(R) * fs, cudaMemcpyDeviceToDevice, c->st));
+  // only the forward scalars: the reverse sweep keeps its own in the same structs
+  CK(cudaMemcpy2DAsync(L.sc, sizeof(SrcScal), K.sc + t * L.nsrc, sizeof(SrcScal), offsetof(SrcScal, g_alpha),
+                       L.nsrc, cudaMemcpyDeviceToDevice, c->st));
+  seg_steps(c, L, j0, P.hi[t], next && P.hi[t] < L.k);
   launch_check();
 }
 
@@ -351,13 +455,22 @@ int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
                   const void* b, int k, void* x, ov_tsl_info* info) {
   check_ptr(b);
   check_ptr(x);
-  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true);
+  const int S = c->opt.segment > 0 && c->opt.segment < k ? c->opt.segment : 0;
+  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true, 1, S > 0 ? S + 2 : 0);
   run(c, OV_KIND_LAYOUT, 2, [&] {
     pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, L.g.V, L.vs, c->st);
     pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, L.g.V, L.vs, c->st);
   });
+  SegPlan P;
+  SegStore<R> K{};
   CK(cudaEventRecord(c->ev[0], c->st));
-  forward_krylov(c, L);
+  if (S > 0) {
+    P = seg_plan(k, S);
+    K = seg_store(c, L, (int)P.lo.size());
+    seg_forward(c, L, P, K);
+  } else {
+    forward_krylov(c, L);
+  }
   CK(cudaEventRecord(c->ev[1], c->st));
   auto hsc = read_scalars(c, L.sc, nsrc);
   int kr = k;
@@ -371,7 +484,17 @@ int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   st = sign_all(c, L, hsc, y, &iters);
   if (st != OV_OK) return st;
   CK(cudaEventRecord(c->ev[2], c->st));
-  run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
+  if (S > 0) {
+    // second pass: x = V_k y, one replayed segment at a time
+    for (size_t t = 0; t < P.lo.size(); ++t) {
+      seg_replay(c, L, P, K, (int)t, false);
+      run(c, OV_KIND_COMBINE, 1, [&] {
+        combine_range(L, P.lo[t], P.hi[t] - P.lo[t], y, static_cast<double*>(x), t > 0, c->st);
+      });
+    }
+  } else {
+    run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
+  }
   launch_check();
   CK(cudaEventRecord(c->ev[3], c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -397,7 +520,7 @@ int block_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, d
   check_ptr(out_bottom);
   if (top) check_ptr(top);
   if (E) check_ptr(E);
-  if (!std::isfinite(m_dir)) throw Status{OV_ERR_INVALID_ARG};
+  if (!std::isfinite(m_dir) || c->opt.segment > 0) throw Status{OV_ERR_INVALID_ARG};
   Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true, 2);
   const int64_t V = L.gl.V, Vf = L.g.V;
   if (E) {
@@ -506,14 +629,23 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   check_ptr(dU);
   if (!dmu) throw Status{OV_ERR_INVALID_ARG};
   if (x) check_ptr(x);
-  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true);
+  const int S = c->opt.segment > 0 && c->opt.segment < k ? c->opt.segment : 0;
+  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true, 1, S > 0 ? S + 2 : 0);
   const int64_t V = L.g.V, vs = L.vs;
   run(c, OV_KIND_LAYOUT, 2, [&] {
     pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, V, vs, c->st);
     pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, V, vs, c->st);
   });
+  SegPlan P;
+  SegStore<R> K{};
   CK(cudaEventRecord(c->ev[0], c->st));
-  forward_krylov(c, L);
+  if (S > 0) {
+    P = seg_plan(k, S);
+    K = seg_store(c, L, (int)P.lo.size());
+    seg_forward(c, L, P, K);
+  } else {
+    forward_krylov(c, L);
+  }
   CK(cudaEventRecord(c->ev[1], c->st));
   auto hsc = read_scalars(c, L.sc, nsrc);
   int kr = k;
@@ -529,7 +661,17 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   const int64_t nsb = (V + 127) / 128;
   zd* gy = wsT<zd>(c, B_GY, (int64_t)nsrc * 2 * k);
   zd* cpart = wsT<zd>(c, B_CPART, (int64_t)nsrc * 2 * k * nsb);
-  run(c, OV_KIND_COMBINE, 2, [&] { basis_dots(L, k, xb, vs, gy, cpart, c->st); });
+  if (S > 0) {
+    // second pass: g_y = V_k^dag xbar, one replayed segment at a time
+    for (size_t t = 0; t < P.lo.size(); ++t) {
+      seg_replay(c, L, P, K, (int)t, false);
+      run(c, OV_KIND_COMBINE, 2, [&] {
+        basis_dots_range(L, P.lo[t], P.hi[t] - P.lo[t], xb, vs, gy + 2 * P.lo[t], cpart, c->st);
+      });
+    }
+  } else {
+    run(c, OV_KIND_COMBINE, 2, [&] { basis_dots(L, k, xb, vs, gy, cpart, c->st); });
+  }
   launch_check();
   CK(cudaEventRecord(c->ev[2], c->st));
   // per source: y = beta0 sgn(T) e1 by Newton, recording the inverses; then
@@ -637,14 +779,31 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
     if (herr) return OV_ERR_SIGN_ILLPOSED;
   }
   CK(cudaEventRecord(c->ev[3], c->st));
-  if (x) run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
+  // (with segments, x is accumulated while the reverse sweep replays each segment)
+  int tcur = S > 0 ? (int)P.lo.size() - 1 : 0;   // the window holds the top segment after the second pass
+  auto seg_combine = [&](int t) {
+    if (x)
+      run(c, OV_KIND_COMBINE, 1, [&] {
+        combine_range(L, P.lo[t], P.hi[t] - P.lo[t], y, static_cast<double*>(x), t != (int)P.lo.size() - 1,
+                      c->st);
+      });
+  };
+  if (S > 0) {
+    seg_combine(tcur);
+  } else if (x) {
+    run(c, OV_KIND_COMBINE, 1, [&] { combine(L, k, y, static_cast<double*>(x), c->st); });
+  }
   CK(cudaEventRecord(c->ev[4], c->st));
   // reverse sweep
   std::vector<int> reb;
   for (int j = k - 2; j >= 0; --j)
     if (rebiorth_at(j + 1, c->opt.rebiorth)) reb.push_back(j);
   const int nreb_max = reb.empty() ? 1 : (int)reb.size();
-  const int m = k < 32 ? k : 32;
+  // force ring length; with segments a divisor of S, so that every flush ends at a segment boundary
+  int m = k < 32 ? k : 32;
+  if (S > 0)
+    for (m = std::min(32, S); S % m; --m) {
+    }
   Rev<R> B{};
   B.nsrc = nsrc;
   B.vs = vs;
@@ -684,6 +843,12 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
       run(c, OV_KIND_FORCE, 4, [&] { force_flush(L, B, nullptr, m, j0, c->st); });
       slot = 0;
       j0 = j;
+    }
+    if (S > 0 && j < P.lo[tcur]) {
+      // entering the segment below: its vectors (and v_{j+1}, w_{j+1}) from its checkpoint
+      --tcur;
+      seg_replay(c, L, P, K, tcur, true);
+      seg_combine(tcur);
     }
     const int prev = slot == 0 ? m - 1 : slot - 1;
     run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_dots(L, B, j, c->st); });
@@ -791,7 +956,8 @@ int guarded(F&& f) {
 }
 
 bool valid_options(const ov_options* o) {
-  return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4;
+  return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4 &&
+         o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0);
 }
 
 }  // namespace

@@ -7,6 +7,7 @@ of b by 1e-16 moves x by 1e-10 and dU by 9e-8 (full re-biorthogonalisation),
 so FP64 parity there is required to 10x those floors.  On the well-conditioned
 m_w = -1 points the floors are ~1e-14, and 1e-11 is required.
 """
+import ctypes
 import functools
 
 import numpy as np
@@ -353,3 +354,61 @@ def test_uneven_batch_reports_each_problem_status():
     assert [r["status"] for r in res] == [0, -1, 0]
     assert torch.equal(res[0]["x"], res[2]["x"])
     assert torch.equal(res[0]["x"], binding.tsl_sign(good["u"], 0.3, -1.0, good["b"], 30))
+
+
+# ---------------------------------------------------------------------------
+# two-pass TSL with segment replay (no re-biorthogonalisation)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("S", [7, 16, 49])
+def test_segment_replay_forward_matches_stored_basis(S):
+    dims, mu, m_w, k = (3, 5, 2, 4), 0.3, -1.0, 50
+    u, b, _ = case(dims, 0.3, 30, 2)
+    xs = binding.tsl_sign(T(u), mu, m_w, T(b), k, rebiorth=0)
+    co = [binding.tsl_coefficients(k, src=s, rebiorth=0) for s in range(2)]
+    xg = binding.tsl_sign(T(u), mu, m_w, T(b), k, rebiorth=0, segment=S)
+    cg = [binding.tsl_coefficients(k, src=s, rebiorth=0, segment=S) for s in range(2)]
+    for s in range(2):
+        for a, c in zip(co[s], cg[s]):
+            assert np.array_equal(a, c)                  # the replayed recurrence is bit for bit
+        assert rel(xg[s].cpu().numpy(), xs[s].cpu().numpy()) <= 1e-13
+        ref = tsl.tsl_forward(u, b[s], mu, m_w, k, rebiorth=0)
+        assert rel(xg[s].cpu().numpy(), ref.x) <= 1e-11
+
+
+@pytest.mark.parametrize("S", [7, 10, 25])
+def test_segment_replay_vjp_matches_stored_basis(S):
+    dims, mu, m_w, k = (3, 5, 2, 4), 0.3, -1.0, 50
+    u, b, xbar = case(dims, 0.3, 31, 2)
+    du, dmu, x = binding.tsl_sign_vjp(T(u), mu, m_w, T(b), k, T(xbar), rebiorth=0)
+    dug, dmug, xg = binding.tsl_sign_vjp(T(u), mu, m_w, T(b), k, T(xbar), rebiorth=0, segment=S)
+    assert rel(dug.cpu().numpy(), du.cpu().numpy()) <= 1e-12
+    assert abs(dmug - dmu) <= 1e-12 * abs(dmu)
+    assert rel(xg.cpu().numpy(), x.cpu().numpy()) <= 1e-13
+    du_o = np.zeros_like(u)
+    dmu_o = 0.0
+    for s in range(2):
+        d, m_, _ = vjp.tsl_vjp(u, b[s], mu, m_w, k, xbar[s], rebiorth=0)
+        du_o += d
+        dmu_o += m_
+    assert rel(dug.cpu().numpy(), du_o) <= 1e-9
+    assert abs(dmug - dmu_o) <= 1e-9 * abs(dmu_o)
+
+
+def test_segment_option_constraints():
+    u, b, _ = case((3, 3, 3, 3), 0.3, 32, 1)
+    with pytest.raises(binding.OVError) as e:       # segments need rebiorth = 0
+        binding.tsl_sign(T(u), 0.3, -1.0, T(b[0]), 20, rebiorth=1, segment=5)
+    assert e.value.status == -1
+    with pytest.raises(binding.OVError) as e:       # not for the block TSL
+        ctx = binding.context("fp64", 0, 2, segment=5)
+        dx = torch.empty_like(T(b[0]))
+        x = torch.empty_like(dx)
+        dims = (ctypes.c_int32 * 4)(3, 3, 3, 3)
+        binding._check(binding.load().ov_tsl_sign_jvp(ctx, dims, binding._ptr(T(u)), 0.3, -1.0, 1,
+                                                      binding._ptr(T(b[0])), 20, None, 1.0, binding._ptr(dx),
+                                                      binding._ptr(x), None), "ov_tsl_sign_jvp")
+    assert e.value.status == -1
+    # eps_A through the two-pass path equals the stored-basis one
+    ea = binding.tsl_eps(T(u), 0.3, -1.0, T(b[0]), 30, rebiorth=0)
+    eg = binding.tsl_eps(T(u), 0.3, -1.0, T(b[0]), 30, rebiorth=0, segment=8)
+    assert abs(eg - ea) <= 1e-10 * ea
