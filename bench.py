@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
     ap.add_argument("--rebiorth", type=int, default=20)
     ap.add_argument("--passes", type=int, default=1)
+    ap.add_argument("--segment", type=int, default=0,
+                    help="two-pass TSL with checkpoints every S steps (needs --rebiorth 0)")
+    ap.add_argument("--m-w", type=float, default=None, help="override the workload's Wilson mass")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
     ap.add_argument("--cpu-k", type=int, default=4, help="Lanczos steps of the oracle sample")
     ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch"],
@@ -124,6 +127,12 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # algorithmic bytes (what the method must move), FP32 real size e = 4, FP64 e = 8
 # ---------------------------------------------------------------------------
+def workload_of(args):
+    import dataclasses
+    wl = inputs.WORKLOADS[args.workload]
+    return wl if args.m_w is None else dataclasses.replace(wl, m_w=args.m_w)
+
+
 def rebiorth_steps(k, period):
     if period <= 0:
         return []
@@ -163,6 +172,8 @@ def algorithmic_flops(kind, k, V, nsrc, period, passes):
     """Algorithmic FP64 flops of one ov_tsl_sign_vjp call for the ALU-bound kinds.
 
     Gram-Schmidt kinds: 4 FMA (8 flop) per complex element and basis vector.
+    stencil_pair: the two H applications and the alpha dot of each step, once
+    (replayed segments are extra work, not algorithmic flops).
     rev_stencil, per site and step: H^dag g_p and H (conj(g_alpha) v_j + g_s)
     (2 x 1368), the seven single complex combinations of fields it adds (g_p,
     the H input, xbar, g_r, g_s and the two previous-step terms: 7 x 12 x 8),
@@ -171,6 +182,8 @@ def algorithmic_flops(kind, k, V, nsrc, period, passes):
     if kind in ("proj_dots", "proj_update"):
         basis = 2 * passes * nsrc * 24 * e64 * V * sum(2 * (j + 1) for j in rebiorth_steps(k, period))
         return basis / 16 * 8
+    if kind == "stencil_pair":   # H v and H^dag w per step, and alpha = w^dag p (one forward sweep)
+        return nsrc * V * k * (2 * H_FLOP_PER_SITE + 12 * 8)
     if kind == "rev_stencil":
         reb = set(rebiorth_steps(k, period))
         nrec, acc = 0, 0
@@ -203,18 +216,19 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    wl = inputs.WORKLOADS[args.workload]
+    wl = workload_of(args)
     k = args.k or wl.k
     u, b, xbar = inputs.make_inputs(wl)
     nsrc = b.shape[0]
     V = wl.volume
     ut, bt, xt = (torch.tensor(a, device=dev) for a in (u, b, xbar))
-    ctx = binding.context(args.precision, args.rebiorth, args.passes)
-    tune = binding.autotune(ut, wl.mu, wl.m_w, nsrc, args.precision, args.rebiorth, args.passes)
+    ctx = binding.context(args.precision, args.rebiorth, args.passes, segment=args.segment)
+    tune = binding.autotune(ut, wl.mu, wl.m_w, nsrc, args.precision, args.rebiorth, args.passes,
+                            segment=args.segment)
 
     def step():
         return binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, args.precision, args.rebiorth, args.passes,
-                                    return_info=True)
+                                    return_info=True, segment=args.segment)
 
     info = None
     for _ in range(args.warmup):
@@ -263,7 +277,7 @@ def run_ours(args, rank, world, local_rank):
     gbs = bytes_dom / (prof[dom][1] / 1e3) / 1e9
     per_launch = {"launches": prof[dom][0], "avg_launch_us": round(1e3 * prof[dom][1] / max(1, prof[dom][0]), 2),
                   "algorithmic_bytes_per_launch": int(bytes_dom / max(1, prof[dom][0]))}
-    if args.precision == "fp64" and dom in ("proj_dots", "proj_update", "rev_stencil"):
+    if args.precision == "fp64" and dom in ("proj_dots", "proj_update", "rev_stencil", "stencil_pair"):
         flops = algorithmic_flops(dom, k, V, nsrc, args.rebiorth, args.passes) * args.steps
         achieved = flops / (prof[dom][1] / 1e3) / 1e12
         # FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA (4 flop) per
@@ -296,7 +310,8 @@ def run_ours(args, rank, world, local_rank):
            "data": "synthetic",
            "config": {"workload": f"{args.workload} lattice, k={k}, mu={wl.mu}, m_w={wl.m_w}, "
                                   f"{nsrc} source(s), forward + gauge-force VJP",
-                      "precision": args.precision, "rebiorth_period": args.rebiorth, "gs_passes": args.passes,
+                      "precision": args.precision, "rebiorth_period": args.rebiorth, "segment": args.segment,
+                      "gs_passes": args.passes,
                       "l2": "working set (Krylov bases) > L2; no flush", "parallelism": f"replicas x{world}"},
            "gpu_launches": launches // args.steps * args.steps, "kernels_ms_per_step": kernels_ms,
            "phase_ms": [round(t, 3) for t in info["t_ms"][:6]], "newton_iters": [info["newton_iters"],
@@ -353,7 +368,7 @@ def e2e_leg(args, ut, bt, xt, wl, k):
         bd.copy_(bh, non_blocking=True)
         xd.copy_(xh, non_blocking=True)
         du, dmu, x = binding.tsl_sign_vjp(ud, wl.mu, wl.m_w, bd, k, xd, args.precision, args.rebiorth,
-                                          args.passes)
+                                          args.passes, segment=args.segment)
         du_h.copy_(du, non_blocking=True)
         x_h.copy_(x, non_blocking=True)
     e1.record()
@@ -471,7 +486,7 @@ def mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar):
 def cpu_leg(args, k):
     """The FP64 oracle on the host cores, on a bounded sample of the workload."""
     from oracle import tsl, vjp
-    wl = inputs.WORKLOADS[args.workload]
+    wl = workload_of(args)
     u, b, xbar = inputs.make_inputs(wl)
     ks = args.cpu_k
     t0 = time.perf_counter()
@@ -487,7 +502,7 @@ def cpu_leg(args, k):
 def run_reference(args, rank):
     if rank != 0:
         return None
-    wl = inputs.WORKLOADS[args.workload]
+    wl = workload_of(args)
     k = args.k or wl.k
     from oracle import tsl, vjp
     u, b, xbar = inputs.make_inputs(wl)
@@ -536,12 +551,13 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         print(json.dumps({"leg": "uneven_batch", "precision": args.precision, "rebiorth_period": args.rebiorth,
+                          "segment": args.segment,
                           "gs_passes": args.passes, **batch_leg(args)}))
         return
     if args.leg == "stencil":
         import torch
         torch.cuda.set_device(local_rank)
-        wl = inputs.WORKLOADS[args.workload]
+        wl = workload_of(args)
         u, _, _ = inputs.make_inputs(wl)
         out = stencil_leg(args, torch.tensor(u, device=f"cuda:{local_rank}"), wl, 6786.9, "measured")
         print(json.dumps(out))

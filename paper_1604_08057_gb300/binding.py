@@ -367,13 +367,13 @@ def launch_count(ctx) -> int:
     return int(load().ov_launch_count(ctx))
 
 
-def autotune(u, mu, m_w, nsrc=1, precision="fp64", rebiorth=1, passes=2) -> dict:
+def autotune(u, mu, m_w, nsrc=1, precision="fp64", rebiorth=1, passes=2, segment=0) -> dict:
     """Time the stencil launch variants on this lattice and keep the fastest in the context."""
     lib = load()
     dims = _dims(u)
     u = u.contiguous()
     rep = TuneReport()
-    ctx = context(precision, rebiorth, passes)
+    ctx = context(precision, rebiorth, passes, segment=segment)
     _check(lib.ov_autotune(ctx, dims, _ptr(u), float(mu), float(m_w), int(nsrc), ctypes.byref(rep)),
            "ov_autotune")
     return {"apply_variant": rep.apply_variant, "pair_variant": rep.pair_variant,
