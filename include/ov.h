@@ -117,6 +117,23 @@ int ov_tsl_sign_vjp(ov_context *ctx, const int32_t dims[4], const void *U, doubl
                     double m_w, int32_t nsrc, const void *b, int32_t k, const void *xbar,
                     void *x, void *dU, double *dmu, ov_tsl_info *info);
 
+/* Reverse mode in two calls, for callers that need x first and the gradient
+ * later (an autograd framework): ov_tsl_sign_fwd computes x as ov_tsl_sign
+ * does and returns a tape that keeps what the reverse mode needs (the bases or,
+ * with options.segment, the segment checkpoints; the recurrence coefficients;
+ * every inverse of the Newton iteration of each source's k x k sign: about
+ * 48 k^2 complex doubles per source).  ov_tsl_sign_vjp_tape then computes dU
+ * and dmu for a cotangent xbar exactly as ov_tsl_sign_vjp would, without
+ * repeating the forward recurrence or the Newton iteration; a tape may serve
+ * several cotangents.  The tape owns its device memory until ov_tape_destroy;
+ * it runs on ctx's stream and must not outlive ctx.  Arguments and errors as
+ * ov_tsl_sign / ov_tsl_sign_vjp; on error no tape is returned. */
+typedef struct ov_tape ov_tape;
+int ov_tsl_sign_fwd(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                    int32_t nsrc, const void *b, int32_t k, void *x, ov_tsl_info *info, ov_tape **tape);
+int ov_tsl_sign_vjp_tape(ov_tape *tape, const void *xbar, void *dU, double *dmu, ov_tsl_info *info);
+int ov_tape_destroy(ov_tape *tape);
+
 /* One problem of an uneven batch: the arguments of ov_tsl_sign (xbar = NULL)
  * or of ov_tsl_sign_vjp (xbar != NULL) for one lattice, mu and k, and its
  * outputs: info and status (OV_OK or the call's error code). */

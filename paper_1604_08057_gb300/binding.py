@@ -63,7 +63,7 @@ class Problem(ctypes.Structure):
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
-           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_strerror"]
+           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -90,6 +90,9 @@ def load(path: str = LIB_PATH):
     lib.ov_tsl_sign_jvp.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, P, ctypes.POINTER(Info)]
     lib.ov_block_tsl_sign.argtypes = [P, dims_t, P, D, D, I32, P, P, I32, P, D, P, P, ctypes.POINTER(Info)]
     lib.ov_tsl_batch.argtypes = [P, I32, ctypes.POINTER(Problem), I32]
+    lib.ov_tsl_sign_fwd.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, ctypes.POINTER(Info), ctypes.POINTER(P)]
+    lib.ov_tsl_sign_vjp_tape.argtypes = [P, P, P, ctypes.POINTER(D), ctypes.POINTER(Info)]
+    lib.ov_tape_destroy.argtypes = [P]
     lib.ov_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, ctypes.POINTER(Info)]
     lib.ov_block_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, ctypes.POINTER(Info)]
     lib.ov_profile_enable.argtypes = [P, I32]
@@ -174,6 +177,57 @@ def tsl_sign(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2, return_in
                            _ptr(x), ctypes.byref(info)), "ov_tsl_sign")
     x = x[0] if single else x
     return (x, info.as_dict()) if return_info else x
+
+
+class Tape:
+    """The forward state kept by ov_tsl_sign_fwd for later VJPs (device memory
+    until the object is freed)."""
+
+    def __init__(self, handle, u, bb, single):
+        self._h = handle
+        self._u = u                # the links the reverse mode writes dU for (shape, device)
+        self._shape = bb.shape
+        self._single = single
+
+    def vjp(self, xbar, return_info=False):
+        """(dU, dmu) for L = sum_src Re <xbar, x> from the kept forward pass."""
+        if self._h is None:
+            raise RuntimeError("tape already freed")
+        xb, _ = _spinors(xbar, self._u)
+        if xb.shape != self._shape:
+            raise ValueError("xbar must have the shape of b")
+        du = torch.empty_like(self._u)
+        dmu = ctypes.c_double(0.0)
+        info = Info()
+        _check(load().ov_tsl_sign_vjp_tape(self._h, _ptr(xb), _ptr(du), ctypes.byref(dmu), ctypes.byref(info)),
+               "ov_tsl_sign_vjp_tape")
+        return (du, dmu.value, info.as_dict()) if return_info else (du, dmu.value)
+
+    def free(self):
+        if self._h is not None and _lib is not None:
+            _lib.ov_tape_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def tsl_sign_fwd(u, mu, m_w, b, k, precision="fp64", rebiorth=1, passes=2, segment=0):
+    """(x, tape): x ~ sgn(H(mu)) b as tsl_sign, and a Tape for VJPs that skip the forward pass."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    x = torch.empty_like(bb)
+    info = Info()
+    h = ctypes.c_void_p()
+    ctx = context(precision, rebiorth, passes, segment=segment)
+    _check(lib.ov_tsl_sign_fwd(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k), _ptr(x),
+                               ctypes.byref(info), ctypes.byref(h)), "ov_tsl_sign_fwd")
+    return (x[0] if single else x), Tape(h, u, bb, single)
 
 
 def tsl_sign_vjp(u, mu, m_w, b, k, xbar, precision="fp64", rebiorth=1, passes=2, want_x=True,

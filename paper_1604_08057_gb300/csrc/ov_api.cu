@@ -21,7 +21,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
 };
 
 struct Status {
@@ -621,40 +621,121 @@ int eps_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, dou
   return OV_OK;
 }
 
+// What the reverse mode needs from the forward pass: the lattice state (bases or
+// segment checkpoints, coefficients), the host scalars, y, and per source the
+// recorded inverses of the Newton sign iteration, its scalings and its result.
 template <typename R>
-int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
-                 const void* b, int k, const void* xbar, void* x, void* dU, double* dmu, ov_tsl_info* info) {
+struct FwdState {
+  Lat<R> L{};
+  std::vector<SrcScal> hsc;
+  int k = 0, nsrc = 0, S = 0;
+  SegPlan P;
+  SegStore<R> K{};
+  zd* y = nullptr;        // [src][k]
+  zd* rec_inv = nullptr;  // [src][NREC][k*k]
+  double* rec_ld = nullptr;  // [src][NREC]
+  zd* fsign = nullptr;    // [src][k*k]
+  std::vector<std::vector<int>> scaling;
+  std::vector<int> iters;
+  std::vector<char> rec_ok;
+  int iters_max = 0;
+};
+
+// forward recurrence and, per source, y = beta0 sgn(T_k) e1 by Newton with every
+// inverse recorded (for the Frechet adjoint of the reverse mode)
+template <typename R>
+int vjp_forward(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                const void* b, int k, FwdState<R>& F, ov_tsl_info* info) {
   check_ptr(b);
-  check_ptr(xbar);
-  check_ptr(dU);
-  if (!dmu) throw Status{OV_ERR_INVALID_ARG};
-  if (x) check_ptr(x);
   const int S = c->opt.segment > 0 && c->opt.segment < k ? c->opt.segment : 0;
-  Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true, 1, S > 0 ? S + 2 : 0);
+  F.S = S;
+  F.k = k;
+  F.nsrc = nsrc;
+  F.L = setup<R>(c, dims, U, mu, m_w, nsrc, k, true, 1, S > 0 ? S + 2 : 0);
+  Lat<R>& L = F.L;
   const int64_t V = L.g.V, vs = L.vs;
   run(c, OV_KIND_LAYOUT, 2, [&] {
     pack_spinors<R>(static_cast<const double*>(b), L.r, nsrc, V, vs, c->st);
     pack_spinors<R>(static_cast<const double*>(b), L.s, nsrc, V, vs, c->st);
   });
-  SegPlan P;
-  SegStore<R> K{};
   CK(cudaEventRecord(c->ev[0], c->st));
   if (S > 0) {
-    P = seg_plan(k, S);
-    K = seg_store(c, L, (int)P.lo.size());
-    seg_forward(c, L, P, K);
+    F.P = seg_plan(k, S);
+    F.K = seg_store(c, L, (int)F.P.lo.size());
+    seg_forward(c, L, F.P, F.K);
   } else {
     forward_krylov(c, L);
   }
   CK(cudaEventRecord(c->ev[1], c->st));
-  auto hsc = read_scalars(c, L.sc, nsrc);
+  F.hsc = read_scalars(c, L.sc, nsrc);
   int kr = k;
-  int st = scalar_status(hsc, &kr, k);
+  int st = scalar_status(F.hsc, &kr, k);
   c->last_k = k;
   c->last_nsrc = nsrc;
   if (info) info->k_reached = kr;
   if (st != OV_OK) return st;
-  zd* y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
+  const int64_t n = (int64_t)k * k;
+  F.y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
+  F.rec_inv = wsT<zd>(c, B_REC, (int64_t)nsrc * NREC * n);
+  F.rec_ld = wsT<double>(c, B_RECLD, (int64_t)nsrc * NREC);
+  F.fsign = wsT<zd>(c, B_FSIGN, (int64_t)nsrc * n);
+  int* derr = wsT<int>(c, B_DERR, 1, true);
+  zd* a[2] = {wsT<zd>(c, B_X, n), wsT<zd>(c, B_XN, n)};
+  F.scaling.assign(nsrc, {});
+  F.iters.assign(nsrc, 0);
+  F.rec_ok.assign(nsrc, 0);
+  F.iters_max = 0;
+  for (int src = 0; src < nsrc; ++src) {
+    NewtonRecord rec;
+    rec.inv = F.rec_inv + (int64_t)src * NREC * n;
+    rec.logdet = F.rec_ld + (int64_t)src * NREC;
+    rec.cap = NREC;
+    run(c, OV_KIND_DENSE, 2, [&] {
+      dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, a[0],
+                    c->st);
+    });
+    int which = 0;
+    const int it = newton(c, a, nullptr, k, derr, &which, &rec);
+    if (it < 0) return OV_ERR_SIGN_ILLPOSED;
+    F.iters[src] = it;
+    F.iters_max = std::max(F.iters_max, it);
+    F.scaling[src] = rec.scaling;
+    F.rec_ok[src] = rec.ok ? 1 : 0;
+    run(c, OV_KIND_DENSE, 2, [&] {
+      dense_copy(a[which], F.fsign + (int64_t)src * n, n, c->st);
+      dense_extract_y(a[which], F.hsc[src].beta0, k, F.y + (int64_t)src * k, c->st);
+    });
+  }
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (herr) return OV_ERR_SIGN_ILLPOSED;
+  CK(cudaEventRecord(c->ev[2], c->st));
+  if (info) {
+    info->newton_iters = F.iters_max;
+    info->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
+    info->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
+  }
+  return OV_OK;
+}
+
+// reverse mode from a forward state: g_y = V^dag xbar, G_T by the Frechet adjoint,
+// x = V y (if x is given), the reverse sweep and the force
+template <typename R>
+int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* dU, double* dmu,
+                ov_tsl_info* info) {
+  check_ptr(xbar);
+  check_ptr(dU);
+  if (!dmu) throw Status{OV_ERR_INVALID_ARG};
+  if (x) check_ptr(x);
+  Lat<R>& L = F.L;
+  const int k = F.k, nsrc = F.nsrc, S = F.S;
+  const SegPlan& P = F.P;
+  const SegStore<R>& K = F.K;
+  const auto& hsc = F.hsc;
+  zd* y = F.y;
+  const int64_t V = L.g.V, vs = L.vs;
+  CK(cudaEventRecord(c->ev[2], c->st));
   // g_y = V^dag xbar
   R* xb = wsT<R>(c, B_XBAR, nsrc * vs);
   run(c, OV_KIND_LAYOUT, 1, [&] { pack_spinors<R>(static_cast<const double*>(xbar), xb, nsrc, V, vs, c->st); });
@@ -662,7 +743,7 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   zd* gy = wsT<zd>(c, B_GY, (int64_t)nsrc * 2 * k);
   zd* cpart = wsT<zd>(c, B_CPART, (int64_t)nsrc * 2 * k * nsb);
   if (S > 0) {
-    // second pass: g_y = V_k^dag xbar, one replayed segment at a time
+    // second pass: g_y one replayed segment at a time
     for (size_t t = 0; t < P.lo.size(); ++t) {
       seg_replay(c, L, P, K, (int)t, false);
       run(c, OV_KIND_COMBINE, 2, [&] {
@@ -673,8 +754,6 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
     run(c, OV_KIND_COMBINE, 2, [&] { basis_dots(L, k, xb, vs, gy, cpart, c->st); });
   }
   launch_check();
-  CK(cudaEventRecord(c->ev[2], c->st));
-  // per source: y = beta0 sgn(T) e1 by Newton, recording the inverses; then
   // G_T = L_sgn(T^dag, beta0 g_y e1^T).  The Theorem-1 block iteration on
   // [[T^dag, G], [0, T^dag]] has diagonal iterates X_i^dag (X_i: the iterates on
   // T, same scalings), so its upper-right block follows from the recorded X_i^{-1}:
@@ -684,7 +763,7 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   zd* gbT = wsT<zd>(c, B_GB, (int64_t)nsrc * k);
   double* gdT = wsT<double>(c, B_GD, (int64_t)nsrc * k);
   int* derr = wsT<int>(c, B_DERR, 1, true);
-  int iters = 0, iters_adj = 0;
+  int iters_adj = 0;
   {
     const int64_t n = (int64_t)k * k;
     zd* a[2] = {wsT<zd>(c, B_X, n), wsT<zd>(c, B_XN, n)};
@@ -695,35 +774,23 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
     double* dstat = wsT<double>(c, B_DSTAT, 4);
     zd* dpart = wsT<zd>(c, B_DPART, (n + 255) / 256 + 64);
     unsigned* dcnt = wsT<unsigned>(c, B_DCNT, 4);
-    NewtonRecord rec;
-    rec.inv = wsT<zd>(c, B_REC, (int64_t)NREC * n);
-    rec.logdet = wsT<double>(c, B_RECLD, NREC);
-    rec.cap = NREC;
     for (int src = 0; src < nsrc; ++src) {
-      rec.scaling.clear();
-      rec.ok = true;
-      run(c, OV_KIND_DENSE, 2, [&] {
-        dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k, a[0],
-                      c->st);
-      });
-      int which = 0;
-      const int it = newton(c, a, nullptr, k, derr, &which, &rec);
-      if (it < 0) return OV_ERR_SIGN_ILLPOSED;
-      if (it > iters) iters = it;
-      zd* f = a[which];
-      run(c, OV_KIND_DENSE, 1, [&] { dense_extract_y(f, hsc[src].beta0, k, y + (int64_t)src * k, c->st); });
-      if (rec.ok) {
+      const int it = F.iters[src];
+      const zd* f = F.fsign + (int64_t)src * n;
+      if (F.rec_ok[src]) {
+        const zd* inv = F.rec_inv + (int64_t)src * NREC * n;
+        const double* ld = F.rec_ld + (int64_t)src * NREC;
         int ce = 0;
         run(c, OV_KIND_DENSE, 2,
             [&] { dense_set_column0(e[0], gy + (int64_t)src * 2 * k, 2, hsc[src].beta0, k, c->st); });
         for (int i = 0; i < it; ++i) {
-          const zd* yi = rec.inv + (int64_t)i * n;
+          const zd* yi = inv + (int64_t)i * n;
           run(c, OV_KIND_DENSE_GEMM, 2, [&] {
             dense_gemm_op(yi, 1, e[ce], 0, t1, k, c->st);
             dense_gemm_op(t1, 0, yi, 1, t2, k, c->st);
           });
           run(c, OV_KIND_DENSE, 1, [&] {
-            dense_newton_combine(e[ce], t2, e[1 - ce], k, rec.logdet + i, rec.scaling[i], -1.0, 1.0, dstat, dpart,
+            dense_newton_combine(e[ce], t2, e[1 - ce], k, ld + i, F.scaling[src][i], -1.0, 1.0, dstat, dpart,
                                  dcnt, c->st);
           });
           ce = 1 - ce;
@@ -878,18 +945,29 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   CK(cudaMemcpyAsync(dmu, B.dmu, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   auto hsc2 = read_scalars(c, L.sc, nsrc);
   prof_collect(c);
-  st = scalar_status(hsc2, nullptr, k);
+  const int st = scalar_status(hsc2, nullptr, k);
   if (st != OV_OK) return st;
   if (info) {
-    info->newton_iters = iters;
+    info->newton_iters = F.iters_max;
     info->newton_iters_adj = iters_adj;
-    info->t_ms[0] = elapsed(c->ev[0], c->ev[1]);
-    info->t_ms[1] = elapsed(c->ev[1], c->ev[2]);
     info->t_ms[2] = elapsed(c->ev[2], c->ev[3]);
     info->t_ms[3] = elapsed(c->ev[3], c->ev[4]);
     info->t_ms[4] = elapsed(c->ev[4], c->ev[5]);
   }
   return OV_OK;
+}
+
+template <typename R>
+int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                 const void* b, int k, const void* xbar, void* x, void* dU, double* dmu, ov_tsl_info* info) {
+  check_ptr(xbar);
+  check_ptr(dU);
+  if (!dmu) throw Status{OV_ERR_INVALID_ARG};
+  if (x) check_ptr(x);
+  FwdState<R> F;
+  const int st = vjp_forward<R>(c, dims, U, mu, m_w, nsrc, b, k, F, info);
+  if (st != OV_OK) return st;
+  return vjp_reverse<R>(c, F, xbar, x, dU, dmu, info);
 }
 
 template <typename R>
@@ -960,7 +1038,35 @@ bool valid_options(const ov_options* o) {
          o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0);
 }
 
+// x = V_k y from a forward state (a second pass over the segments if there are any)
+template <typename R>
+void fwd_combine(ov_context* c, FwdState<R>& F, void* x) {
+  Lat<R>& L = F.L;
+  if (F.S > 0) {
+    for (size_t t = 0; t < F.P.lo.size(); ++t) {
+      seg_replay(c, L, F.P, F.K, (int)t, false);
+      run(c, OV_KIND_COMBINE, 1, [&] {
+        combine_range(L, F.P.lo[t], F.P.hi[t] - F.P.lo[t], F.y, static_cast<double*>(x), t > 0, c->st);
+      });
+    }
+  } else {
+    run(c, OV_KIND_COMBINE, 1, [&] { combine(L, F.k, F.y, static_cast<double*>(x), c->st); });
+  }
+  launch_check();
+  CK(cudaStreamSynchronize(c->st));
+  prof_collect(c);
+}
+
 }  // namespace
+
+// A forward pass kept for reverse mode: a private context whose workspace holds
+// the bases (or segment checkpoints), the coefficients and the Newton record.
+struct ov_tape {
+  ov_context* parent = nullptr;
+  ov_context* ctx = nullptr;
+  FwdState<double>* f64 = nullptr;
+  FwdState<float>* f32 = nullptr;
+};
 
 extern "C" {
 
@@ -1226,6 +1332,70 @@ int ov_tsl_batch(ov_context* c, int32_t nprob, ov_problem* probs, int32_t nworke
   cudaGetLastError();
   for (int32_t i = 0; i < nprob && status == OV_OK; ++i) status = probs[i].status;
   return status;
+}
+
+int ov_tape_destroy(ov_tape* t) {
+  if (!t) return OV_ERR_INVALID_ARG;
+  delete t->f64;
+  delete t->f32;
+  if (t->ctx) ov_context_destroy(t->ctx);
+  delete t;
+  return OV_OK;
+}
+
+int ov_tsl_sign_fwd(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                    const void* b, int32_t k, void* x, ov_tsl_info* info, ov_tape** tape) {
+  if (!c || !tape || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
+  *tape = nullptr;
+  if (info) std::memset(info, 0, sizeof(*info));
+  ov_tape* t = new (std::nothrow) ov_tape();
+  if (!t) return OV_ERR_OOM;
+  t->parent = c;
+  int st = ov_context_create(&t->ctx, &c->opt, c->st);
+  if (st != OV_OK) {
+    delete t;
+    return st;
+  }
+  std::copy(c->tuned_apply, c->tuned_apply + 2, t->ctx->tuned_apply);
+  std::copy(c->tuned_pair, c->tuned_pair + 2, t->ctx->tuned_pair);
+  st = guarded([&] {
+    check_ptr(x);
+    int s;
+    if (c->opt.precision == OV_MIXED) {
+      t->f32 = new FwdState<float>();
+      s = vjp_forward<float>(t->ctx, dims, U, mu, m_w, nsrc, b, k, *t->f32, info);
+      if (s == OV_OK) fwd_combine(t->ctx, *t->f32, x);
+    } else {
+      t->f64 = new FwdState<double>();
+      s = vjp_forward<double>(t->ctx, dims, U, mu, m_w, nsrc, b, k, *t->f64, info);
+      if (s == OV_OK) fwd_combine(t->ctx, *t->f64, x);
+    }
+    return s;
+  });
+  c->launches += t->ctx->launches;
+  t->ctx->launches = 0;
+  if (st != OV_OK) {
+    ov_tape_destroy(t);
+    return st;
+  }
+  *tape = t;
+  return OV_OK;
+}
+
+int ov_tsl_sign_vjp_tape(ov_tape* t, const void* xbar, void* dU, double* dmu, ov_tsl_info* info) {
+  if (!t || !t->ctx || (!t->f64 && !t->f32)) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  const int st = guarded([&] {
+    if (t->f32) {
+      if (info) info->k_reached = t->f32->k;
+      return vjp_reverse<float>(t->ctx, *t->f32, xbar, nullptr, dU, dmu, info);
+    }
+    if (info) info->k_reached = t->f64->k;
+    return vjp_reverse<double>(t->ctx, *t->f64, xbar, nullptr, dU, dmu, info);
+  });
+  t->parent->launches += t->ctx->launches;
+  t->ctx->launches = 0;
+  return st;
 }
 
 int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, double* beta, double* delta) {

@@ -412,3 +412,21 @@ def test_segment_option_constraints():
     ea = binding.tsl_eps(T(u), 0.3, -1.0, T(b[0]), 30, rebiorth=0)
     eg = binding.tsl_eps(T(u), 0.3, -1.0, T(b[0]), 30, rebiorth=0, segment=8)
     assert abs(eg - ea) <= 1e-10 * ea
+
+
+# ---------------------------------------------------------------------------
+# reverse mode from a tape (forward kept on the device)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,reb,passes,segment", [("fp64", 10, 2, 0), ("fp64", 0, 2, 7), ("mixed", 1, 2, 0)])
+def test_tape_vjp_equals_direct_vjp(precision, reb, passes, segment):
+    dims, mu, m_w, k = (3, 5, 2, 4), 0.3, -1.0, 50
+    u, b, xbar = case(dims, 0.3, 40, 2)
+    xbar2 = inputs.gaussian_spinors(dims, 2, np.random.default_rng(41))
+    opts = dict(precision=precision, rebiorth=reb, passes=passes, segment=segment)
+    x, tape = binding.tsl_sign_fwd(T(u), mu, m_w, T(b), k, **opts)
+    assert torch.equal(x, binding.tsl_sign(T(u), mu, m_w, T(b), k, **opts))
+    for xb in (xbar, xbar2):                          # one tape, two cotangents
+        du_t, dmu_t = tape.vjp(T(xb))
+        du, dmu, _ = binding.tsl_sign_vjp(T(u), mu, m_w, T(b), k, T(xb), **opts)
+        assert torch.equal(du_t, du) and dmu_t == dmu
+    tape.free()
