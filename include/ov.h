@@ -170,8 +170,11 @@ int ov_tsl_batch(ov_context *ctx, int32_t nprob, ov_problem *probs, int32_t nwor
  * TSL step's H/H^dagger pair (both products sharing each link load in one
  * thread, or computed one after the other, x threads per block) -- on this
  * lattice, nsrc sources and the context's precision, and keeps the fastest
- * of each in the context for later calls.  U is as in ov_apply_H; the
- * spinor data used for timing is internal scratch.  rep may be NULL. */
+ * of each in the context for later calls (a variant replaces variant 0, or an
+ * earlier pick, only when it is more than 2% faster: variants reduce in
+ * different block sizes, so results differ between them at rounding level).
+ * U is as in ov_apply_H; the spinor data used for timing is internal
+ * scratch.  rep may be NULL. */
 typedef struct {
   int32_t apply_variant;    /* chosen variant of the ov_apply_H stencil */
   int32_t pair_variant;     /* chosen variant of the TSL stencil pair */

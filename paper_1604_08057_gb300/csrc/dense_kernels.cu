@@ -17,9 +17,13 @@ __global__ void k_zero(zd* a, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) a[i] = mk(0.0, 0.0);
 }
-__global__ void k_copy(const zd* __restrict__ a, zd* __restrict__ b, int64_t n) {
+// batched: problem p (blockIdx.y) at a + p * sa, b + p * sb; act (may be null) switches problems off
+__global__ void k_copy(const zd* __restrict__ a, int64_t sa, zd* __restrict__ b, int64_t sb, int64_t n,
+                       const int* __restrict__ act) {
+  const int p = blockIdx.y;
+  if (act && !act[p]) return;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) b[i] = a[i];
+  if (i < n) b[p * sb + i] = a[p * sa + i];
 }
 __global__ void k_adjoint(const zd* __restrict__ a, zd* __restrict__ b, int k) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -59,7 +63,13 @@ __global__ void k_extract_tri(const zd* __restrict__ e, int k, zd* ga, zd* gb, d
 }
 
 void dense_zero(zd* a, int64_t n, cudaStream_t st) { k_zero<<<nblk(n, 256), 256, 0, st>>>(a, n); }
-void dense_copy(const zd* a, zd* b, int64_t n, cudaStream_t st) { k_copy<<<nblk(n, 256), 256, 0, st>>>(a, b, n); }
+void dense_copy(const zd* a, zd* b, int64_t n, cudaStream_t st) {
+  k_copy<<<nblk(n, 256), 256, 0, st>>>(a, 0, b, 0, n, nullptr);
+}
+void dense_copy_batch(const zd* a, int64_t sa, zd* b, int64_t sb, int64_t n, int nb, const int* act,
+                      cudaStream_t st) {
+  k_copy<<<dim3(nblk(n, 256), nb), 256, 0, st>>>(a, sa, b, sb, n, act);
+}
 void dense_adjoint(const zd* a, zd* b, int k, cudaStream_t st) {
   k_adjoint<<<nblk((int64_t)k * k, 256), 256, 0, st>>>(a, b, k);
 }
@@ -108,18 +118,35 @@ __device__ __forceinline__ void gj_offer(unsigned long long* key, double nrm, in
   atomicMax(key, gj_key(nrm, i));
 }
 
+// Batched over problems p = blockIdx.y (matrices at stride k*k, row flags and
+// pivots at stride k, keys at stride k + 1); act (may be null) switches problems off.
 // used-row flags cleared and the candidates of column 0 offered (keys zeroed beforehand)
-__global__ void k_gj_init(const zd* __restrict__ x, int k, unsigned long long* keys, int* used, int* err) {
+__global__ void k_gj_init(const zd* __restrict__ x, int k, unsigned long long* keys, int* used, int* err,
+                          const int* __restrict__ act) {
+  const int p = blockIdx.y;
+  if (act && !act[p]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= k) return;
-  used[i] = 0;
-  gj_offer(keys, norm2(x[(int64_t)i * k]), i, err);
+  used[(int64_t)p * k + i] = 0;
+  gj_offer(keys + (int64_t)p * (k + 1), norm2(x[(int64_t)p * k * k + (int64_t)i * k]), i, err);
 }
 
 template <int JPT>
 __global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict__ xin, zd* __restrict__ xout, int k,
                                                         int kk, unsigned long long* keys, int* used, int* prows,
-                                                        double* logdet, int* err) {
+                                                        double* logdet, int ld_stride, int* err,
+                                                        const int* __restrict__ act) {
+  const int pb = blockIdx.y;   // the problem
+  if (act && !act[pb]) return;
+  {
+    const int64_t n = (int64_t)k * k;
+    xin += pb * n;
+    xout += pb * n;
+    keys += (int64_t)pb * (k + 1);
+    used += (int64_t)pb * k;
+    prows += (int64_t)pb * k;
+    logdet += (int64_t)pb * ld_stride;
+  }
   const int i = blockIdx.x;   // the block's row
   const zd* xr = xin + (int64_t)i * k;
   zd* yr = xout + (int64_t)i * k;
@@ -201,35 +228,43 @@ __global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict_
   }
 }
 
-__global__ void k_gj_invperm(const int* __restrict__ prows, int* q, int k) {
+__global__ void k_gj_invperm(const int* __restrict__ prows, int* q, int k, const int* __restrict__ act) {
+  const int p = blockIdx.y;
+  if (act && !act[p]) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < k) q[prows[c]] = c;
+  if (c < k) q[(int64_t)p * k + prows[(int64_t)p * k + c]] = c;
 }
 __global__ void k_gj_gather(const zd* __restrict__ x, zd* __restrict__ out, const int* __restrict__ prows,
-                            const int* __restrict__ q, int k) {
+                            const int* __restrict__ q, int k, const int* __restrict__ act) {
+  const int p = blockIdx.y;
+  if (act && !act[p]) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)k * k) return;
+  const int64_t n = (int64_t)k * k;
+  if (t >= n) return;
   const int i = (int)(t / k), j = (int)(t % k);
-  out[t] = x[(int64_t)prows[i] * k + q[j]];
+  out[p * n + t] = x[p * n + (int64_t)prows[(int64_t)p * k + i] * k + q[(int64_t)p * k + j]];
 }
 
-static void gj_launch_all(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int* used,
-                          unsigned long long* keys, double* logdet, int* err, cudaStream_t st) {
-  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)(k + 1), st);
-  k_gj_init<<<nblk(k, 128), 128, 0, st>>>(a, k, keys, used, err);
+static void gj_launch_all(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const int* act, int* ipiv,
+                          int* used, unsigned long long* keys, double* logdet, int ld_stride, int* err,
+                          cudaStream_t st) {
+  cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)(k + 1) * nb, st);
+  k_gj_init<<<dim3(nblk(k, 128), nb), 128, 0, st>>>(a, k, keys, used, err, act);
   const zd* in = a;
   zd* bufs[2] = {w0, w1};
   for (int kk = 0; kk < k; ++kk) {
     zd* out = bufs[kk & 1];
     if (k <= GJ_THREADS * GJ_JPT)
-      k_gj_step<GJ_JPT><<<k, GJ_THREADS, 0, st>>>(in, out, k, kk, keys, used, ipiv, logdet, err);
+      k_gj_step<GJ_JPT><<<dim3(k, nb), GJ_THREADS, 0, st>>>(in, out, k, kk, keys, used, ipiv, logdet, ld_stride,
+                                                            err, act);
     else
-      k_gj_step<0><<<k, GJ_THREADS, 0, st>>>(in, out, k, kk, keys, used, ipiv, logdet, err);
+      k_gj_step<0><<<dim3(k, nb), GJ_THREADS, 0, st>>>(in, out, k, kk, keys, used, ipiv, logdet, ld_stride, err,
+                                                       act);
     in = out;
   }
   int* q = used;   // the flags are no longer needed
-  k_gj_invperm<<<nblk(k, 128), 128, 0, st>>>(ipiv, q, k);
-  k_gj_gather<<<nblk((int64_t)k * k, 256), 256, 0, st>>>(in, ainv, ipiv, q, k);
+  k_gj_invperm<<<dim3(nblk(k, 128), nb), 128, 0, st>>>(ipiv, q, k, act);
+  k_gj_gather<<<dim3(nblk((int64_t)k * k, 256), nb), 256, 0, st>>>(in, ainv, ipiv, q, k, act);
 }
 
 // The k + 4 launches of one inversion are captured once per (k, buffers) as a
@@ -237,22 +272,22 @@ static void gj_launch_all(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipi
 // per-launch overhead of k back-to-back launches is a large part of their time.
 namespace {
 struct GjGraph {
-  const void* ptrs[9];
-  int k, dev;
+  const void* ptrs[11];
+  int k, nb, ld_stride, dev;
   cudaGraphExec_t exec;
 };
 std::mutex g_gj_mutex;
 std::vector<GjGraph> g_gj_graphs;
 }  // namespace
 
-void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, unsigned long long* keys,
-                   double* logdet, int* err, cudaStream_t st) {
-  const void* ptrs[9] = {a, ainv, w0, w1, ipiv, used, keys, logdet, err};
+void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const int* act, int* ipiv, int* used,
+                   unsigned long long* keys, double* logdet, int ld_stride, int* err, cudaStream_t st) {
+  const void* ptrs[11] = {a, ainv, w0, w1, ipiv, used, keys, logdet, err, act, nullptr};
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(g_gj_mutex);
   for (const GjGraph& g : g_gj_graphs) {
-    if (g.k == k && g.dev == dev && std::equal(ptrs, ptrs + 9, g.ptrs)) {
+    if (g.k == k && g.nb == nb && g.ld_stride == ld_stride && g.dev == dev && std::equal(ptrs, ptrs + 11, g.ptrs)) {
       cudaGraphLaunch(g.exec, st);
       return;
     }
@@ -263,7 +298,7 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int*
   bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
-    gj_launch_all(a, ainv, w0, w1, k, ipiv, used, keys, logdet, err, cap);
+    gj_launch_all(a, ainv, w0, w1, k, nb, act, ipiv, used, keys, logdet, ld_stride, err, cap);
     ok = cudaStreamEndCapture(cap, &graph) == cudaSuccess && graph &&
          cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
   }
@@ -271,7 +306,7 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int*
   if (cap) cudaStreamDestroy(cap);
   if (!ok) {   // capture unavailable: launch directly
     cudaGetLastError();
-    gj_launch_all(a, ainv, w0, w1, k, ipiv, used, keys, logdet, err, st);
+    gj_launch_all(a, ainv, w0, w1, k, nb, act, ipiv, used, keys, logdet, ld_stride, err, st);
     return;
   }
   if (g_gj_graphs.size() >= 64) {
@@ -279,8 +314,10 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int*
     g_gj_graphs.erase(g_gj_graphs.begin());
   }
   GjGraph g;
-  std::copy(ptrs, ptrs + 9, g.ptrs);
+  std::copy(ptrs, ptrs + 11, g.ptrs);
   g.k = k;
+  g.nb = nb;
+  g.ld_stride = ld_stride;
   g.dev = dev;
   g.exec = exec;
   g_gj_graphs.push_back(g);
@@ -292,10 +329,17 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int* ipiv, int*
 // ---------------------------------------------------------------------------
 constexpr int GT = 32, GK = 16;
 // C = op(A) op(B); op = identity (0) or conjugate transpose (1)
-__global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, const zd* __restrict__ b,
-                                              zd* __restrict__ c, int k, int ha, int hb) {
+// batched over problems p = blockIdx.z: A at a + p * sa, B at b + p * sb, C at c + p * sc
+__global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, int64_t sa, const zd* __restrict__ b,
+                                              int64_t sb, zd* __restrict__ c, int64_t sc, int k, int ha, int hb,
+                                              const int* __restrict__ act) {
   __shared__ zd as[GT][GK + 1];
   __shared__ zd bs[GK][GT + 1];
+  const int pz = blockIdx.z;
+  if (act && !act[pz]) return;
+  a += pz * sa;
+  b += pz * sb;
+  c += pz * sc;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
   zd acc[2][2];
@@ -334,22 +378,40 @@ __global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, const zd
     }
 }
 void dense_gemm(const zd* a, const zd* b, zd* c, int k, cudaStream_t st) {
-  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, b, c, k, 0, 0);
+  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, 0, b, 0, c, 0, k, 0, 0, nullptr);
 }
 void dense_gemm_op(const zd* a, int ha, const zd* b, int hb, zd* c, int k, cudaStream_t st) {
-  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, b, c, k, ha, hb);
+  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, 0, b, 0, c, 0, k, ha, hb, nullptr);
+}
+void dense_gemm_batch(const zd* a, int64_t sa, int ha, const zd* b, int64_t sb, int hb, zd* c, int64_t sc, int k,
+                      int nb, const int* act, cudaStream_t st) {
+  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT), nb), 256, 0, st>>>(a, sa, b, sb, c, sc, k, ha, hb, act);
 }
 
 // Xn = 0.5 (g X + s Xi / g);  stats += w * (|Xn - X|^2, |Xn|^2)
+// Batched over problems p = blockIdx.y: matrices at stride n, log|det| at
+// logdet + p * ld_stride, scaling flag scal[p * scal_stride] (or `scaling` for
+// all when scal is null), stats at stats + 4 p, partials and ticket per problem.
 __global__ void __launch_bounds__(256) k_newton_combine(const zd* __restrict__ x, const zd* __restrict__ xi,
                                                         zd* __restrict__ xn, int64_t n, int k,
-                                                        const double* __restrict__ logdet, int scaling,
+                                                        const double* __restrict__ logdet, int ld_stride,
+                                                        const int* __restrict__ scal, int scal_stride, int scaling,
                                                         double s, double w, double* stats, zd* part,
-                                                        unsigned* cnt) {
+                                                        int64_t part_stride, unsigned* cnt,
+                                                        const int* __restrict__ act) {
   __shared__ zd scratch[32];
+  const int p = blockIdx.y;
+  if (act && !act[p]) return;
+  x += p * n;
+  xi += p * n;
+  xn += p * n;
+  stats += 4 * p;
+  part += p * part_stride;
+  cnt += 4 * p;
+  const int sc = scal ? scal[(int64_t)p * scal_stride] : scaling;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   zd v[1] = {mk(0.0, 0.0)};
-  const double g = scaling ? exp(-(*logdet) / k) : 1.0;
+  const double g = sc ? exp(-logdet[(int64_t)p * ld_stride] / k) : 1.0;
   if (i < n) {
     const zd a = x[i], b = xi[i];
     const double h = 0.5 * s / g;
@@ -371,7 +433,16 @@ __global__ void __launch_bounds__(256) k_newton_combine(const zd* __restrict__ x
 void dense_newton_combine(const zd* x, const zd* xi, zd* xn, int k, const double* logdet, int scaling,
                           double s, double w, double* stats, zd* part, unsigned* cnt, cudaStream_t st) {
   const int64_t n = (int64_t)k * k;
-  k_newton_combine<<<nblk(n, 256), 256, 0, st>>>(x, xi, xn, n, k, logdet, scaling, s, w, stats, part, cnt);
+  k_newton_combine<<<nblk(n, 256), 256, 0, st>>>(x, xi, xn, n, k, logdet, 0, nullptr, 0, scaling, s, w, stats, part,
+                                                 0, cnt, nullptr);
+}
+void dense_newton_combine_batch(const zd* x, const zd* xi, zd* xn, int k, int nb, const int* act,
+                                const double* logdet, int ld_stride, const int* scal, int scal_stride, double s,
+                                double w, double* stats, zd* part, int64_t part_stride, unsigned* cnt,
+                                cudaStream_t st) {
+  const int64_t n = (int64_t)k * k;
+  k_newton_combine<<<dim3(nblk(n, 256), nb), 256, 0, st>>>(x, xi, xn, n, k, logdet, ld_stride, scal, scal_stride, 0,
+                                                           s, w, stats, part, part_stride, cnt, act);
 }
 
 }  // namespace ov

@@ -132,18 +132,30 @@ void dense_build_t(const zd* alpha, const zd* beta, const double* delta, int k, 
 void dense_adjoint(const zd* A, zd* B, int k, cudaStream_t st);
 void dense_copy(const zd* A, zd* B, int64_t n, cudaStream_t st);
 void dense_zero(zd* A, int64_t n, cudaStream_t st);
-// Ainv = A^{-1} by Gauss-Jordan with partial pivoting (A is not modified; w0, w1 are
-// k x k work buffers; ipiv, used: k ints; cand: 2 * ceil(k/4) entries);
-// logdet[0] += sum log|pivot| = log|det A|
-void dense_inverse(const zd* A, zd* Ainv, zd* w0, zd* w1, int k, int* ipiv, int* used, unsigned long long* keys,
-                   double* logdet, int* err, cudaStream_t st);
+// Batched forms: nb problems, problem p at A + p * sA (etc.); act (device, may be
+// null = all) switches problems off, so each problem can stop on its own.
+void dense_copy_batch(const zd* A, int64_t sA, zd* B, int64_t sB, int64_t n, int nb, const int* act,
+                      cudaStream_t st);
+// Ainv = A^{-1} by Gauss-Jordan with partial pivoting for nb problems (matrices
+// at stride k*k; A is not modified; w0, w1 work matrices; ipiv, used: k ints and
+// keys: k + 1 words per problem); logdet[p * ld_stride] += log|det A_p|
+void dense_inverse(const zd* A, zd* Ainv, zd* w0, zd* w1, int k, int nb, const int* act, int* ipiv, int* used,
+                   unsigned long long* keys, double* logdet, int ld_stride, int* err, cudaStream_t st);
 void dense_gemm(const zd* A, const zd* B, zd* C, int k, cudaStream_t st);   // C = A B
 // C = op(A) op(B), op = conjugate transpose when the flag is set
 void dense_gemm_op(const zd* A, int hA, const zd* B, int hB, zd* C, int k, cudaStream_t st);
+void dense_gemm_batch(const zd* A, int64_t sA, int hA, const zd* B, int64_t sB, int hB, zd* C, int64_t sC, int k,
+                      int nb, const int* act, cudaStream_t st);
 // Xn = 0.5 (g X + s Xi / g) with g = |det|^(-1/k) from *logdet when scaling, else 1;
 // stats[0] += w |Xn - X|^2, stats[1] += w |Xn|^2 (deterministic order)
 void dense_newton_combine(const zd* X, const zd* Xi, zd* Xn, int k, const double* logdet, int scaling,
                           double s, double w, double* stats, zd* part, unsigned* cnt, cudaStream_t st);
+// batched: log|det| at logdet[p * ld_stride], scaling flag scal[p * scal_stride],
+// stats at stats + 4 p, partials at part + p * part_stride, tickets at cnt + 4 p
+void dense_newton_combine_batch(const zd* X, const zd* Xi, zd* Xn, int k, int nb, const int* act,
+                                const double* logdet, int ld_stride, const int* scal, int scal_stride, double s,
+                                double w, double* stats, zd* part, int64_t part_stride, unsigned* cnt,
+                                cudaStream_t st);
 void dense_set_column0(zd* E, const zd* gy, int64_t gy_stride, double beta0, int k, cudaStream_t st);
 void dense_extract_y(const zd* F, double beta0, int k, zd* y, cudaStream_t st);
 void dense_extract_tri(const zd* E, int k, zd* ga, zd* gb, double* gd, cudaStream_t st);
