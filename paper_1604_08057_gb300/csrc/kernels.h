@@ -70,6 +70,7 @@ struct Rev {
   int* reb_steps;            // [nreb_max] step of each recorded projection (host-ordered)
   int nreb_max;
   double* force;             // FP64 accumulator, 36 complex * V  (zd, layout e*V + x)
+  double* force_parts;       // small lattices: force_splits(V) partial forces (72 V doubles each), or null
   double* dmu;               // single accumulator
   zd* dmu_part;              // partials for dmu
   unsigned* dmu_cnt;
@@ -123,6 +124,10 @@ template <typename R> void rev_alpha_dots(const Lat<R>& L, const Rev<R>& B, int 
 template <typename R> void rev_combine(const Lat<R>& L, const Rev<R>& B, int j, int slot, cudaStream_t st);
 template <typename R> void rev_stencil(const Lat<R>& L, const Rev<R>& B, int j, int slot, int prev_slot,
                                        int nrec, cudaStream_t st);
+// splits of the force contraction's (source, term) items: 1 unless the lattice has
+// too few sites to fill the GPU, at most kForceSplitMax
+constexpr int kForceSplitMax = 8;
+int force_splits(int64_t V);
 template <typename R> void force_flush(const Lat<R>& L, const Rev<R>& B, const int* steps_dev, int nterms,
                                        int first_slot, cudaStream_t st);
 void unpack_force(const double* force, double* du_aos, int64_t V, cudaStream_t st);

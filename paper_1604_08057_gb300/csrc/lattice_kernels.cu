@@ -1078,7 +1078,9 @@ __device__ void force_term(const Lat<R>& L, int64_t x, int64_t xf, const R* a, c
 }
 
 template <int NU, typename R>
-__device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterms, int j0, zd* dmu_site) {
+__device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterms, int j0, int i0, int i1,
+                          double* part, zd* dmu_site) {
+  // items i0 .. i1-1 of the (source, term) pairs, source outer
   int c[4];
   site_coords(L.g, x, c);
   const int64_t xf = neighbour(L.g, x, c, NU, +1);
@@ -1086,10 +1088,11 @@ __device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterm
   zd accd[9];
 #pragma unroll
   for (int e = 0; e < 9; ++e) acc[e] = accd[e] = mk(0.0, 0.0);
-  for (int src = 0; src < L.nsrc; ++src) {
+  for (int src = i0 / nterms; src * nterms < i1; ++src) {
+    const int t0 = max(i0 - src * nterms, 0), t1 = min(i1 - src * nterms, nterms);
     if constexpr (sizeof(R) == 8) {
       // FP64 fields: accumulate straight into the FP64 sums
-      for (int t = 0; t < nterms; ++t) {
+      for (int t = t0; t < t1; ++t) {
         const int j = j0 - t;
         force_term<NU>(L, x, xf, B.ring(B.gp_ring, t, src), L.basis_v(src, j), acc, accd);
         if (j < L.k - 1) force_term<NU>(L, x, xf, L.basis_w(src, j), B.ring(B.gs_ring, t, src), acc, accd);
@@ -1099,7 +1102,7 @@ __device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterm
       cplx<R> G[9], Gd[9];
 #pragma unroll
       for (int e = 0; e < 9; ++e) G[e] = Gd[e] = czero<R>();
-      for (int t = 0; t < nterms; ++t) {
+      for (int t = t0; t < t1; ++t) {
         const int j = j0 - t;
         force_term<NU>(L, x, xf, B.ring(B.gp_ring, t, src), L.basis_v(src, j), G, Gd);
         if (j < L.k - 1) force_term<NU>(L, x, xf, L.basis_w(src, j), B.ring(B.gs_ring, t, src), G, Gd);
@@ -1111,13 +1114,19 @@ __device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterm
       }
     }
   }
-  double2* f = reinterpret_cast<double2*>(B.force);
+  if (part) {   // a split of the items: its own partial sum, added in split order later
+    double2* f = reinterpret_cast<double2*>(part);
 #pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    double2 o = f[(int64_t)(NU * 9 + e) * L.g.V + x];
-    o.x += acc[e].re;
-    o.y += acc[e].im;
-    f[(int64_t)(NU * 9 + e) * L.g.V + x] = o;
+    for (int e = 0; e < 9; ++e) f[(int64_t)(NU * 9 + e) * L.g.V + x] = make_double2(acc[e].re, acc[e].im);
+  } else {
+    double2* f = reinterpret_cast<double2*>(B.force);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      double2 o = f[(int64_t)(NU * 9 + e) * L.g.V + x];
+      o.x += acc[e].re;
+      o.y += acc[e].im;
+      f[(int64_t)(NU * 9 + e) * L.g.V + x] = o;
+    }
   }
   if (NU == 3) {
     double dm = 0.0;
@@ -1130,30 +1139,54 @@ __device__ void force_dir(const Lat<R>& L, const Rev<R>& B, int64_t x, int nterm
   }
 }
 
-// one launch per direction (smaller register footprint); the dmu partials come from NU = 3
+// One launch per direction (smaller register footprint); on small lattices the
+// (source, term) items are split over blockIdx.y, each split writing its own
+// partial force, added in split order by k_force_reduce.  dmu comes from NU = 3.
 template <int NU, typename R>
-__global__ void __launch_bounds__(BS) k_force(Lat<R> L, Rev<R> B, int nterms, int j0) {
+__global__ void __launch_bounds__(BS) k_force(Lat<R> L, Rev<R> B, int nterms, int j0, int nsplit, double* parts) {
   __shared__ zd scratch[32];
   const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int split = blockIdx.y, nitems = L.nsrc * nterms;
+  const int i0 = (int)((int64_t)split * nitems / nsplit), i1 = (int)((int64_t)(split + 1) * nitems / nsplit);
+  double* part = nsplit > 1 ? parts + (int64_t)split * 72 * L.g.V : nullptr;
   zd v[1] = {mk(0.0, 0.0)};
-  if (x < L.g.V) force_dir<NU>(L, B, x, nterms, j0, &v[0]);
+  if (x < L.g.V) force_dir<NU>(L, B, x, nterms, j0, i0, i1, part, &v[0]);
   if (NU != 3) return;
   block_sum<1>(v, scratch);
-  if (threadIdx.x == 0) B.dmu_part[blockIdx.x] = v[0];
-  if (arrive_last(B.dmu_cnt, gridDim.x)) {
+  if (threadIdx.x == 0) B.dmu_part[split * gridDim.x + blockIdx.x] = v[0];
+  if (arrive_last(B.dmu_cnt, gridDim.x * gridDim.y)) {
     zd s[1];
-    sum_partials<1>(B.dmu_part, gridDim.x, s, scratch);
+    sum_partials<1>(B.dmu_part, gridDim.x * gridDim.y, s, scratch);
     if (threadIdx.x == 0) *B.dmu += s[0].re;
   }
+}
+__global__ void k_force_reduce(double* __restrict__ force, const double* __restrict__ parts, int nsplit, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = force[i];
+  for (int sp = 0; sp < nsplit; ++sp) a += parts[sp * n + i];
+  force[i] = a;
+}
+int force_splits(int64_t V) {
+  const int64_t blocks = (V + BS - 1) / BS;
+  if (blocks >= 152) return 1;
+  const int64_t want = (2 * 152 + blocks - 1) / blocks;
+  return (int)(want < kForceSplitMax ? want : kForceSplitMax);
 }
 template <typename R>
 void force_flush(const Lat<R>& L, const Rev<R>& B, const int* /*unused*/, int nterms, int j0, cudaStream_t st) {
   if (nterms <= 0) return;
   const unsigned nb = nblocks(L.g.V, BS);
-  k_force<0, R><<<nb, BS, 0, st>>>(L, B, nterms, j0);
-  k_force<1, R><<<nb, BS, 0, st>>>(L, B, nterms, j0);
-  k_force<2, R><<<nb, BS, 0, st>>>(L, B, nterms, j0);
-  k_force<3, R><<<nb, BS, 0, st>>>(L, B, nterms, j0);
+  int nsplit = B.force_parts ? force_splits(L.g.V) : 1;
+  if (nsplit > L.nsrc * nterms) nsplit = L.nsrc * nterms;
+  k_force<0, R><<<dim3(nb, nsplit), BS, 0, st>>>(L, B, nterms, j0, nsplit, B.force_parts);
+  k_force<1, R><<<dim3(nb, nsplit), BS, 0, st>>>(L, B, nterms, j0, nsplit, B.force_parts);
+  k_force<2, R><<<dim3(nb, nsplit), BS, 0, st>>>(L, B, nterms, j0, nsplit, B.force_parts);
+  k_force<3, R><<<dim3(nb, nsplit), BS, 0, st>>>(L, B, nterms, j0, nsplit, B.force_parts);
+  if (nsplit > 1) {
+    const int64_t n = 72 * L.g.V;
+    k_force_reduce<<<nblocks(n, 256), 256, 0, st>>>(B.force, B.force_parts, nsplit, n);
+  }
 }
 
 // explicit instantiations

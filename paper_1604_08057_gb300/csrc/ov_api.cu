@@ -21,7 +21,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
 };
 
 struct Status {
@@ -991,8 +991,12 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
   if (!reb.empty())
     CK(cudaMemcpyAsync(B.reb_steps, reb.data(), sizeof(int) * reb.size(), cudaMemcpyHostToDevice, c->st));
   B.force = wsT<double>(c, B_FORCE, 72 * V, true);
+  {
+    const int ns = force_splits(V);
+    B.force_parts = ns > 1 ? wsT<double>(c, B_FPARTS, (int64_t)ns * 72 * V) : nullptr;
+  }
   B.dmu = wsT<double>(c, B_DMU, 1, true);
-  B.dmu_part = wsT<zd>(c, B_DMUPART, 4 * ((V + 127) / 128) + 64);
+  B.dmu_part = wsT<zd>(c, B_DMUPART, kForceSplitMax * ((V + 127) / 128) + 64);
   B.dmu_cnt = wsT<unsigned>(c, B_DMUCNT, 4);
   zd* coef = wsT<zd>(c, B_COEF, (int64_t)nsrc * 2 * k);
   run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_init(L, B, c->st); });
