@@ -430,3 +430,49 @@ def test_tape_vjp_equals_direct_vjp(precision, reb, passes, segment):
         du, dmu, _ = binding.tsl_sign_vjp(T(u), mu, m_w, T(b), k, T(xb), **opts)
         assert torch.equal(du_t, du) and dmu_t == dmu
     tape.free()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(1, 2, 3, 2), (2, 1, 1, 5), (1, 1, 1, 3)])
+def test_degenerate_lattice_extents(dims):
+    """Extents 1 and 2: a hop wraps onto the site itself or onto the same neighbour both ways."""
+    u, b, _ = case(dims, 0.3, 50, 2)
+    for dagger in (False, True):
+        got = binding.apply_H(T(u), 0.3, -1.0, T(b), dagger=dagger).cpu().numpy()
+        for s in range(2):
+            want = (dirac.apply_h_dagger if dagger else dirac.apply_h)(u, b[s], 0.3, -1.0)
+            assert rel(got[s], want) <= 1e-13
+    k = min(12, 12 * int(np.prod(dims)) - 1)
+    x = binding.tsl_sign(T(u), 0.3, -1.0, T(b), k).cpu().numpy()
+    for s in range(2):
+        assert rel(x[s], tsl.tsl_forward(u, b[s], 0.3, -1.0, k).x) <= 1e-11
+
+
+def test_hermitian_limit_mu_zero():
+    """At mu = 0, H is Hermitian: the left and right Lanczos vectors coincide, so the
+    coefficients are real and beta = delta, as in the oracle."""
+    dims, k = (3, 3, 2, 3), 40
+    u, b, _ = case(dims, 0.3, 51, 1)
+    x = binding.tsl_sign(T(u), 0.0, -1.0, T(b[0]), k).cpu().numpy()
+    a, bt, d = binding.tsl_coefficients(k)
+    assert np.abs(a.imag).max() <= 1e-12 * np.abs(a.real).max()
+    assert np.abs(bt[1:] - d[1:]).max() <= 1e-12 * np.abs(d[1:]).max()
+    assert rel(x, tsl.tsl_forward(u, b[0], 0.0, -1.0, k).x) <= 1e-11
+
+
+def test_out_of_range_arguments():
+    u, b, _ = case((2, 2, 2, 2), 0.3, 52, 1)
+    for k in (1, 4097):
+        with pytest.raises(binding.OVError) as e:
+            binding.tsl_sign(T(u), 0.3, -1.0, T(b[0]), k)
+        assert e.value.status == -1
+    with pytest.raises(binding.OVError) as e:          # kappa = 1/(2 m_w + 8) undefined
+        binding.apply_H(T(u), 0.3, -4.0, T(b[0]))
+    assert e.value.status == -1
+    # a zero direction: the derivative vanishes and x is still sgn(H) b
+    dx, x = binding.tsl_sign_jvp(T(u), 0.3, -1.0, T(b[0]), 20, None, 0.0)
+    assert float(dx.abs().max()) == 0.0
+    assert rel(x.cpu().numpy(), tsl.tsl_forward(u, b[0], 0.3, -1.0, 20).x) <= 1e-10
+
