@@ -329,10 +329,12 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const i
 // ---------------------------------------------------------------------------
 constexpr int GT = 32, GK = 16;
 // C = op(A) op(B); op = identity (0) or conjugate transpose (1)
-// batched over problems p = blockIdx.z: A at a + p * sa, B at b + p * sb, C at c + p * sc
-__global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, int64_t sa, const zd* __restrict__ b,
-                                              int64_t sb, zd* __restrict__ c, int64_t sc, int k, int ha, int hb,
-                                              const int* __restrict__ act) {
+// C (M x N) = op(A) (M x K) op(B) (K x N), row-major with leading dimensions
+// lda, ldb, ldc (op = H: the operand is stored transposed and conjugated).
+// Batched over problems p = blockIdx.z: A at a + p * sa, B at b + p * sb, C at c + p * sc.
+__global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, int64_t sa, int lda, const zd* __restrict__ b,
+                                              int64_t sb, int ldb, zd* __restrict__ c, int64_t sc, int ldc, int M,
+                                              int N, int K, int ha, int hb, const int* __restrict__ act) {
   __shared__ zd as[GT][GK + 1];
   __shared__ zd bs[GK][GT + 1];
   const int pz = blockIdx.z;
@@ -345,18 +347,18 @@ __global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, int64_t 
   zd acc[2][2];
   for (int r = 0; r < 2; ++r)
     for (int q = 0; q < 2; ++q) acc[r][q] = mk(0.0, 0.0);
-  for (int k0 = 0; k0 < k; k0 += GK) {
+  for (int k0 = 0; k0 < K; k0 += GK) {
     for (int t = threadIdx.x; t < GT * GK; t += 256) {
       // op(A)[gi][gk]: row-major read along gk, or (conjugated) along gi for the adjoint
       const int r = ha ? t % GT : t / GK, q = ha ? t / GT : t % GK;
       const int gi = row0 + r, gk = k0 + q;
       zd av = mk(0.0, 0.0);
-      if (gi < k && gk < k) av = ha ? conj(a[(int64_t)gk * k + gi]) : a[(int64_t)gi * k + gk];
+      if (gi < M && gk < K) av = ha ? conj(a[(int64_t)gk * lda + gi]) : a[(int64_t)gi * lda + gk];
       as[r][q] = av;
       const int r2 = hb ? t % GK : t / GT, q2 = hb ? t / GK : t % GT;
       const int gk2 = k0 + r2, gj = col0 + q2;
       zd bv = mk(0.0, 0.0);
-      if (gk2 < k && gj < k) bv = hb ? conj(b[(int64_t)gj * k + gk2]) : b[(int64_t)gk2 * k + gj];
+      if (gk2 < K && gj < N) bv = hb ? conj(b[(int64_t)gj * ldb + gk2]) : b[(int64_t)gk2 * ldb + gj];
       bs[r2][q2] = bv;
     }
     __syncthreads();
@@ -374,18 +376,61 @@ __global__ void __launch_bounds__(256) k_gemm(const zd* __restrict__ a, int64_t 
   for (int r = 0; r < 2; ++r)
     for (int q = 0; q < 2; ++q) {
       const int gi = row0 + ty * 2 + r, gj = col0 + tx * 2 + q;
-      if (gi < k && gj < k) c[(int64_t)gi * k + gj] = acc[r][q];
+      if (gi < M && gj < N) c[(int64_t)gi * ldc + gj] = acc[r][q];
     }
 }
 void dense_gemm(const zd* a, const zd* b, zd* c, int k, cudaStream_t st) {
-  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, 0, b, 0, c, 0, k, 0, 0, nullptr);
+  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, 0, k, b, 0, k, c, 0, k, k, k, k, 0, 0, nullptr);
 }
 void dense_gemm_op(const zd* a, int ha, const zd* b, int hb, zd* c, int k, cudaStream_t st) {
-  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, 0, b, 0, c, 0, k, ha, hb, nullptr);
+  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT)), 256, 0, st>>>(a, 0, k, b, 0, k, c, 0, k, k, k, k, ha, hb, nullptr);
 }
 void dense_gemm_batch(const zd* a, int64_t sa, int ha, const zd* b, int64_t sb, int hb, zd* c, int64_t sc, int k,
                       int nb, const int* act, cudaStream_t st) {
-  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT), nb), 256, 0, st>>>(a, sa, b, sb, c, sc, k, ha, hb, act);
+  k_gemm<<<dim3(nblk(k, GT), nblk(k, GT), nb), 256, 0, st>>>(a, sa, k, b, sb, k, c, sc, k, k, k, k, ha, hb, act);
+}
+void dense_gemm_rect_batch(const zd* a, int64_t sa, int lda, int ha, const zd* b, int64_t sb, int ldb, int hb, zd* c,
+                           int64_t sc, int ldc, int M, int N, int K, int nb, const int* act, cudaStream_t st) {
+  k_gemm<<<dim3(nblk(N, GT), nblk(M, GT), nb), 256, 0, st>>>(a, sa, lda, b, sb, ldb, c, sc, ldc, M, N, K, ha, hb,
+                                                             act);
+}
+
+// Low-rank start of the Frechet adjoint: E_0 = beta0_p g_p e_1^T = A B^H with
+// A[:, 0] = beta0_p g_p (g at gy + p * gy_pstride, element i at i * gy_stride),
+// B[:, 0] = e_1; factors are k x ld row-major, problem p at p * k * ld (zeroed first)
+__global__ void k_lr_init(zd* fa, zd* fb, int k, int ld, const zd* __restrict__ gy, int64_t gy_pstride,
+                          int64_t gy_stride, const double* __restrict__ beta0) {
+  const int p = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  const zd g = gy[p * gy_pstride + (int64_t)i * gy_stride];
+  const double b0 = beta0[p];
+  fa[(int64_t)p * k * ld + (int64_t)i * ld] = mk(b0 * g.re, b0 * g.im);
+  fb[(int64_t)p * k * ld + (int64_t)i * ld] = mk(i == 0 ? 1.0 : 0.0, 0.0);
+}
+// A[:, 0:r] *= g/2,  A[:, r:2r] *= -1/(2g),  g = |det X_i|^(-1/k) when scaling, else 1
+__global__ void k_lr_scale(zd* fa, int k, int ld, int r, const double* __restrict__ logdet, int ld_stride,
+                           const int* __restrict__ scal, int scal_stride, const int* __restrict__ act) {
+  const int p = blockIdx.y;
+  if (act && !act[p]) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)k * 2 * r) return;
+  const int i = (int)(t / (2 * r)), j = (int)(t % (2 * r));
+  const double g = scal[(int64_t)p * scal_stride] ? exp(-logdet[(int64_t)p * ld_stride] / k) : 1.0;
+  const double f = j < r ? 0.5 * g : -0.5 / g;
+  zd& v = fa[(int64_t)p * k * ld + (int64_t)i * ld + j];
+  v = mk(f * v.re, f * v.im);
+}
+void dense_lr_init(zd* fa, zd* fb, int k, int ld, const zd* gy, int64_t gy_pstride, int64_t gy_stride,
+                   const double* beta0, int nb, cudaStream_t st) {
+  cudaMemsetAsync(fa, 0, sizeof(zd) * (size_t)k * ld * nb, st);
+  cudaMemsetAsync(fb, 0, sizeof(zd) * (size_t)k * ld * nb, st);
+  k_lr_init<<<dim3(nblk(k, 128), nb), 128, 0, st>>>(fa, fb, k, ld, gy, gy_pstride, gy_stride, beta0);
+}
+void dense_lr_scale(zd* fa, int k, int ld, int r, const double* logdet, int ld_stride, const int* scal,
+                    int scal_stride, int nb, const int* act, cudaStream_t st) {
+  k_lr_scale<<<dim3(nblk((int64_t)k * 2 * r, 256), nb), 256, 0, st>>>(fa, k, ld, r, logdet, ld_stride, scal,
+                                                                      scal_stride, act);
 }
 
 // Xn = 0.5 (g X + s Xi / g);  stats += w * (|Xn - X|^2, |Xn|^2)

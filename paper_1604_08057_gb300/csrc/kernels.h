@@ -151,6 +151,14 @@ void dense_gemm(const zd* A, const zd* B, zd* C, int k, cudaStream_t st);   // C
 void dense_gemm_op(const zd* A, int hA, const zd* B, int hB, zd* C, int k, cudaStream_t st);
 void dense_gemm_batch(const zd* A, int64_t sA, int hA, const zd* B, int64_t sB, int hB, zd* C, int64_t sC, int k,
                       int nb, const int* act, cudaStream_t st);
+// C (M x N) = op(A) op(B) with leading dimensions (op = conjugate transpose when the flag is set)
+void dense_gemm_rect_batch(const zd* A, int64_t sA, int lda, int hA, const zd* B, int64_t sB, int ldb, int hB, zd* C,
+                           int64_t sC, int ldc, int M, int N, int K, int nb, const int* act, cudaStream_t st);
+// low-rank Frechet adjoint: factors A, B (k x ld each per problem) of E = A B^H
+void dense_lr_init(zd* A, zd* B, int k, int ld, const zd* gy, int64_t gy_pstride, int64_t gy_stride,
+                   const double* beta0, int nb, cudaStream_t st);
+void dense_lr_scale(zd* A, int k, int ld, int r, const double* logdet, int ld_stride, const int* scal,
+                    int scal_stride, int nb, const int* act, cudaStream_t st);
 // Xn = 0.5 (g X + s Xi / g) with g = |det|^(-1/k) from *logdet when scaling, else 1;
 // stats[0] += w |Xn - X|^2, stats[1] += w |Xn|^2 (deterministic order)
 void dense_newton_combine(const zd* X, const zd* Xi, zd* Xn, int k, const double* logdet, int scaling,

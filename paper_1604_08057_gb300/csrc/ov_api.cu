@@ -21,7 +21,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
 };
 
 struct Status {
@@ -852,16 +852,53 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
     std::vector<int> hscal((size_t)nsrc * NREC, 0), act(nsrc, 0), cur(nsrc, 0), extra(nsrc, 0);
     std::vector<double> prev(nsrc, INFINITY), hs(4 * (size_t)nsrc);
     int rec_max = 0;
+    std::vector<double> hb0(nsrc, 0.0);
+    std::vector<int> okm(nsrc, 0);
     for (int src = 0; src < nsrc; ++src) {
+      hb0[src] = hsc[src].beta0;
       if (!F.rec_ok[src]) continue;
+      okm[src] = 1;
       for (size_t i = 0; i < F.scaling[src].size(); ++i) hscal[(size_t)src * NREC + i] = F.scaling[src][i];
       rec_max = std::max(rec_max, F.iters[src]);
-      run(c, OV_KIND_DENSE, 2,
-          [&] { dense_set_column0(e[0] + src * n, gy + (int64_t)src * 2 * k, 2, hsc[src].beta0, k, c->st); });
     }
     CK(cudaMemcpyAsync(rscal, hscal.data(), sizeof(int) * hscal.size(), cudaMemcpyHostToDevice, c->st));
-    for (int i = 0; i < rec_max; ++i) {
-      const int ce = i & 1;
+    // Low-rank start: E_0 = beta0 g_y e_1^T has rank one and each iteration at most
+    // doubles the rank, so while it is small E = A B^H is kept as k x r factors:
+    //   A <- [g A / 2 | -Y A / (2 g)],  B <- [B | Y^H B]   (Y = X_i^{-H}),
+    // two k x k x r products instead of two k^3 ones; E is formed once the rank
+    // would pass rmax.  (Factors beyond a source's own rank stay zero.)
+    int rmax = 0;
+    for (int r = 2; r <= 256 && r <= k / 2; r *= 2) rmax = r;
+    if (rmax < 2) rmax = 1;
+    zd* fa = wsT<zd>(c, B_LRA, (int64_t)nsrc * k * rmax);
+    zd* fb = wsT<zd>(c, B_LRB, (int64_t)nsrc * k * rmax);
+    double* b0dev = wsT<double>(c, B_BETA0, nsrc);
+    CK(cudaMemcpyAsync(b0dev, hb0.data(), sizeof(double) * nsrc, cudaMemcpyHostToDevice, c->st));
+    run(c, OV_KIND_DENSE, 1, [&] { dense_lr_init(fa, fb, k, rmax, gy, 2 * (int64_t)k, 2, b0dev, nsrc, c->st); });
+    int i0 = 0, rank = 1;
+    const int64_t fs = (int64_t)k * rmax;
+    while (2 * rank <= rmax && i0 < rec_max) {
+      for (int src = 0; src < nsrc; ++src) act[src] = F.rec_ok[src] && i0 < F.iters[src];
+      CK(cudaMemcpyAsync(act_dev, act.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, c->st));
+      const zd* yi = F.rec_inv + (int64_t)i0 * n;
+      run(c, OV_KIND_DENSE_GEMM, 2, [&] {
+        dense_gemm_rect_batch(yi, (int64_t)NREC * n, k, 1, fa, fs, rmax, 0, fa + rank, fs, rmax, k, rank, k, nsrc,
+                              act_dev, c->st);
+        dense_gemm_rect_batch(yi, (int64_t)NREC * n, k, 0, fb, fs, rmax, 0, fb + rank, fs, rmax, k, rank, k, nsrc,
+                              act_dev, c->st);
+      });
+      run(c, OV_KIND_DENSE, 1, [&] {
+        dense_lr_scale(fa, k, rmax, rank, F.rec_ld + i0, NREC, rscal + i0, NREC, nsrc, act_dev, c->st);
+      });
+      rank *= 2;
+      ++i0;
+    }
+    CK(cudaMemcpyAsync(act_dev, okm.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, c->st));
+    run(c, OV_KIND_DENSE_GEMM, 1, [&] {
+      dense_gemm_rect_batch(fa, fs, rmax, 0, fb, fs, rmax, 1, e[0], n, k, k, k, rank, nsrc, act_dev, c->st);
+    });
+    for (int i = i0; i < rec_max; ++i) {
+      const int ce = (i - i0) & 1;
       for (int src = 0; src < nsrc; ++src) act[src] = F.rec_ok[src] && i < F.iters[src];
       CK(cudaMemcpyAsync(act_dev, act.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, c->st));
       const zd* yi = F.rec_inv + (int64_t)i * n;
@@ -874,10 +911,11 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
                                    1.0, dstat, dpart, pstride, dcnt, c->st);
       });
     }
-    // bring every source's iterate to e[0] (its parity is its own iteration count)
+    // bring every source's iterate to e[0] (its parity is its own count of dense iterations)
     for (int src = 0; src < nsrc; ++src) {
       if (!F.rec_ok[src]) continue;
-      if (F.iters[src] & 1) run(c, OV_KIND_DENSE, 1, [&] { dense_copy(e[1] + src * n, e[0] + src * n, n, c->st); });
+      if (std::max(F.iters[src] - i0, 0) & 1)
+        run(c, OV_KIND_DENSE, 1, [&] { dense_copy(e[1] + src * n, e[0] + src * n, n, c->st); });
       act[src] = 1;
     }
     for (int x = 1; x <= 4; ++x) {
