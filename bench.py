@@ -319,6 +319,7 @@ def run_ours(args, rank, world, local_rank):
            "roofline": roofline, "clocks": clk, "autotune": tune}
 
     if not args.no_extras and rank == 0:
+        out["forward_only"] = forward_leg(args, ut, bt, wl, k)
         out["e2e"] = e2e_leg(args, ut, bt, xt, wl, k)
         out["dw_stencil"] = stencil_leg(args, ut, wl, hbm, peak_src)
         out["mixed_path"] = mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar)
@@ -345,6 +346,24 @@ def fp64_peak(dev, n=4096, reps=3):
     e1.record()
     torch.cuda.synchronize()
     return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
+def forward_leg(args, ut, bt, wl, k, reps=2):
+    """Seconds per sgn(H)b alone (ov_tsl_sign, same workload and schedule), device-timed."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    opts = (args.precision, args.rebiorth, args.passes)
+    binding.tsl_sign(ut, wl.mu, wl.m_w, bt, k, *opts, segment=args.segment)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        _, info = binding.tsl_sign(ut, wl.mu, wl.m_w, bt, k, *opts, return_info=True, segment=args.segment)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"value": round(e0.elapsed_time(e1) / 1e3 / reps, 6), "unit": "s per sgn(H)b", "steps": reps,
+            "newton_iters": info["newton_iters"]}
 
 
 def e2e_leg(args, ut, bt, xt, wl, k):
