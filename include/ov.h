@@ -251,6 +251,11 @@ int ov_tsl_coefficients(ov_context *ctx, int32_t src, int32_t k, double *alpha, 
 #define OV_KIND_DENSE_GEMM   11  /* k x k products of the block Frechet iteration */
 #define OV_NKIND             12
 int ov_profile_enable(ov_context *ctx, int32_t enable);
+/* Restrict the timing to the kinds whose bit (1 << OV_KIND_*) is set in
+ * kind_mask (all kinds by default): each timed launch group costs two event
+ * records on the stream, so a caller timing one kernel kind inside a long run
+ * can leave the others untimed. */
+int ov_profile_select(ov_context *ctx, uint32_t kind_mask);
 /* Totals since the last reset for `kind`: number of timed launches and summed
  * device milliseconds.  reset != 0 clears all kinds after reading. */
 int ov_profile_read(ov_context *ctx, int32_t kind, int64_t *launches, double *ms, int32_t reset);

@@ -63,7 +63,7 @@ class Problem(ctypes.Structure):
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
-           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_strerror"]
+           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     lib.ov_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, ctypes.POINTER(Info)]
     lib.ov_block_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, ctypes.POINTER(Info)]
     lib.ov_profile_enable.argtypes = [P, I32]
+    lib.ov_profile_select.argtypes = [P, ctypes.c_uint32]
     lib.ov_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D), I32]
     lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
     lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
@@ -399,6 +400,12 @@ def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2, segment=0
 
 def profile_enable(ctx, on=True):
     _check(load().ov_profile_enable(ctx, int(bool(on))), "ov_profile_enable")
+
+
+def profile_select(ctx, kinds=None):
+    """Time only the named kinds (None: all)."""
+    mask = 0xFFFFFFFF if kinds is None else sum(1 << KINDS.index(k) for k in kinds)
+    _check(load().ov_profile_select(ctx, mask), "ov_profile_select")
 
 
 def profile_read(ctx, reset=False) -> dict:

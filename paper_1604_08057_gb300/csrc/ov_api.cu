@@ -53,6 +53,7 @@ constexpr int NPROF = 8192;   // event pairs recorded before an intermediate col
 
 struct Prof {
   bool on = false;
+  uint32_t mask = ~0u;   // kinds to time (bit per OV_KIND_*)
   int n = 0;
   cudaEvent_t a[NPROF] = {}, b[NPROF] = {};
   int kind[NPROF] = {};
@@ -96,7 +97,7 @@ void prof_collect(ov_context* c) {
 template <typename F>
 void run(ov_context* c, int kind, int64_t nl, F&& f) {
   Prof* p = c->prof;
-  const bool rec = p && p->on;
+  const bool rec = p && p->on && ((p->mask >> kind) & 1u);
   if (rec && p->n == NPROF) prof_collect(c);
   if (rec) CK(cudaEventRecord(p->a[p->n], c->st));
   f();
@@ -1258,20 +1259,36 @@ int ov_context_destroy(ov_context* c) {
   return OV_OK;
 }
 
-int ov_profile_enable(ov_context* c, int32_t enable) {
-  if (!c) return OV_ERR_INVALID_ARG;
-  if (!c->prof) {
-    if (!enable) return OV_OK;
-    c->prof = new (std::nothrow) Prof();
-    if (!c->prof) return OV_ERR_OOM;
-    for (int i = 0; i < NPROF; ++i) {
-      if (cudaEventCreate(&c->prof->a[i]) != cudaSuccess || cudaEventCreate(&c->prof->b[i]) != cudaSuccess) {
-        cudaGetLastError();
-        return OV_ERR_CUDA;
-      }
+static int prof_create(ov_context* c) {
+  if (c->prof) return OV_OK;
+  c->prof = new (std::nothrow) Prof();
+  if (!c->prof) return OV_ERR_OOM;
+  for (int i = 0; i < NPROF; ++i) {
+    if (cudaEventCreate(&c->prof->a[i]) != cudaSuccess || cudaEventCreate(&c->prof->b[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return OV_ERR_CUDA;
     }
   }
+  return OV_OK;
+}
+
+int ov_profile_enable(ov_context* c, int32_t enable) {
+  if (!c) return OV_ERR_INVALID_ARG;
+  if (!c->prof && !enable) return OV_OK;
+  const int st = prof_create(c);
+  if (st != OV_OK) return st;
   c->prof->on = enable != 0;
+  return OV_OK;
+}
+
+int ov_profile_select(ov_context* c, uint32_t kind_mask) {
+  if (!c) return OV_ERR_INVALID_ARG;
+  int st = prof_create(c);
+  if (st != OV_OK) return st;
+  // pairs already recorded keep their kinds; collect them under the old mask
+  st = guarded([&] { prof_collect(c); return OV_OK; });
+  if (st != OV_OK) return st;
+  c->prof->mask = kind_mask;
   return OV_OK;
 }
 

@@ -476,3 +476,30 @@ def test_out_of_range_arguments():
     assert float(dx.abs().max()) == 0.0
     assert rel(x.cpu().numpy(), tsl.tsl_forward(u, b[0], 0.3, -1.0, 20).x) <= 1e-10
 
+
+
+def test_profile_select_times_only_selected_kinds():
+    """The kind mask leaves results and launch counts alone and times only the selected kinds."""
+    u, b, _ = case((4, 4, 4, 4), 0.3, 1)
+    ut, bt = (torch.tensor(a, device=DEV) for a in (u, b))
+    ctx = binding.context("fp64", 1, 2)
+    binding.profile_enable(ctx, True)
+    binding.profile_read(ctx, reset=True)
+    x_all = binding.tsl_sign(ut, 0.3, -2.0, bt, 40, "fp64", 1, 2)
+    all_kinds = binding.profile_read(ctx, reset=True)
+    binding.profile_select(ctx, ["stencil_pair", "proj_dots"])
+    l0 = binding.launch_count(ctx)
+    x_sel = binding.tsl_sign(ut, 0.3, -2.0, bt, 40, "fp64", 1, 2)
+    nl = binding.launch_count(ctx) - l0
+    sel = binding.profile_read(ctx, reset=True)
+    binding.profile_select(ctx, None)
+    binding.profile_enable(ctx, False)
+    assert torch.equal(x_all, x_sel)
+    assert nl > 0
+    for kd in binding.KINDS:
+        if kd in ("stencil_pair", "proj_dots"):
+            assert sel[kd][0] == all_kinds[kd][0] > 0
+            assert sel[kd][1] > 0.0
+        else:
+            assert sel[kd] == (0, 0.0)
+    assert sum(v[0] for v in all_kinds.values()) > sel["stencil_pair"][0] + sel["proj_dots"][0]
