@@ -48,6 +48,8 @@ extern "C" {
 #define OV_ERR_CUDA           -5  /* a CUDA runtime call failed */
 #define OV_ERR_NONFINITE      -6  /* a NaN or Inf appeared in a recurrence coefficient */
 #define OV_ERR_SCRATCH_LIMIT  -7  /* the problem does not fit the fixed scratch of ov_apply_H_noalloc */
+#define OV_ERR_TIMEOUT        -8  /* a device-side wait between blocks ran past its limit (2 s); the
+                                     blocks stop and the context stays usable */
 
 /* Precision of lattice vectors, links and stencil arithmetic.
  * OV_FP64 : everything in FP64.
@@ -68,7 +70,13 @@ typedef struct {
                         * recomputes each segment bit for bit when x = V_k y, g_y = V_k^dag xbar
                         * and the reverse sweep need its vectors.  Requires rebiorth = 0 (every
                         * projection reads the whole basis); not for the block TSL. */
-  int32_t reserved[4];
+  int32_t dense;       /* k x k inversions of the Newton sign (Gauss-Jordan, partial pivoting):
+                        * 0: one cooperative launch per inversion where the problems' rows fit
+                        * in shared memory (rows stay on chip for all k elimination steps; the
+                        * steps are separated by bounded inter-block waits), else 1;
+                        * 1: one launch per elimination step, replayed as a CUDA graph.
+                        * Both give bitwise identical results. */
+  int32_t reserved[3];
 } ov_options;
 
 typedef struct {
@@ -251,6 +259,14 @@ int ov_tsl_coefficients(ov_context *ctx, int32_t src, int32_t k, double *alpha, 
 #define OV_KIND_DENSE_GEMM   11  /* k x k products of the block Frechet iteration */
 #define OV_NKIND             12
 int ov_profile_enable(ov_context *ctx, int32_t enable);
+/* Self-test of the bounded inter-block wait used by the cooperative k x k
+ * inversion (an implementation detail with no counterpart in the paper): two
+ * blocks wait on a counter that nothing increments; the first gives up after
+ * limit_ns (1 .. 1e8 ns) and flags it, the second, with a 100x longer limit,
+ * must leave through that flag.  Returns OV_ERR_TIMEOUT when both left as
+ * designed (*elapsed_ms = device time of the launch), OV_ERR_CUDA otherwise.
+ * No GPU state outlives the call. */
+int ov_selftest_wait(ov_context *ctx, uint64_t limit_ns, double *elapsed_ms);
 /* Restrict the timing to the kinds whose bit (1 << OV_KIND_*) is set in
  * kind_mask (all kinds by default): each timed launch group costs two event
  * records on the stream, so a caller timing one kernel kind inside a long run

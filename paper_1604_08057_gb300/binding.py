@@ -34,7 +34,8 @@ class OVError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
-                ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("dense", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class TuneReport(ctypes.Structure):
@@ -63,7 +64,7 @@ class Problem(ctypes.Structure):
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
-           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_strerror"]
+           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
     lib.ov_block_tsl_eps.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, P, ctypes.POINTER(Info)]
     lib.ov_profile_enable.argtypes = [P, I32]
     lib.ov_profile_select.argtypes = [P, ctypes.c_uint32]
+    lib.ov_selftest_wait.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(D)]
     lib.ov_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D), I32]
     lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
     lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
@@ -128,6 +130,15 @@ def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=
                    "ov_context_create")
         _contexts[key] = h
     return _contexts[key]
+
+
+def dense_mode(mode: int, precision: str = "fp64", rebiorth: int = 1, passes: int = 2, segment: int = 0):
+    """How the k x k inversions run on the cached context for these options:
+    0 one cooperative launch per inversion where the rows fit on chip (default),
+    1 one launch per Gauss-Jordan step replayed as a graph (identical results)."""
+    ctx = context(precision, rebiorth, passes, segment=segment)
+    opt = Options(_PREC[precision], rebiorth, passes, segment, int(mode))
+    _check(load().ov_context_set_options(ctx, ctypes.byref(opt)), "ov_context_set_options")
 
 
 def _dims(u: torch.Tensor):
@@ -400,6 +411,13 @@ def tsl_coefficients(k, src=0, precision="fp64", rebiorth=1, passes=2, segment=0
 
 def profile_enable(ctx, on=True):
     _check(load().ov_profile_enable(ctx, int(bool(on))), "ov_profile_enable")
+
+
+def selftest_wait(limit_ns: int = 1_000_000):
+    """Run the bounded-wait self-test; returns (status, device ms)."""
+    ms = ctypes.c_double(0.0)
+    st = load().ov_selftest_wait(context(), int(limit_ns), ctypes.byref(ms))
+    return st, ms.value
 
 
 def profile_select(ctx, kinds=None):

@@ -106,6 +106,18 @@ void dense_extract_tri(const zd* e, int k, zd* ga, zd* gb, double* gd, cudaStrea
 constexpr int GJ_THREADS = 128;
 constexpr int GJ_JPT = 8;   // columns per thread held in registers (k <= 1024)
 
+// The inversion's products with explicit roundings, so that every kernel form
+// (one launch per step, or one cooperative launch) rounds them identically,
+// whatever the compiler would contract on its own.
+__device__ __forceinline__ double gj_nrm(zd a) { return fma(a.re, a.re, a.im * a.im); }
+__device__ __forceinline__ zd gj_mul(zd a, zd b) {
+  return mk(fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re));
+}
+__device__ __forceinline__ zd gj_recip(zd b) {
+  const double d = gj_nrm(b);
+  return mk(b.re / d, -b.im / d);
+}
+
 __device__ __forceinline__ unsigned long long gj_key(double nrm, int i) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(nrm);
   return ((b >> 12) << 12) | (unsigned long long)(4095 - i);
@@ -128,7 +140,7 @@ __global__ void k_gj_init(const zd* __restrict__ x, int k, unsigned long long* k
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= k) return;
   used[(int64_t)p * k + i] = 0;
-  gj_offer(keys + (int64_t)p * (k + 1), norm2(x[(int64_t)p * k * k + (int64_t)i * k]), i, err);
+  gj_offer(keys + (int64_t)p * (k + 1), gj_nrm(x[(int64_t)p * k * k + (int64_t)i * k]), i, err);
 }
 
 template <int JPT>
@@ -170,8 +182,8 @@ __global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict_
   // 1/pivot and the row factor m = X[i][kk]/pivot, once per warp
   zd inv = mk(0.0, 0.0), m = mk(0.0, 0.0);
   if ((threadIdx.x & 31) == 0) {
-    inv = zdiv(mk(1.0, 0.0), piv);
-    m = fr * inv;
+    inv = gj_recip(piv);
+    m = gj_mul(fr, inv);
   }
   inv.re = __shfl_sync(0xffffffffu, inv.re, 0);
   inv.im = __shfl_sync(0xffffffffu, inv.im, 0);
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict_
       if (j >= k) break;
       zd v;
       if (i == p) {
-        v = (j == kk) ? inv : pv[q] * inv;
+        v = (j == kk) ? inv : gj_mul(pv[q], inv);
       } else if (j == kk) {
         v = mk(-m.re, -m.im);
       } else {
@@ -199,13 +211,13 @@ __global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict_
         cmsub(v, m, pv[q]);
       }
       yr[j] = v;
-      if (j == kk + 1 && offer) gj_offer(keys + kk + 1, norm2(v), i, err);
+      if (j == kk + 1 && offer) gj_offer(keys + kk + 1, gj_nrm(v), i, err);
     }
   } else {
     for (int j = threadIdx.x; j < k; j += GJ_THREADS) {
       zd v;
       if (i == p) {
-        v = (j == kk) ? inv : pr[j] * inv;
+        v = (j == kk) ? inv : gj_mul(pr[j], inv);
       } else if (j == kk) {
         v = mk(-m.re, -m.im);
       } else {
@@ -213,13 +225,13 @@ __global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict_
         cmsub(v, m, pr[j]);
       }
       yr[j] = v;
-      if (j == kk + 1 && offer) gj_offer(keys + kk + 1, norm2(v), i, err);
+      if (j == kk + 1 && offer) gj_offer(keys + kk + 1, gj_nrm(v), i, err);
     }
   }
   if (threadIdx.x == 0) {
     if (bad && i == 0) atomicOr(err, ERRB_SINGULAR);
     if (i == p) {
-      const double a = sqrt(norm2(piv));
+      const double a = sqrt(gj_nrm(piv));
       if (!(a > 0.0) || !isfinite(a)) atomicOr(err, ERRB_SINGULAR);
       *logdet += log(a);
       prows[kk] = p;
@@ -267,6 +279,325 @@ static void gj_launch_all(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, 
   k_gj_gather<<<dim3(nblk((int64_t)k * k, 256), nb), 256, 0, st>>>(in, ainv, ipiv, q, k, act);
 }
 
+// ---------------------------------------------------------------------------
+// The same Gauss-Jordan inversion as one cooperative launch per inversion.
+// Problem p owns blocks (0..bp-1, p); block b keeps rows [b*R, b*R + R) of its
+// matrix in shared memory for all k steps, so the matrix is read once and the
+// inverse written once.  Step kk needs the pivot row p_kk as it stood after
+// step kk-1; every block therefore publishes, at the end of each step, its own
+// best candidate row for the next column (fully updated, to a double-buffered
+// slot in global memory) and offers its key by atomicMax.  One barrier per
+// step separates the offers from their use; the candidate row is updated and
+// published before the bulk of the block's rows, so the barrier's latency is
+// hidden behind that update.  The arithmetic of every entry, the pivot keys
+// and the order of the log|det| sum are those of k_gj_step, so both forms give
+// identical results.  Waits are bounded by a time limit: a block that runs out
+// sets ERRB_TIMEOUT, and every block of every problem leaves at its next wait.
+// ---------------------------------------------------------------------------
+constexpr int GJP_THREADS = 256;
+constexpr int GJP_RMAX = 32;                       // rows per block (one warp ranks them)
+constexpr unsigned long long GJP_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// wait until *ctr >= target; false when another block gave up or the limit passed
+__device__ bool wait_count(const unsigned* ctr, unsigned target, int* err, unsigned long long limit_ns) {
+  const unsigned long long t0 = gtimer();
+  for (unsigned spin = 0;; ++spin) {
+    if (ld_acquire(ctr) >= target) return true;
+    if (*(volatile int*)err & ERRB_TIMEOUT) return false;
+    if ((spin & 255u) == 255u && (gtimer() - t0 > limit_ns || spin > (1u << 23))) {
+      atomicOr(err, ERRB_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// JPT: columns per thread (k <= JPT * GJP_THREADS); the pivot row's entries of
+// the thread's columns are held in registers for the bulk update.
+template <int JPT>
+__global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict__ a, zd* __restrict__ ainv, int k,
+                                                          int R, int bp, zd* pub0, zd* pub1,
+                                                          unsigned long long* keys, unsigned* ctr, int* ipiv,
+                                                          double* logdet, int ld_stride, int* err,
+                                                          const int* __restrict__ act, unsigned long long limit_ns) {
+  extern __shared__ double4 gjp_smem[];
+  zd* xs = reinterpret_cast<zd*>(gjp_smem);   // R rows x k
+  zd* pv = xs + (int64_t)R * k;               // the step's pivot row as it stood before the step
+  int* prow = reinterpret_cast<int*>(pv + k); // pivot row of each step
+  int* qs = prow + k;                         // inverse permutation (at the end)
+  __shared__ zd ms[GJP_RMAX];                 // row factors X[i][kk] / pivot
+  __shared__ int used_s[GJP_RMAX];
+  __shared__ unsigned long long best_s;
+  __shared__ int ok_s;
+  const int pb = blockIdx.y;
+  if (act && !act[pb]) return;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int r0 = b * R, nr = min(R, k - r0);
+  const int64_t n = (int64_t)k * k;
+  a += pb * n;
+  ainv += pb * n;
+  keys += (int64_t)pb * (k + 1);
+  ctr += pb;
+  ipiv += (int64_t)pb * k;
+  logdet += (int64_t)pb * ld_stride;
+  pub0 += (int64_t)pb * bp * k;
+  pub1 += (int64_t)pb * bp * k;
+  double ld = 0.0;
+  if (b == 0 && t == 0) ld = *logdet;
+
+  for (int64_t e = t; e < (int64_t)nr * k; e += GJP_THREADS) xs[e] = a[(int64_t)r0 * k + e];
+  if (t < GJP_RMAX) used_s[t] = 0;
+  __syncthreads();
+  // offers for column 0: the rows as loaded
+  if (t < 32) {
+    unsigned long long key = 0ull;
+    if (t < nr) {
+      const double nrm = gj_nrm(xs[(int64_t)t * k]);
+      if (!(nrm >= 0.0)) atomicOr(err, ERRB_SINGULAR);
+      else key = gj_key(nrm, r0 + t);
+    }
+    key = warp_max_u64(key);
+    if (t == 0) best_s = key;
+  }
+  __syncthreads();
+  if (best_s) {
+    const int lr = 4095 - (int)(best_s & 4095ull) - r0;
+    for (int j = t; j < k; j += GJP_THREADS) pub0[(int64_t)b * k + j] = xs[(int64_t)lr * k + j];
+  }
+  __syncthreads();
+  if (t == 0) {
+    if (best_s) atomicMax(keys, best_s);
+    __threadfence();
+    atomicAdd(ctr, 1u);
+  }
+
+  for (int kk = 0; kk < k; ++kk) {
+    if (t == 0) {
+      ok_s = wait_count(ctr, (unsigned)bp * (unsigned)(kk + 1), err, limit_ns) ? 1 : 0;
+      __threadfence();
+    }
+    __syncthreads();
+    if (!ok_s) return;
+    const unsigned long long key = __ldcg(keys + kk);
+    const int p = 4095 - (int)(key & 4095ull);
+    if (key == 0ull || p < 0 || p >= k) {   // every block sees the same key and leaves
+      if (b == 0 && t == 0) atomicOr(err, ERRB_SINGULAR);
+      return;
+    }
+    const zd* prg = ((kk & 1) ? pub1 : pub0) + (int64_t)(p / R) * k;
+    zd pvr[JPT];
+#pragma unroll
+    for (int q = 0; q < JPT; ++q) {
+      const int j = t + q * GJP_THREADS;
+      pvr[q] = j < k ? ld_cg(prg + j) : mk(0.0, 0.0);
+      if (j < k) pv[j] = pvr[q];
+    }
+    const zd piv = ld_cg(prg + kk);
+    const zd inv = gj_recip(piv);
+    const int lp = p - r0;   // local index of the pivot row (in range only in its owner)
+    if (t < nr) ms[t] = gj_mul(xs[(int64_t)t * k + kk], inv);
+    if (t == 0) {
+      prow[kk] = p;
+      if (lp >= 0 && lp < nr) used_s[lp] = 1;
+      if (b == 0) {
+        const double am = sqrt(gj_nrm(piv));
+        if (!(am > 0.0) || !isfinite(am)) atomicOr(err, ERRB_SINGULAR);
+        ld += log(am);
+      }
+    }
+    __syncthreads();
+    int skip = -1;
+    if (kk + 1 < k) {
+      // rank this block's candidates for column kk+1 by their updated entries
+      if (t < 32) {
+        unsigned long long kb = 0ull;
+        if (t < nr && !used_s[t]) {
+          zd v = xs[(int64_t)t * k + kk + 1];
+          cmsub(v, ms[t], pv[kk + 1]);
+          const double nrm = gj_nrm(v);
+          if (!(nrm >= 0.0)) atomicOr(err, ERRB_SINGULAR);
+          else kb = gj_key(nrm, r0 + t);
+        }
+        kb = warp_max_u64(kb);
+        if (t == 0) best_s = kb;
+      }
+      __syncthreads();
+      const unsigned long long bk = best_s;
+      if (bk) {
+        // update and publish the best candidate first
+        skip = 4095 - (int)(bk & 4095ull) - r0;
+        const zd m = ms[skip];
+        zd* out = ((kk & 1) ? pub0 : pub1) + (int64_t)b * k;
+        zd* row = xs + (int64_t)skip * k;
+#pragma unroll
+        for (int q = 0; q < JPT; ++q) {
+          const int j = t + q * GJP_THREADS;
+          if (j < k) {
+            zd v;
+            if (j == kk) {
+              v = mk(-m.re, -m.im);
+            } else {
+              v = row[j];
+              cmsub(v, m, pvr[q]);
+            }
+            row[j] = v;
+            out[j] = v;
+          }
+        }
+      }
+      __syncthreads();
+      if (t == 0) {
+        if (bk) atomicMax(keys + kk + 1, bk);
+        __threadfence();
+        atomicAdd(ctr, 1u);
+      }
+    }
+    // the rest of the block's rows: X[i][j] -= m_i X[p][j] ...
+    for (int r = 0; r < nr; ++r) {
+      if (r == skip || r == lp) continue;
+      const zd m = ms[r];
+      zd* row = xs + (int64_t)r * k;
+#pragma unroll
+      for (int q = 0; q < JPT; ++q) {
+        const int j = t + q * GJP_THREADS;
+        if (j < k) {
+          zd v = row[j];
+          cmsub(v, m, pvr[q]);
+          row[j] = v;
+        }
+      }
+    }
+    // ... except column kk, which receives -m_i (same thread: after its own write) ...
+    if (t == kk % GJP_THREADS) {
+      for (int r = 0; r < nr; ++r) {
+        if (r == skip || r == lp) continue;
+        const zd m = ms[r];
+        xs[(int64_t)r * k + kk] = mk(-m.re, -m.im);
+      }
+    }
+    // ... and the pivot row, which is normalised
+    if (lp >= 0 && lp < nr) {
+      zd* row = xs + (int64_t)lp * k;
+#pragma unroll
+      for (int q = 0; q < JPT; ++q) {
+        const int j = t + q * GJP_THREADS;
+        if (j < k) row[j] = (j == kk) ? inv : gj_mul(pvr[q], inv);
+      }
+    }
+    __syncthreads();
+  }
+  // inv(A)[i][j] = X[p_i][q_j] with q = p^{-1}: this block's row g goes to row q_g
+  for (int c = t; c < k; c += GJP_THREADS) qs[prow[c]] = c;
+  __syncthreads();
+  for (int r = 0; r < nr; ++r) {
+    zd* dst = ainv + (int64_t)qs[r0 + r] * k;
+    const zd* src = xs + (int64_t)r * k;
+    for (int j = t; j < k; j += GJP_THREADS) dst[j] = src[qs[j]];
+  }
+  if (b == 0) {
+    for (int c = t; c < k; c += GJP_THREADS) ipiv[c] = prow[c];
+    if (t == 0) *logdet = ld;
+  }
+}
+
+// Self-test of the bounded wait: block 0 waits (limit_ns) on a counter that
+// nothing increments and gives up; block 1, with a 100x longer limit, must
+// leave through block 0's ERRB_TIMEOUT.  how[b] = 1 when block b gave up.
+__global__ void k_wait_probe(const unsigned* ctr, int* err, int* how, unsigned long long limit_ns) {
+  if (threadIdx.x != 0) return;
+  const bool ok = wait_count(ctr, 1u, err, blockIdx.x == 0 ? limit_ns : 100ull * limit_ns);
+  how[blockIdx.x] = ok ? 0 : 1;
+}
+void dense_wait_probe(unsigned* ctr, int* err, int* how, unsigned long long limit_ns, cudaStream_t st) {
+  k_wait_probe<<<2, 32, 0, st>>>(ctr, err, how, limit_ns);
+}
+
+// Launch shape of the persistent form for (k, nb), or false where it does not
+// fit: rows per block R <= 32, the block's rows in shared memory, and all
+// nb * bp blocks resident at once (a cooperative launch checks this too).
+typedef void (*GjpKernel)(const zd*, zd*, int, int, int, zd*, zd*, unsigned long long*, unsigned*, int*, double*, int,
+                          int*, const int*, unsigned long long);
+static GjpKernel gjp_kernel(int k) {
+  if (k <= 2 * GJP_THREADS) return k_gj_persist<2>;
+  if (k <= 4 * GJP_THREADS) return k_gj_persist<4>;
+  if (k <= 6 * GJP_THREADS) return k_gj_persist<6>;
+  return nullptr;
+}
+
+static bool gjp_shape(int k, int nb, int* R_out, int* bp_out, size_t* smem_out) {
+  int dev = 0, nsm = 0, smem_optin = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return false;
+  }
+  const GjpKernel kern = gjp_kernel(k);
+  if (nsm <= 0 || k < 2 || !kern || nb < 1) return false;
+  const int per = std::max(1, nsm / nb);
+  const int R = (k + per - 1) / per;
+  if (R > GJP_RMAX) return false;
+  const int bp = (k + R - 1) / R;
+  const size_t smem = ((size_t)R * k + k) * sizeof(zd) + 2 * (size_t)k * sizeof(int);
+  if (smem + 2048 > (size_t)smem_optin) return false;
+  // one value for every caller (worker threads may race here)
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - 2048) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, GJP_THREADS, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if ((int64_t)per_sm * nsm < (int64_t)bp * nb) return false;
+  *R_out = R;
+  *bp_out = bp;
+  *smem_out = smem;
+  return true;
+}
+
+static bool gj_persist_launch(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const int* act, int* ipiv,
+                              int* used, unsigned long long* keys, double* logdet, int ld_stride, int* err,
+                              cudaStream_t st) {
+  int R = 0, bp = 0;
+  size_t smem = 0;
+  if (!gjp_shape(k, nb, &R, &bp, &smem)) return false;
+  // the arrival counters live in the (otherwise unused) row-flag array
+  unsigned* ctr = reinterpret_cast<unsigned*>(used);
+  if (cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)(k + 1) * nb, st) != cudaSuccess ||
+      cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (size_t)nb, st) != cudaSuccess)
+    return false;
+  unsigned long long limit = GJP_WAIT_NS;
+  void* args[] = {(void*)&a, (void*)&ainv, (void*)&k, (void*)&R, (void*)&bp, (void*)&w0, (void*)&w1,
+                  (void*)&keys, (void*)&ctr, (void*)&ipiv, (void*)&logdet, (void*)&ld_stride, (void*)&err,
+                  (void*)&act, (void*)&limit};
+  if (cudaLaunchCooperativeKernel((const void*)gjp_kernel(k), dim3(bp, nb), dim3(GJP_THREADS), args, smem, st) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 // The k + 4 launches of one inversion are captured once per (k, buffers) as a
 // CUDA graph and replayed on the caller's stream: the steps are short, so the
 // per-launch overhead of k back-to-back launches is a large part of their time.
@@ -280,8 +611,10 @@ std::mutex g_gj_mutex;
 std::vector<GjGraph> g_gj_graphs;
 }  // namespace
 
-void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const int* act, int* ipiv, int* used,
-                   unsigned long long* keys, double* logdet, int ld_stride, int* err, cudaStream_t st) {
+int dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const int* act, int* ipiv, int* used,
+                  unsigned long long* keys, double* logdet, int ld_stride, int* err, int mode, cudaStream_t st) {
+  if (mode != GJ_STEPS && gj_persist_launch(a, ainv, w0, w1, k, nb, act, ipiv, used, keys, logdet, ld_stride, err, st))
+    return 1;
   const void* ptrs[11] = {a, ainv, w0, w1, ipiv, used, keys, logdet, err, act, nullptr};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -289,7 +622,7 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const i
   for (const GjGraph& g : g_gj_graphs) {
     if (g.k == k && g.nb == nb && g.ld_stride == ld_stride && g.dev == dev && std::equal(ptrs, ptrs + 11, g.ptrs)) {
       cudaGraphLaunch(g.exec, st);
-      return;
+      return k + 3;
     }
   }
   cudaStream_t cap = nullptr;
@@ -307,7 +640,7 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const i
   if (!ok) {   // capture unavailable: launch directly
     cudaGetLastError();
     gj_launch_all(a, ainv, w0, w1, k, nb, act, ipiv, used, keys, logdet, ld_stride, err, st);
-    return;
+    return k + 3;
   }
   if (g_gj_graphs.size() >= 64) {
     cudaGraphExecDestroy(g_gj_graphs.front().exec);
@@ -322,6 +655,7 @@ void dense_inverse(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const i
   g.exec = exec;
   g_gj_graphs.push_back(g);
   cudaGraphLaunch(exec, st);
+  return k + 3;
 }
 
 // ---------------------------------------------------------------------------

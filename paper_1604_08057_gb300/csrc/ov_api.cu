@@ -357,6 +357,18 @@ struct NewtonRecord {
 };
 constexpr int NREC = 48;
 
+// status of the k x k stage from its device error word: a device-side wait that
+// ran past its limit, an ill-posed sign (singular or non-finite), or success
+int sign_status(ov_context* c, const int* derr) {
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return (herr & ERRB_TIMEOUT) ? OV_ERR_TIMEOUT : herr ? OV_ERR_SIGN_ILLPOSED : OV_OK;
+}
+int sign_failed(ov_context* c, const int* derr) {
+  return sign_status(c, derr) == OV_ERR_TIMEOUT ? OV_ERR_TIMEOUT : OV_ERR_SIGN_ILLPOSED;
+}
+
 int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, NewtonRecord* rec = nullptr) {
   const int64_t n = (int64_t)k * k;
   zd* ai = wsT<zd>(c, B_XI, n);
@@ -376,8 +388,9 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
   double hs[3];
   for (it = 1; it <= 100; ++it) {
     CK(cudaMemsetAsync(dstat, 0, 3 * sizeof(double), c->st));
-    run(c, OV_KIND_DENSE, (int64_t)k + 3, [&] {
-      dense_inverse(a[cur], ai, w0, w1, k, 1, nullptr, ipiv, used, keys, dstat + 2, 0, err_dev, c->st);
+    run(c, OV_KIND_DENSE, 0, [&] {
+      c->launches += dense_inverse(a[cur], ai, w0, w1, k, 1, nullptr, ipiv, used, keys, dstat + 2, 0, err_dev,
+                                   c->opt.dense, c->st);
     });
     if (rec) {
       const int slot = it - 1;
@@ -452,8 +465,9 @@ int newton_batch(ov_context* c, zd* a[2], int k, int nb, int* err_dev, std::vect
     CK(cudaMemcpyAsync(act_dev, act.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(scal_dev, scaling.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemsetAsync(dstat, 0, sizeof(double) * 4 * nb, c->st));
-    run(c, OV_KIND_DENSE, (int64_t)k + 3, [&] {
-      dense_inverse(a[cur], ai, w0, w1, k, nb, act_dev, ipiv, used, keys, dstat + 2, 4, err_dev, c->st);
+    run(c, OV_KIND_DENSE, 0, [&] {
+      c->launches += dense_inverse(a[cur], ai, w0, w1, k, nb, act_dev, ipiv, used, keys, dstat + 2, 4, err_dev,
+                                   c->opt.dense, c->st);
     });
     if (rec_inv) {
       const int slot = it - 1;
@@ -515,15 +529,15 @@ int sign_all(ov_context* c, Lat<R>& L, const std::vector<SrcScal>& hsc, zd* y, i
     });
   std::vector<int> which, its;
   const int itmax = newton_batch(c, a, k, nsrc, derr, which, its);
-  if (itmax < 0) return OV_ERR_SIGN_ILLPOSED;
+  if (itmax < 0) return sign_failed(c, derr);
   for (int src = 0; src < nsrc; ++src)
     run(c, OV_KIND_DENSE, 1, [&] {
       dense_extract_y(a[which[src]] + src * n, hsc[src].beta0, k, y + (int64_t)src * k, c->st);
     });
-  int herr = 0;
-  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
-  if (herr) return OV_ERR_SIGN_ILLPOSED;
+  {
+    const int ss = sign_status(c, derr);
+    if (ss != OV_OK) return ss;
+  }
   if (iters) *iters = itmax;
   return OV_OK;
 }
@@ -772,16 +786,16 @@ int vjp_forward(ov_context* c, const int32_t dims[4], const void* U, double mu, 
     });
   std::vector<int> which;
   F.iters_max = newton_batch(c, a, k, nsrc, derr, which, F.iters, F.rec_inv, F.rec_ld, NREC, &F.scaling, &F.rec_ok);
-  if (F.iters_max < 0) return OV_ERR_SIGN_ILLPOSED;
+  if (F.iters_max < 0) return sign_failed(c, derr);
   for (int src = 0; src < nsrc; ++src)
     run(c, OV_KIND_DENSE, 2, [&] {
       dense_copy(a[which[src]] + src * n, F.fsign + (int64_t)src * n, n, c->st);
       dense_extract_y(a[which[src]] + src * n, F.hsc[src].beta0, k, F.y + (int64_t)src * k, c->st);
     });
-  int herr = 0;
-  CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
-  if (herr) return OV_ERR_SIGN_ILLPOSED;
+  {
+    const int ss = sign_status(c, derr);
+    if (ss != OV_OK) return ss;
+  }
   CK(cudaEventRecord(c->ev[2], c->st));
   if (info) {
     info->newton_iters = F.iters_max;
@@ -937,7 +951,7 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
       for (int src = 0; src < nsrc; ++src) {
         if (!act[src]) continue;
         const double step = std::sqrt(hs[4 * src] / hs[4 * src + 1]);
-        if (!std::isfinite(step)) return OV_ERR_SIGN_ILLPOSED;
+        if (!std::isfinite(step)) return sign_failed(c, derr);
         extra[src] = x;
         cur[src] = 1 - ce;
         if (step <= 1e-14 || step >= 0.5 * prev[src]) act[src] = 0;
@@ -966,7 +980,7 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
       });
       int wb = 0;
       const int itb = newton(c, a, eb, k, derr, &wb);
-      if (itb < 0) return OV_ERR_SIGN_ILLPOSED;
+      if (itb < 0) return sign_failed(c, derr);
       if (itb > iters_adj) iters_adj = itb;
       run(c, OV_KIND_DENSE, 1, [&] {
         dense_extract_tri(eb[wb], k, gaT + (int64_t)src * k, gbT + (int64_t)src * k, gdT + (int64_t)src * k,
@@ -975,10 +989,8 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
     }
   }
   {
-    int herr = 0;
-    CK(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    if (herr) return OV_ERR_SIGN_ILLPOSED;
+    const int ss = sign_status(c, derr);
+    if (ss != OV_OK) return ss;
   }
   CK(cudaEventRecord(c->ev[3], c->st));
   // (with segments, x is accumulated while the reverse sweep replays each segment)
@@ -1177,7 +1189,7 @@ int guarded(F&& f) {
 
 bool valid_options(const ov_options* o) {
   return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4 &&
-         o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0);
+         o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0) && (o->dense == 0 || o->dense == 1);
 }
 
 // x = V_k y from a forward state (a second pass over the segments if there are any)
@@ -1310,6 +1322,26 @@ int ov_profile_read(ov_context* c, int32_t kind, int64_t* launches, double* ms, 
 }
 
 int64_t ov_launch_count(ov_context* c) { return c ? c->launches : -1; }
+
+int ov_selftest_wait(ov_context* c, uint64_t limit_ns, double* elapsed_ms) {
+  if (!c || !elapsed_ms || limit_ns == 0 || limit_ns > 100000000ull) return OV_ERR_INVALID_ARG;
+  return guarded([&] {
+    int* w = wsT<int>(c, B_DERR, 4);
+    CK(cudaMemsetAsync(w, 0, 4 * sizeof(int), c->st));
+    CK(cudaEventRecord(c->ev[0], c->st));
+    dense_wait_probe(reinterpret_cast<unsigned*>(w), w + 1, w + 2, limit_ns, c->st);
+    launch_check();
+    c->launches += 1;
+    CK(cudaEventRecord(c->ev[1], c->st));
+    int h[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(h, w, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    *elapsed_ms = elapsed(c->ev[0], c->ev[1]);
+    // both blocks must have given up, the second through the first one's flag
+    if (h[0] != 0 || !(h[1] & ERRB_TIMEOUT) || h[2] != 1 || h[3] != 1) return OV_ERR_CUDA;
+    return OV_ERR_TIMEOUT;
+  });
+}
 
 int ov_context_set_options(ov_context* c, const ov_options* opt) {
   if (!c || !opt || !valid_options(opt)) return OV_ERR_INVALID_ARG;
@@ -1581,6 +1613,7 @@ const char* ov_strerror(int s) {
     case OV_ERR_CUDA: return "CUDA runtime error";
     case OV_ERR_NONFINITE: return "non-finite recurrence coefficient";
     case OV_ERR_SCRATCH_LIMIT: return "problem too large for the fixed 32 MiB scratch of ov_apply_H_noalloc";
+    case OV_ERR_TIMEOUT: return "a device-side wait ran past its time limit";
     default: return "unknown status";
   }
 }

@@ -503,3 +503,37 @@ def test_profile_select_times_only_selected_kinds():
         else:
             assert sel[kd] == (0, 0.0)
     assert sum(v[0] for v in all_kinds.values()) > sel["stencil_pair"][0] + sel["proj_dots"][0]
+
+
+@pytest.mark.parametrize("dims,nsrc,k", [((4, 4, 4, 4), 1, 200), ((4, 4, 4, 4), 4, 120), ((4, 4, 4, 4), 1, 700),
+                                         ((4, 4, 4, 4), 1, 1100), ((2, 2, 2, 2), 1, 37)])
+def test_dense_modes_identical(dims, nsrc, k):
+    """The cooperative k x k inversion and the per-step form give bitwise equal results (sign and VJP)."""
+    u, b, xbar = case(dims, 0.3, 21, nsrc)
+    ut, bt, xt = (torch.tensor(a, device=DEV) for a in (u, b, xbar))
+    out = {}
+    for mode in (1, 0):
+        binding.dense_mode(mode, "fp64", 1, 2)
+        try:
+            x, info = binding.tsl_sign(ut, 0.3, -2.0, bt, k, "fp64", 1, 2, return_info=True)
+            du, dmu, _ = binding.tsl_sign_vjp(ut, 0.3, -2.0, bt, k, xt, "fp64", 1, 2)
+        finally:
+            binding.dense_mode(0, "fp64", 1, 2)
+        out[mode] = (x, info["newton_iters"], du, dmu)
+    dx = float((out[0][0] - out[1][0]).abs().max() / out[1][0].abs().max())
+    ddu = float((out[0][2] - out[1][2]).abs().max() / out[1][2].abs().max())
+    assert torch.equal(out[0][0], out[1][0]), f"x differs by {dx:.3e} (iters {out[0][1]} vs {out[1][1]})"
+    assert out[0][1] == out[1][1]
+    assert torch.equal(out[0][2], out[1][2]), f"dU differs by {ddu:.3e}"
+    assert out[0][3] == out[1][3]
+
+
+def test_bounded_wait_gives_up():
+    """The inter-block wait of the cooperative inversion returns an error status when nothing arrives."""
+    status, ms = binding.selftest_wait(1_000_000)
+    assert status == -8
+    assert 0.5 < ms < 50.0
+    # the context is still usable afterwards
+    u, b, _ = case((2, 2, 2, 2), 0.3, 3)
+    x = binding.tsl_sign(torch.tensor(u, device=DEV), 0.3, -2.0, torch.tensor(b, device=DEV), 20, "fp64", 1, 2)
+    assert torch.isfinite(torch.view_as_real(x)).all()
