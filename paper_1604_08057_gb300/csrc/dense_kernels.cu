@@ -284,15 +284,18 @@ static void gj_launch_all(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, 
 // Problem p owns blocks (0..bp-1, p); block b keeps rows [b*R, b*R + R) of its
 // matrix in shared memory for all k steps, so the matrix is read once and the
 // inverse written once.  Step kk needs the pivot row p_kk as it stood after
-// step kk-1; every block therefore publishes, at the end of each step, its own
-// best candidate row for the next column (fully updated, to a double-buffered
-// slot in global memory) and offers its key by atomicMax.  One barrier per
-// step separates the offers from their use; the candidate row is updated and
-// published before the bulk of the block's rows, so the barrier's latency is
-// hidden behind that update.  The arithmetic of every entry, the pivot keys
-// and the order of the log|det| sum are those of k_gj_step, so both forms give
-// identical results.  Waits are bounded by a time limit: a block that runs out
-// sets ERRB_TIMEOUT, and every block of every problem leaves at its next wait.
+// step kk-1; every block therefore publishes, during step kk-1, its own best
+// candidate row for column kk (fully updated, to a double-buffered row slot in
+// global memory), then its key (plus one; 1 = no candidate) to its own word of
+// step kk's key slots with a release store.  A block's wait for step kk is a
+// warp reading all bp key words of the step until none is zero; their maximum
+// is the pivot, so the wait and the pivot search are one round of loads.  The
+// candidate row is updated and published before the bulk of the block's rows,
+// so the other blocks' progress overlaps that update.  The arithmetic of every
+// entry, the pivot keys and the order of the log|det| sum are those of
+// k_gj_step, so both forms give identical results.  Waits are bounded by a
+// time limit: a warp that runs out sets ERRB_TIMEOUT, and every block of
+// every problem leaves at its next wait.
 // ---------------------------------------------------------------------------
 constexpr int GJP_THREADS = 256;
 constexpr int GJP_RMAX = 32;                       // rows per block (one warp ranks them)
@@ -303,22 +306,13 @@ __device__ __forceinline__ unsigned long long gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-// wait until *ctr >= target; false when another block gave up or the limit passed
-__device__ bool wait_count(const unsigned* ctr, unsigned target, int* err, unsigned long long limit_ns) {
-  const unsigned long long t0 = gtimer();
-  for (unsigned spin = 0;; ++spin) {
-    if (ld_acquire(ctr) >= target) return true;
-    if (*(volatile int*)err & ERRB_TIMEOUT) return false;
-    if ((spin & 255u) == 255u && (gtimer() - t0 > limit_ns || spin > (1u << 23))) {
-      atomicOr(err, ERRB_TIMEOUT);
-      return false;
-    }
-  }
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
@@ -328,24 +322,53 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   }
   return v;
 }
+// One full warp waits until the n words at slots are all non-zero and returns
+// their maximum (in every lane), or 0 when another block gave up or the limit
+// passed (then ERRB_TIMEOUT is set).
+__device__ unsigned long long warp_wait_slots(const unsigned long long* slots, int n, int* err,
+                                              unsigned long long limit_ns) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long t0 = gtimer();
+  for (unsigned spin = 0;; ++spin) {
+    bool all = true;
+    unsigned long long m = 0ull;
+    for (int q = lane; q < n; q += 32) {
+      const unsigned long long v = ld_acquire_u64(slots + q);
+      all = all && v != 0ull;
+      m = v > m ? v : m;
+    }
+    if (__all_sync(0xffffffffu, all)) return warp_max_u64(m);
+    if ((spin & 63u) == 63u) {
+      int stop = 0;
+      if (lane == 0) {
+        if (*(volatile int*)err & ERRB_TIMEOUT) {
+          stop = 1;
+        } else if (gtimer() - t0 > limit_ns || spin > (1u << 22)) {
+          atomicOr(err, ERRB_TIMEOUT);
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, stop, 0)) return 0ull;
+    }
+  }
+}
 
 // JPT: columns per thread (k <= JPT * GJP_THREADS); the pivot row's entries of
 // the thread's columns are held in registers for the bulk update.
 template <int JPT>
 __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict__ a, zd* __restrict__ ainv, int k,
                                                           int R, int bp, zd* pub0, zd* pub1,
-                                                          unsigned long long* keys, unsigned* ctr, int* ipiv,
-                                                          double* logdet, int ld_stride, int* err,
-                                                          const int* __restrict__ act, unsigned long long limit_ns) {
-  extern __shared__ double4 gjp_smem[];
+                                                          unsigned long long* slots, int* ipiv, double* logdet,
+                                                          int ld_stride, int* err, const int* __restrict__ act,
+                                                          unsigned long long limit_ns) {
+  extern __shared__ double2 gjp_smem[];
   zd* xs = reinterpret_cast<zd*>(gjp_smem);   // R rows x k
   zd* pv = xs + (int64_t)R * k;               // the step's pivot row as it stood before the step
   int* prow = reinterpret_cast<int*>(pv + k); // pivot row of each step
   int* qs = prow + k;                         // inverse permutation (at the end)
   __shared__ zd ms[GJP_RMAX];                 // row factors X[i][kk] / pivot
   __shared__ int used_s[GJP_RMAX];
-  __shared__ unsigned long long best_s;
-  __shared__ int ok_s;
+  __shared__ unsigned long long best_s, key_s;
   const int pb = blockIdx.y;
   if (act && !act[pb]) return;
   const int b = blockIdx.x, t = threadIdx.x;
@@ -353,8 +376,7 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
   const int64_t n = (int64_t)k * k;
   a += pb * n;
   ainv += pb * n;
-  keys += (int64_t)pb * (k + 1);
-  ctr += pb;
+  slots += (int64_t)pb * (k + 1) * GJ_KEY_SLOTS;
   ipiv += (int64_t)pb * k;
   logdet += (int64_t)pb * ld_stride;
   pub0 += (int64_t)pb * bp * k;
@@ -382,22 +404,19 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
     for (int j = t; j < k; j += GJP_THREADS) pub0[(int64_t)b * k + j] = xs[(int64_t)lr * k + j];
   }
   __syncthreads();
-  if (t == 0) {
-    if (best_s) atomicMax(keys, best_s);
-    __threadfence();
-    atomicAdd(ctr, 1u);
-  }
+  if (t == 0) st_release_u64(slots + b, best_s + 1ull);
 
   for (int kk = 0; kk < k; ++kk) {
-    if (t == 0) {
-      ok_s = wait_count(ctr, (unsigned)bp * (unsigned)(kk + 1), err, limit_ns) ? 1 : 0;
-      __threadfence();
+    if (t < 32) {
+      const unsigned long long mx = warp_wait_slots(slots + (int64_t)kk * GJ_KEY_SLOTS, bp, err, limit_ns);
+      if (t == 0) key_s = mx;
     }
     __syncthreads();
-    if (!ok_s) return;
-    const unsigned long long key = __ldcg(keys + kk);
+    const unsigned long long mx = key_s;
+    if (mx == 0ull) return;                   // a wait gave up: every block leaves
+    const unsigned long long key = mx - 1ull;
     const int p = 4095 - (int)(key & 4095ull);
-    if (key == 0ull || p < 0 || p >= k) {   // every block sees the same key and leaves
+    if (key == 0ull || p < 0 || p >= k) {     // every block sees the same key and leaves
       if (b == 0 && t == 0) atomicOr(err, ERRB_SINGULAR);
       return;
     }
@@ -463,11 +482,7 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
         }
       }
       __syncthreads();
-      if (t == 0) {
-        if (bk) atomicMax(keys + kk + 1, bk);
-        __threadfence();
-        atomicAdd(ctr, 1u);
-      }
+      if (t == 0) st_release_u64(slots + (int64_t)(kk + 1) * GJ_KEY_SLOTS + b, bk + 1ull);
     }
     // the rest of the block's rows: X[i][j] -= m_i X[p][j] ...
     for (int r = 0; r < nr; ++r) {
@@ -517,23 +532,22 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
   }
 }
 
-// Self-test of the bounded wait: block 0 waits (limit_ns) on a counter that
-// nothing increments and gives up; block 1, with a 100x longer limit, must
+// Self-test of the bounded wait: block 0's warp waits (limit_ns) on a key word
+// that nothing writes and gives up; block 1's, with a 100x longer limit, must
 // leave through block 0's ERRB_TIMEOUT.  how[b] = 1 when block b gave up.
-__global__ void k_wait_probe(const unsigned* ctr, int* err, int* how, unsigned long long limit_ns) {
-  if (threadIdx.x != 0) return;
-  const bool ok = wait_count(ctr, 1u, err, blockIdx.x == 0 ? limit_ns : 100ull * limit_ns);
-  how[blockIdx.x] = ok ? 0 : 1;
+__global__ void k_wait_probe(const unsigned long long* slot, int* err, int* how, unsigned long long limit_ns) {
+  const unsigned long long mx = warp_wait_slots(slot, 1, err, blockIdx.x == 0 ? limit_ns : 100ull * limit_ns);
+  if (threadIdx.x == 0) how[blockIdx.x] = mx == 0ull ? 1 : 0;
 }
-void dense_wait_probe(unsigned* ctr, int* err, int* how, unsigned long long limit_ns, cudaStream_t st) {
-  k_wait_probe<<<2, 32, 0, st>>>(ctr, err, how, limit_ns);
+void dense_wait_probe(unsigned long long* slot, int* err, int* how, unsigned long long limit_ns, cudaStream_t st) {
+  k_wait_probe<<<2, 32, 0, st>>>(slot, err, how, limit_ns);
 }
 
 // Launch shape of the persistent form for (k, nb), or false where it does not
 // fit: rows per block R <= 32, the block's rows in shared memory, and all
 // nb * bp blocks resident at once (a cooperative launch checks this too).
-typedef void (*GjpKernel)(const zd*, zd*, int, int, int, zd*, zd*, unsigned long long*, unsigned*, int*, double*, int,
-                          int*, const int*, unsigned long long);
+typedef void (*GjpKernel)(const zd*, zd*, int, int, int, zd*, zd*, unsigned long long*, int*, double*, int, int*,
+                          const int*, unsigned long long);
 static GjpKernel gjp_kernel(int k) {
   if (k <= 2 * GJP_THREADS) return k_gj_persist<2>;
   if (k <= 4 * GJP_THREADS) return k_gj_persist<4>;
@@ -556,6 +570,7 @@ static bool gjp_shape(int k, int nb, int* R_out, int* bp_out, size_t* smem_out) 
   const int R = (k + per - 1) / per;
   if (R > GJP_RMAX) return false;
   const int bp = (k + R - 1) / R;
+  if (bp > GJ_KEY_SLOTS) return false;
   const size_t smem = ((size_t)R * k + k) * sizeof(zd) + 2 * (size_t)k * sizeof(int);
   if (smem + 2048 > (size_t)smem_optin) return false;
   // one value for every caller (worker threads may race here)
@@ -575,26 +590,55 @@ static bool gjp_shape(int k, int nb, int* R_out, int* bp_out, size_t* smem_out) 
   return true;
 }
 
+// Cooperative inversions issued from different streams (the worker contexts of
+// a batch) are chained through one event per device, so that no two of them
+// are ever partly resident at once, each waiting for blocks that the other
+// holds the room for.
+namespace {
+struct CoopChain {
+  int dev;
+  cudaEvent_t ev;
+};
+std::mutex g_coop_mutex;
+std::vector<CoopChain> g_coop;
+}  // namespace
+
 static bool gj_persist_launch(const zd* a, zd* ainv, zd* w0, zd* w1, int k, int nb, const int* act, int* ipiv,
                               int* used, unsigned long long* keys, double* logdet, int ld_stride, int* err,
                               cudaStream_t st) {
   int R = 0, bp = 0;
   size_t smem = 0;
   if (!gjp_shape(k, nb, &R, &bp, &smem)) return false;
-  // the arrival counters live in the (otherwise unused) row-flag array
-  unsigned* ctr = reinterpret_cast<unsigned*>(used);
-  if (cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)(k + 1) * nb, st) != cudaSuccess ||
-      cudaMemsetAsync(ctr, 0, sizeof(unsigned) * (size_t)nb, st) != cudaSuccess)
+  // the key slots: (k + 1) steps x GJ_KEY_SLOTS words per problem, all zero at the start
+  if (cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)(k + 1) * GJ_KEY_SLOTS * nb, st) != cudaSuccess)
     return false;
   unsigned long long limit = GJP_WAIT_NS;
-  void* args[] = {(void*)&a, (void*)&ainv, (void*)&k, (void*)&R, (void*)&bp, (void*)&w0, (void*)&w1,
-                  (void*)&keys, (void*)&ctr, (void*)&ipiv, (void*)&logdet, (void*)&ld_stride, (void*)&err,
-                  (void*)&act, (void*)&limit};
+  void* args[] = {(void*)&a,      (void*)&ainv, (void*)&k,         (void*)&R,   (void*)&bp,
+                  (void*)&w0,     (void*)&w1,   (void*)&keys,      (void*)&ipiv, (void*)&logdet,
+                  (void*)&ld_stride, (void*)&err, (void*)&act, (void*)&limit};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(g_coop_mutex);
+  cudaEvent_t ev = nullptr;
+  for (const CoopChain& c : g_coop)
+    if (c.dev == dev) ev = c.ev;
+  if (!ev) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    g_coop.push_back({dev, ev});
+  }
+  if (cudaStreamWaitEvent(st, ev, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   if (cudaLaunchCooperativeKernel((const void*)gjp_kernel(k), dim3(bp, nb), dim3(GJP_THREADS), args, smem, st) !=
       cudaSuccess) {
     cudaGetLastError();
     return false;
   }
+  cudaEventRecord(ev, st);
   return true;
 }
 

@@ -143,16 +143,17 @@ void dense_copy_batch(const zd* A, int64_t sA, zd* B, int64_t sB, int64_t n, int
                       cudaStream_t st);
 // Ainv = A^{-1} by Gauss-Jordan with partial pivoting for nb problems (matrices
 // at stride k*k; A is not modified; w0, w1 work matrices; ipiv, used: k ints and
-// keys: k + 1 words per problem); logdet[p * ld_stride] += log|det A_p|.
+// keys: (k + 1) * GJ_KEY_SLOTS words per problem); logdet[p * ld_stride] += log|det A_p|.
 // mode GJ_AUTO: one cooperative launch per inversion where the rows fit in
 // shared memory, else (and with GJ_STEPS) one launch per elimination step,
 // replayed as a CUDA graph.  Both give identical results.  Returns the number
 // of kernels launched.
 enum : int { GJ_AUTO = 0, GJ_STEPS = 1 };
+constexpr int GJ_KEY_SLOTS = 160;   // pivot-key words per step and problem (>= blocks per problem)
 int dense_inverse(const zd* A, zd* Ainv, zd* w0, zd* w1, int k, int nb, const int* act, int* ipiv, int* used,
                   unsigned long long* keys, double* logdet, int ld_stride, int* err, int mode, cudaStream_t st);
 // the bounded inter-block wait of the cooperative inversion, made to run out
-void dense_wait_probe(unsigned* ctr, int* err, int* how, unsigned long long limit_ns, cudaStream_t st);
+void dense_wait_probe(unsigned long long* slot, int* err, int* how, unsigned long long limit_ns, cudaStream_t st);
 void dense_gemm(const zd* A, const zd* B, zd* C, int k, cudaStream_t st);   // C = A B
 // C = op(A) op(B), op = conjugate transpose when the flag is set
 void dense_gemm_op(const zd* A, int hA, const zd* B, int hB, zd* C, int k, cudaStream_t st);

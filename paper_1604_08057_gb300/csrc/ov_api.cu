@@ -376,7 +376,7 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
   zd* t2 = e ? wsT<zd>(c, B_TMP2, n) : nullptr;
   int* ipiv = wsT<int>(c, B_IPIV, k);
   int* used = wsT<int>(c, B_COL, k);
-  unsigned long long* keys = wsT<unsigned long long>(c, B_PROW, k + 1);
+  unsigned long long* keys = wsT<unsigned long long>(c, B_PROW, (int64_t)(k + 1) * GJ_KEY_SLOTS);
   zd* w0 = wsT<zd>(c, B_W0, n);
   zd* w1 = wsT<zd>(c, B_W1, n);
   double* dstat = wsT<double>(c, B_DSTAT, 4);   // [0] diff^2, [1] norm^2, [2] log|det|
@@ -447,7 +447,7 @@ int newton_batch(ov_context* c, zd* a[2], int k, int nb, int* err_dev, std::vect
   zd* w1 = wsT<zd>(c, B_W1, nb * n);
   int* ipiv = wsT<int>(c, B_IPIV, (int64_t)nb * k);
   int* used = wsT<int>(c, B_COL, (int64_t)nb * k);
-  unsigned long long* keys = wsT<unsigned long long>(c, B_PROW, (int64_t)nb * (k + 1));
+  unsigned long long* keys = wsT<unsigned long long>(c, B_PROW, (int64_t)nb * (k + 1) * GJ_KEY_SLOTS);
   double* dstat = wsT<double>(c, B_DSTAT, 4 * (int64_t)nb);
   zd* dpart = wsT<zd>(c, B_DPART, nb * pstride);
   unsigned* dcnt = wsT<unsigned>(c, B_DCNT, 4 * (int64_t)nb);
@@ -1326,19 +1326,20 @@ int64_t ov_launch_count(ov_context* c) { return c ? c->launches : -1; }
 int ov_selftest_wait(ov_context* c, uint64_t limit_ns, double* elapsed_ms) {
   if (!c || !elapsed_ms || limit_ns == 0 || limit_ns > 100000000ull) return OV_ERR_INVALID_ARG;
   return guarded([&] {
-    int* w = wsT<int>(c, B_DERR, 4);
-    CK(cudaMemsetAsync(w, 0, 4 * sizeof(int), c->st));
+    // [0, 1]: the key word nothing writes, [2]: error word, [3], [4]: how each block left
+    int* w = wsT<int>(c, B_DERR, 8);
+    CK(cudaMemsetAsync(w, 0, 8 * sizeof(int), c->st));
     CK(cudaEventRecord(c->ev[0], c->st));
-    dense_wait_probe(reinterpret_cast<unsigned*>(w), w + 1, w + 2, limit_ns, c->st);
+    dense_wait_probe(reinterpret_cast<unsigned long long*>(w), w + 2, w + 3, limit_ns, c->st);
     launch_check();
     c->launches += 1;
     CK(cudaEventRecord(c->ev[1], c->st));
-    int h[4] = {0, 0, 0, 0};
+    int h[8] = {};
     CK(cudaMemcpyAsync(h, w, sizeof(h), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     *elapsed_ms = elapsed(c->ev[0], c->ev[1]);
     // both blocks must have given up, the second through the first one's flag
-    if (h[0] != 0 || !(h[1] & ERRB_TIMEOUT) || h[2] != 1 || h[3] != 1) return OV_ERR_CUDA;
+    if (h[0] != 0 || h[1] != 0 || !(h[2] & ERRB_TIMEOUT) || h[3] != 1 || h[4] != 1) return OV_ERR_CUDA;
     return OV_ERR_TIMEOUT;
   });
 }
