@@ -6,7 +6,11 @@ U = expm(i 0.2 A), mu = 0.3, m_w = -2, one Gaussian source, k = 800, one
 Gaussian cotangent; FP64 throughout (at this point the k-step map amplifies
 rounding by ~1e6 and FP32 basis vectors break the recurrence down; the
 mixed-precision path is reported separately), pair-periodic
-re-biorthogonalisation every 20 steps with one Gram-Schmidt pass.  One step = one ov_tsl_sign_vjp call (forward recurrence, sign,
+re-biorthogonalisation every 60 steps with one Gram-Schmidt pass (at this
+point x stays within 1e-9 and dU within 1e-4 of the result with
+re-biorthogonalisation at every step, for any period from 10 to 100, and the
+error estimate eps_A is the same; every period pays the same Krylov
+truncation error, ~1e-2).  One step = one ov_tsl_sign_vjp call (forward recurrence, sign,
 x = V y, Frechet adjoint, reverse sweep, force, dmu) on inputs resident in
 HBM; the Krylov bases (5.9 GB) exceed the 129 MB L2, so no flush is needed.
 
@@ -39,6 +43,7 @@ from paper_1604_08057_gb300 import inputs  # noqa: E402
 
 METRIC = "s per sgn(H)b + dsgn/dU at 14^4, k=800"
 REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+MIXED_SCHEDULES = (20, 10, 1)   # re-biorthogonalisation periods tried by the mixed-path leg
 
 
 def parse_args():
@@ -50,7 +55,9 @@ def parse_args():
     ap.add_argument("--workload", default="14x14^3")
     ap.add_argument("--k", type=int, default=0, help="override the workload's k")
     ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
-    ap.add_argument("--rebiorth", type=int, default=20)
+    ap.add_argument("--rebiorth", type=int, default=None,
+                    help="re-biorthogonalisation period P (default 60 for the headline workload, "
+                         "20 for the uneven batch)")
     ap.add_argument("--passes", type=int, default=1)
     ap.add_argument("--segment", type=int, default=0,
                     help="two-pass TSL with checkpoints every S steps (needs --rebiorth 0)")
@@ -61,6 +68,10 @@ def parse_args():
                     help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling); "
                          "batch: the uneven batch of 32 problems (forward + VJP) through ov_tsl_batch")
     args = ap.parse_args()
+    # P = 60 at 14x14^3, k = 800: x within 1e-9 and dU within 1e-4 of the P = 1 result
+    # (P = 20: 2e-10 and 4e-4), the same eps_A; the uneven batch keeps P = 20
+    if args.rebiorth is None:
+        args.rebiorth = 20 if args.leg == "batch" else 60
     if args.warmup < 1:
         ap.error("--warmup must be at least 1 (the last warm-up step gives the per-kernel breakdown)")
     return args
@@ -476,40 +487,48 @@ def stencil_leg(args, ut, wl, hbm, peak_src, nsrc=32, reps=20):
 
 def mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar):
     """The mixed-precision path: at the workload point, and at m_w = -1 where the
-    k-step map is well conditioned (timed against the FP64 path there).  FP32
-    bases need two Gram-Schmidt passes (one pass breaks down at m_w = -1)."""
+    k-step map is well conditioned (timed against the FP64 path there, on the same
+    schedule).  FP32 bases need two Gram-Schmidt passes and frequent projections:
+    at m_w = -1 one pass breaks down at P = 20 and two passes break down at P = 60,
+    while two passes at P = 20 complete.  The schedules MIXED_SCHEDULES are tried
+    in turn (the first that completes is timed) and every failure is reported."""
     import torch
     from paper_1604_08057_gb300 import binding
-    res = {"gs_passes": 2}
     passes = 2
+    res = {"gs_passes": passes}
     try:
-        binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, "mixed", args.rebiorth, passes)
-        res["workload_point"] = "completed"
+        binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, "mixed", MIXED_SCHEDULES[0], passes)
+        res["workload_point"] = f"completed (P = {MIXED_SCHEDULES[0]})"
     except binding.OVError as exc:
-        res["workload_point"] = f"status {exc.status}: {exc}"
+        res["workload_point"] = f"P = {MIXED_SCHEDULES[0]}: status {exc.status}: {exc}"
     m_w = -1.0
-    out = {}
-    for prec in ("fp64", "mixed"):
-        try:
-            binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, args.rebiorth, passes)
-            torch.cuda.synchronize()
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record()
-            du, dmu, x = binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, args.rebiorth, passes)
-            t1.record()
-            torch.cuda.synchronize()
-            out[prec] = (t0.elapsed_time(t1) / 1e3, du, dmu, x)
-        except binding.OVError as exc:
-            out[prec] = f"status {exc.status}"
-    if all(isinstance(v, tuple) for v in out.values()):
-        (t64, du64, dmu64, x64), (t32, du32, dmu32, x32) = out["fp64"], out["mixed"]
-        rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
-        res["m_w=-1"] = {"fp64_s": round(t64, 4), "mixed_s": round(t32, 4), "speedup": round(t64 / t32, 2),
-                         "mixed_vs_fp64_rel_x": rel(x32, x64), "mixed_vs_fp64_rel_dU": rel(du32, du64),
-                         "mixed_vs_fp64_rel_dmu": abs(dmu32 - dmu64) / abs(dmu64)}
-    else:
-        res["m_w=-1"] = {p: (v if isinstance(v, str) else "ok") for p, v in out.items()}
+    tried = {}
+    for reb in MIXED_SCHEDULES:
+        out = {}
+        for prec in ("fp64", "mixed"):
+            try:
+                binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, reb, passes)
+                torch.cuda.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record()
+                du, dmu, x = binding.tsl_sign_vjp(ut, wl.mu, m_w, bt, k, xt, prec, reb, passes)
+                t1.record()
+                torch.cuda.synchronize()
+                out[prec] = (t0.elapsed_time(t1) / 1e3, du, dmu, x)
+            except binding.OVError as exc:
+                out[prec] = f"status {exc.status}"
+        if all(isinstance(v, tuple) for v in out.values()):
+            (t64, du64, dmu64, x64), (t32, du32, dmu32, x32) = out["fp64"], out["mixed"]
+            rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+            res["m_w=-1"] = {"rebiorth_period": reb, "fp64_s": round(t64, 4), "mixed_s": round(t32, 4),
+                             "speedup": round(t64 / t32, 2), "mixed_vs_fp64_rel_x": rel(x32, x64),
+                             "mixed_vs_fp64_rel_dU": rel(du32, du64),
+                             "mixed_vs_fp64_rel_dmu": abs(dmu32 - dmu64) / abs(dmu64)}
+            break
+        tried[f"P={reb}"] = {p: (v if isinstance(v, str) else "ok") for p, v in out.items()}
+    if tried:
+        res["m_w=-1_schedules_not_completed"] = tried
     return res
 
 
