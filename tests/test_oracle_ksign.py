@@ -79,3 +79,50 @@ def test_theorem2_block_eigendecomposition_is_wrong():
     via_eig = sign_eig(blk)[:m, m:]
     exact = frechet_sign_daleckii_krein(a, e)
     assert np.linalg.norm(via_eig - exact) > 1e-3 * np.linalg.norm(exact)
+
+
+VARIANTS = [("det", "stagnation"), ("det", "predicted"), ("norm", "stagnation"), ("norm", "predicted")]
+
+
+@pytest.mark.parametrize("m", [5, 40, 120])
+@pytest.mark.parametrize("scaling_kind,stop", VARIANTS)
+def test_sign_variants_match_spectral_form(m, scaling_kind, stop):
+    """Every scaling and stop rule converges to the spectral sign (Sec. 2, Eq. spectral_form)."""
+    rng = np.random.default_rng(100 + m)
+    a = _rand_matrix(m, rng)
+    f = ksign.sign_newton(a, scaling_kind=scaling_kind, stop=stop)
+    assert np.allclose(f, sign_eig(a), atol=1e-9)
+    assert np.allclose(f @ f, np.eye(m), atol=1e-10)
+    h = a + a.conj().T
+    lam, q = np.linalg.eigh(h)
+    want = q @ np.diag(np.sign(lam)) @ q.conj().T
+    assert np.allclose(ksign.sign_newton(h, scaling_kind=scaling_kind, stop=stop), want, atol=1e-10)
+
+
+def test_sign_variants_on_a_tsl_tridiagonal():
+    """On T_k of the 4x4^3 workload (k = 200) the variants agree with the determinant-scaled
+    iteration to the sign's own rounding level, and norm scaling with the predicted stop
+    needs fewer inversions."""
+    from oracle import tsl
+    from paper_1604_08057_gb300 import inputs
+    wl = inputs.WORKLOADS["4x4^3"]
+    u, b, _ = inputs.make_inputs(wl, nsrc=1)
+    res = tsl.tsl_forward(u, b[0], wl.mu, wl.m_w, wl.k, rebiorth=20, passes=1)
+    ref, it_ref = ksign.sign_newton(res.t, return_iters=True)
+    floor = np.linalg.norm(ref @ ref - np.eye(wl.k)) / np.sqrt(wl.k)
+    iters = {}
+    for scaling_kind, stop in VARIANTS:
+        f, it = ksign.sign_newton(res.t, return_iters=True, scaling_kind=scaling_kind, stop=stop)
+        iters[(scaling_kind, stop)] = it
+        assert np.linalg.norm(f[:, 0] - ref[:, 0]) <= 10 * floor * np.linalg.norm(ref[:, 0])
+        assert np.linalg.norm(f @ f - np.eye(wl.k)) / np.sqrt(wl.k) <= 10 * floor
+    assert iters[("det", "stagnation")] == it_ref
+    assert iters[("det", "predicted")] <= it_ref - 1
+    assert iters[("norm", "predicted")] <= it_ref - 2
+
+
+def test_sign_rejects_unknown_rules():
+    with pytest.raises(ValueError):
+        ksign.sign_newton(np.eye(3), scaling_kind="spectral")
+    with pytest.raises(ValueError):
+        ksign.sign_newton(np.eye(3), stop="never")
