@@ -345,6 +345,7 @@ def run_ours(args, rank, world, local_rank):
         out["e2e"] = e2e_leg(args, ut, bt, xt, wl, k)
         out["dw_stencil"] = stencil_leg(args, ut, wl, hbm, peak_src)
         out["mixed_path"] = mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar)
+        out["schedule_compare"] = schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x)
         if world == 1:
             out["cpu_baseline"] = cpu_leg(args, k)
     return out
@@ -386,6 +387,33 @@ def forward_leg(args, ut, bt, wl, k, reps=2):
     torch.cuda.synchronize()
     return {"value": round(e0.elapsed_time(e1) / 1e3 / reps, 6), "unit": "s per sgn(H)b", "steps": reps,
             "newton_iters": info["newton_iters"]}
+
+
+def schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x, periods=(20,)):
+    """The same call with other re-biorthogonalisation periods: device time and the
+    distance of x, dU and dmu from the headline step's results."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    res = {"headline_period": args.rebiorth}
+    rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+    for period in periods:
+        if period == args.rebiorth:
+            continue
+        try:
+            binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, args.precision, period, args.passes)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            du_p, dmu_p, x_p = binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, args.precision, period, args.passes)
+            e1.record()
+            torch.cuda.synchronize()
+            res[f"P={period}"] = {"s_per_call": round(e0.elapsed_time(e1) / 1e3, 4),
+                                  "rel_x_vs_headline": rel(x_p, x), "rel_dU_vs_headline": rel(du_p, du),
+                                  "rel_dmu_vs_headline": abs(dmu_p - dmu) / abs(dmu)}
+        except binding.OVError as exc:
+            res[f"P={period}"] = f"status {exc.status}"
+    return res
 
 
 def e2e_leg(args, ut, bt, xt, wl, k):
