@@ -413,6 +413,8 @@ def schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x, periods=(20,)):
                                   "rel_dmu_vs_headline": abs(dmu_p - dmu) / abs(dmu)}
         except binding.OVError as exc:
             res[f"P={period}"] = f"status {exc.status}"
+        except RuntimeError as exc:   # e.g. device memory: the headline line must still print
+            res[f"P={period}"] = f"error: {exc}"
     return res
 
 
