@@ -63,7 +63,6 @@ def parse_args():
                     help="two-pass TSL with checkpoints every S steps (needs --rebiorth 0)")
     ap.add_argument("--m-w", type=float, default=None, help="override the workload's Wilson mass")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
-    ap.add_argument("--cpu-k", type=int, default=4, help="Lanczos steps of the oracle sample")
     ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch"],
                     help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling); "
                          "batch: the uneven batch of 32 problems (forward + VJP) through ov_tsl_batch")
@@ -286,14 +285,7 @@ def run_ours(args, rank, world, local_rank):
     ms_total, value = job_seconds_per_unit(e0.elapsed_time(e1), args.steps, world, dev)
 
     # roofline of the dominant lattice kernel
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    hbm, peak_src = hbm_peak()
     bytes_dom = algorithmic_bytes(dom, k, V, nsrc, e, args.rebiorth, args.passes) * args.steps
     gbs = bytes_dom / (prof[dom][1] / 1e3) / 1e9
     per_launch = {"launches": prof[dom][0], "avg_launch_us": round(1e3 * prof[dom][1] / max(1, prof[dom][0]), 2),
@@ -346,12 +338,24 @@ def run_ours(args, rank, world, local_rank):
         out["dw_stencil"] = stencil_leg(args, ut, wl, hbm, peak_src)
         out["mixed_path"] = mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar)
         out["schedule_compare"] = schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x)
+        out["diagnostics"] = diagnostics_leg(args, ut, bt, xt, wl, k, ms_total / args.steps)
         if world == 1:
-            out["cpu_baseline"] = cpu_leg(args, k)
+            out["cpu_baseline"], out["parity"] = cpu_leg(args, k, ut)
     return out
 
 
 PROJ_DOTS_TRAFFIC_RATIO = 1.050
+
+
+def hbm_peak():
+    """(HBM copy bandwidth in GB/s, its source): the measured figure of
+    MEASURED_PEAKS.json when present, else the profiling fallback of 6.8 TB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+        return float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
 
 
 def fp64_peak(dev, n=4096, reps=3):
@@ -416,6 +420,30 @@ def schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x, periods=(20,)):
         except RuntimeError as exc:   # e.g. device memory: the headline line must still print
             res[f"P={period}"] = f"error: {exc}"
     return res
+
+
+def diagnostics_leg(args, ut, bt, xt, wl, k, ms_step):
+    """The headline call once more with the run diagnostics on: the sampled loss of
+    biorthogonality of the bases, min |Re| of the Ritz values and ||T_k||, and
+    what the diagnostics cost."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    opts = (args.precision, args.rebiorth, args.passes)
+    binding.diagnostics_mode(True, *opts, segment=args.segment)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, _, info = binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, *opts, return_info=True,
+                                             segment=args.segment)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return {"biorth_loss": info["biorth_loss"], "min_abs_re_ritz": info["min_abs_re_ritz"],
+                "t_norm": info["t_norm"], "s_per_call_with_diagnostics": round(dt, 4),
+                "s_per_call_without": round(ms_step / 1e3, 4)}
+    except binding.OVError as exc:
+        return {"status": exc.status, "error": str(exc)}
+    finally:
+        binding.diagnostics_mode(False, *opts, segment=args.segment)
 
 
 def e2e_leg(args, ut, bt, xt, wl, k):
@@ -526,11 +554,27 @@ def mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar):
     from paper_1604_08057_gb300 import binding
     passes = 2
     res = {"gs_passes": passes}
-    try:
-        binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, "mixed", MIXED_SCHEDULES[0], passes)
-        res["workload_point"] = f"completed (P = {MIXED_SCHEDULES[0]})"
-    except binding.OVError as exc:
-        res["workload_point"] = f"P = {MIXED_SCHEDULES[0]}: status {exc.status}: {exc}"
+    rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+    # at the workload point: projections at every step (the most the schedule can do),
+    # against the FP64 path on the same schedule
+    wp = {}
+    for prec in ("mixed", "fp64"):
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            du, dmu, x = binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, prec, 1, passes)
+            torch.cuda.synchronize()
+            wp[prec] = (time.perf_counter() - t0, du, dmu, x)
+        except binding.OVError as exc:
+            wp[prec] = f"status {exc.status}: {exc}"
+    if all(isinstance(v, tuple) for v in wp.values()):
+        (t32, du32, dmu32, x32), (t64, du64, dmu64, x64) = wp["mixed"], wp["fp64"]
+        res["workload_point"] = {"rebiorth_period": 1, "mixed_s": round(t32, 3), "fp64_s": round(t64, 3),
+                                 "mixed_vs_fp64_rel_x": rel(x32, x64), "mixed_vs_fp64_rel_dU": rel(du32, du64),
+                                 "mixed_vs_fp64_rel_dmu": abs(dmu32 - dmu64) / abs(dmu64)}
+    else:
+        res["workload_point"] = {p: (v if isinstance(v, str) else "ok") for p, v in wp.items()}
+        res["workload_point"]["rebiorth_period"] = 1
     m_w = -1.0
     tried = {}
     for reb in MIXED_SCHEDULES:
@@ -550,7 +594,6 @@ def mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar):
                 out[prec] = f"status {exc.status}"
         if all(isinstance(v, tuple) for v in out.values()):
             (t64, du64, dmu64, x64), (t32, du32, dmu32, x32) = out["fp64"], out["mixed"]
-            rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
             res["m_w=-1"] = {"rebiorth_period": reb, "fp64_s": round(t64, 4), "mixed_s": round(t32, 4),
                              "speedup": round(t64 / t32, 2), "mixed_vs_fp64_rel_x": rel(x32, x64),
                              "mixed_vs_fp64_rel_dU": rel(du32, du64),
@@ -562,20 +605,94 @@ def mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar):
     return res
 
 
-def cpu_leg(args, k):
-    """The FP64 oracle on the host cores, on a bounded sample of the workload."""
-    from oracle import tsl, vjp
-    wl = workload_of(args)
-    u, b, xbar = inputs.make_inputs(wl)
-    ks = args.cpu_k
+CPU_SMALL_K = 6   # Lanczos steps of the oracle's full-size samples
+
+
+def oracle_time(fn, reps=1):
     t0 = time.perf_counter()
-    fwd = tsl.tsl_forward(u, b[0], wl.mu, wl.m_w, ks, rebiorth=args.rebiorth, passes=args.passes)
-    vjp.tsl_vjp(u, b[0], wl.mu, wl.m_w, ks, xbar[0], rebiorth=args.rebiorth, passes=args.passes, fwd=fwd)
-    dt = time.perf_counter() - t0
-    return {"value": round(dt * k / ks, 3), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"forward + VJP at {args.workload} with k={ks} took {dt:.2f} s; scaled linearly to k={k} "
-                      f"(omits the O(k^2) re-biorthogonalisation and O(k^3) sign terms, so it understates "
-                      f"the oracle's time)"}
+    for _ in range(reps):
+        out = fn()
+    return (time.perf_counter() - t0) / reps, out
+
+
+def cpu_composed(args, k, period, passes):
+    """The FP64 oracle's seconds per forward + VJP call at the workload, composed
+    from pieces timed on the host (the oracle as it stands):
+
+      * t_step: one Lanczos step of the forward and reverse sweeps at full size,
+        from a forward + VJP run with CPU_SMALL_K steps and no projections;
+      * t_proj(j): the projections of step j (forward Gram-Schmidt and its
+        adjoint, both linear in j), from the same run with projections at every
+        step minus the first, divided by sum (j + 1);
+      * the k x k sign (Newton) and its Frechet adjoint (block Newton), timed on
+        the T_k of the 4x4^3 workload's oracle run at k = 200 and scaled by
+        (k / 200)^3 (dense O(k^3) iterations);
+      * the 4x4^3 workload itself (k = 200, period 20, one pass), run end to end.
+
+    Returns (estimate in s, details, the 4x4^3 oracle result)."""
+    from oracle import ksign, tsl, vjp
+    wl = workload_of(args)
+    u, b, xbar = inputs.make_inputs(wl, nsrc=1)
+    ks = CPU_SMALL_K
+
+    def run(reb):
+        fwd = tsl.tsl_forward(u, b[0], wl.mu, wl.m_w, ks, rebiorth=reb, passes=passes)
+        return vjp.tsl_vjp(u, b[0], wl.mu, wl.m_w, ks, xbar[0], rebiorth=reb, passes=passes, fwd=fwd)
+
+    t_plain, _ = oracle_time(lambda: run(0))
+    t_proj_all, _ = oracle_time(lambda: run(1))
+    t_step = t_plain / ks
+    proj_units_small = sum(j + 1 for j in rebiorth_steps(ks, 1))
+    t_unit = max(0.0, t_proj_all - t_plain) / proj_units_small
+    proj_units = sum(j + 1 for j in rebiorth_steps(k, period))
+    # the 4x4^3 workload end to end (also the parity reference of the GPU path)
+    w0 = inputs.WORKLOADS["4x4^3"]
+    u0, b0, x0 = inputs.make_inputs(w0)
+
+    def small():
+        f = tsl.tsl_forward(u0, b0[0], w0.mu, w0.m_w, w0.k, rebiorth=20, passes=1)
+        d, m, _ = vjp.tsl_vjp(u0, b0[0], w0.mu, w0.m_w, w0.k, x0[0], rebiorth=20, passes=1, fwd=f)
+        return f, d, m
+
+    t_small, (f0, du0, dmu0) = oracle_time(small)
+    g = np.zeros_like(f0.t)
+    g[:, 0] = f0.beta0 * np.arange(1, w0.k + 1)
+    t_sign, _ = oracle_time(lambda: ksign.sign_newton(f0.t))
+    t_frechet, _ = oracle_time(lambda: ksign.frechet_adjoint_sign(f0.t, g))
+    scale = (k / w0.k) ** 3
+    est = k * t_step + proj_units * t_unit + scale * (t_sign + t_frechet)
+    details = {"t_step_s": round(t_step, 4), "t_proj_per_basis_vector_s": round(t_unit, 5),
+               "proj_basis_vectors": proj_units, "t_sign_k200_s": round(t_sign, 3),
+               "t_frechet_k200_s": round(t_frechet, 3), "dense_scale": round(scale, 1),
+               "workload_4x4^3_k200_s": round(t_small, 3)}
+    return est, details, (w0, u0, b0, x0, f0, du0, dmu0)
+
+
+def cpu_leg(args, k, ut):
+    """The FP64 oracle on the host cores: the 4x4^3 workload measured end to end, and
+    the benchmark's workload composed from timed pieces (``cpu_composed``).  The
+    same 4x4^3 oracle run is the reference of the GPU path's errors there (x, dU,
+    dmu of the FP64 path, period 20, one pass)."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    t0 = time.perf_counter()
+    est, details, (w0, u0, b0, x0, f0, du0, dmu0) = cpu_composed(args, k, args.rebiorth, args.passes)
+    wall = time.perf_counter() - t0
+    dev = ut.device
+    du, dmu, x = binding.tsl_sign_vjp(torch.tensor(u0, device=dev), w0.mu, w0.m_w, torch.tensor(b0[0], device=dev),
+                                      w0.k, torch.tensor(x0[0], device=dev), "fp64", 20, 1)
+    rel = lambda a, c: float(np.linalg.norm(a - c) / np.linalg.norm(c))
+    parity = {"workload": "4x4^3 lattice, k=200, mu=0.3, m_w=-2, period 20, one pass (FP64 GPU vs FP64 oracle)",
+              "rel_x": rel(x.cpu().numpy(), f0.x), "rel_dU": rel(du.cpu().numpy(), du0),
+              "rel_dmu": abs(dmu - dmu0) / abs(dmu0),
+              "oracle_rounding_floor": {"x": 1.0e-10, "dU": 7.4e-7, "dmu": 2.7e-7}}
+    cpu = {"value": round(est, 2), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": (f"composed from oracle pieces timed on the host ({wall:.1f} s of CPU work): "
+                      f"{CPU_SMALL_K}-step forward + VJP runs at {args.workload} with and without projections, "
+                      f"the k x k sign and Frechet adjoint at k=200 scaled by (k/200)^3, and the 4x4^3 "
+                      f"workload end to end ({details['workload_4x4^3_k200_s']} s per call)"),
+           "pieces": details}
+    return cpu, parity
 
 
 def run_reference(args, rank):
@@ -583,32 +700,31 @@ def run_reference(args, rank):
         return None
     wl = workload_of(args)
     k = args.k or wl.k
-    from oracle import tsl, vjp
-    u, b, xbar = inputs.make_inputs(wl)
-    ks = args.cpu_k
-
-    def sample():
-        fwd = tsl.tsl_forward(u, b[0], wl.mu, wl.m_w, ks, rebiorth=args.rebiorth, passes=args.passes)
-        vjp.tsl_vjp(u, b[0], wl.mu, wl.m_w, ks, xbar[0], rebiorth=args.rebiorth, passes=args.passes, fwd=fwd)
-
-    for _ in range(args.warmup):
-        sample()
+    from oracle import tsl
+    w0 = inputs.WORKLOADS["4x4^3"]
+    u0, b0, _ = inputs.make_inputs(w0)
+    for _ in range(args.warmup):   # warm-up: the oracle's stencil and recurrence on a small lattice
+        tsl.tsl_forward(u0, b0[0], w0.mu, w0.m_w, 40, rebiorth=20, passes=1)
+    vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        sample()
+        est, details, _ = cpu_composed(args, k, args.rebiorth, args.passes)
+        vals.append(est)
     dt = (time.perf_counter() - t0) / args.steps
-    value = dt * k / ks
-    desc = (f"FP64 numpy oracle, forward + VJP at {args.workload} with k={ks} per step ({dt:.2f} s), "
-            f"scaled linearly to k={k}")
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "s", "n_gpus": args.gpus,
+    value = statistics.median(vals)
+    desc = (f"FP64 numpy oracle, composed per step from pieces timed on the host ({dt:.1f} s of CPU work per "
+            f"step): {CPU_SMALL_K}-step forward + VJP runs at {args.workload} with and without projections, the "
+            f"k x k sign and Frechet adjoint at k=200 scaled by (k/200)^3")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 1),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"{args.workload} lattice, k={k}, mu={wl.mu}, m_w={wl.m_w}, "
-                                   f"1 source, forward + gauge-force VJP"},
-            "cpu_baseline": {"value": round(value, 3), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": desc},
-            "e2e": {"value": round(value, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                                   f"1 source, forward + gauge-force VJP",
+                       "rebiorth_period": args.rebiorth, "gs_passes": args.passes},
+            "cpu_baseline": {"value": round(value, 2), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": desc, "pieces": details},
+            "e2e": {"value": round(value, 2), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
@@ -638,7 +754,8 @@ def main():
         torch.cuda.set_device(local_rank)
         wl = workload_of(args)
         u, _, _ = inputs.make_inputs(wl)
-        out = stencil_leg(args, torch.tensor(u, device=f"cuda:{local_rank}"), wl, 6786.9, "measured")
+        hbm, peak_src = hbm_peak()
+        out = stencil_leg(args, torch.tensor(u, device=f"cuda:{local_rank}"), wl, hbm, peak_src)
         print(json.dumps(out))
         return
     out = run_ours(args, rank, world, local_rank)

@@ -50,6 +50,7 @@ extern "C" {
 #define OV_ERR_SCRATCH_LIMIT  -7  /* the problem does not fit the fixed scratch of ov_apply_H_noalloc */
 #define OV_ERR_TIMEOUT        -8  /* a device-side wait between blocks ran past its limit (2 s); the
                                      blocks stop and the context stays usable */
+#define OV_ERR_NOCONV         -9  /* the eigenvalue iteration of the Ritz diagnostic did not converge */
 
 /* Precision of lattice vectors, links and stencil arithmetic.
  * OV_FP64 : everything in FP64.
@@ -76,7 +77,16 @@ typedef struct {
                         * steps are separated by bounded inter-block waits), else 1;
                         * 1: one launch per elimination step, replayed as a CUDA graph.
                         * Both give bitwise identical results. */
-  int32_t reserved[3];
+  int32_t diagnostics; /* 0: none.  1: after the forward recurrence of ov_tsl_sign, ov_tsl_sign_vjp,
+                        * ov_tsl_sign_fwd and ov_tsl_batch, measure (a) the loss of
+                        * biorthogonality of the stored bases, sampled on the last pair of basis
+                        * vectors: max over i < k of |w_i^dag v_k|, |v_i^dag w_k| and of
+                        * |w_k^dag v_k - 1| (one dot-product sweep over both bases; not with
+                        * segments), and (b) the Ritz values, the eigenvalues of T_k (host,
+                        * ov_tridiag_eigenvalues), and return OV_ERR_SIGN_ILLPOSED, with info
+                        * filled, when min |Re lambda(T_k)| <= 1e-14 ||T_k||_inf (sgn is not
+                        * defined on the imaginary axis, Sec. 2 Eq. spectral_form). */
+  int32_t reserved[2];
 } ov_options;
 
 typedef struct {
@@ -84,11 +94,15 @@ typedef struct {
   int32_t newton_iters;     /* Newton iterations of the k x k sign (forward) */
   int32_t newton_iters_adj; /* Newton iterations of the Frechet adjoint (VJP only) */
   int32_t reserved;
-  double  min_abs_re_ritz;  /* unused (0) unless computed by the caller */
+  double  min_abs_re_ritz;  /* with options.diagnostics: min over sources and Ritz values of
+                               |Re lambda(T_k)|; else 0 */
   double  t_ms[8];          /* phase times (ms).  ov_tsl_sign: 0 forward Krylov, 1 k x k sign,
                                2 combine.  ov_tsl_sign_vjp: 0 forward Krylov, 1 g_y = V^dag xbar,
                                2 k x k sign and Frechet adjoint, 3 combine, 4 reverse sweep and
                                force.  Others unused. */
+  double  biorth_loss;      /* with options.diagnostics: the sampled loss of biorthogonality
+                               (max over sources; -1 with segments); else 0 */
+  double  t_norm;           /* with options.diagnostics: max over sources of ||T_k||_inf; else 0 */
 } ov_tsl_info;
 
 typedef struct ov_context ov_context;
@@ -290,15 +304,51 @@ int64_t ov_launch_count(ov_context *ctx);
  * every GPU that loads the library holds until the process exits; the call
  * allocates and frees nothing.  It needs (72 V + 2 nsrc ceil64(24 V)) * 8
  * bytes (ceil64 rounds up to a multiple of 64) and returns
- * OV_ERR_SCRATCH_LIMIT when that exceeds the array.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture.  All calls share
+ * OV_ERR_SCRATCH_LIMIT when that exceeds the array (nsrc above 4096 is
+ * OV_ERR_INVALID_ARG).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  The cached address belongs to the device's
+ * primary context: after cudaDeviceReset it is stale, so do not use this
+ * entry point in a process that resets a device it has already called it
+ * on.  A launch error left pending by earlier work on the calling thread is
+ * cleared on entry (cudaGetLastError), so OV_ERR_CUDA always refers to this
+ * call's own launches.  All calls share
  * the one array: calls whose work overlaps on the GPU (different streams, or
  * different host threads on one device) race and corrupt each other's
  * results; calls ordered on one stream are safe. */
 #define OV_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ov_apply_H_noalloc(const int32_t dims[4], const void *U, double mu, double m_w, int32_t nsrc,
                        const void *in, void *out, int32_t dagger, void *stream);
+
+/* Eigenvalues of one TSL tridiagonal T_k (the Ritz values), on the host: no
+ * GPU and no context needed.  Host arrays as ov_tsl_coefficients writes them:
+ * alpha[2k] and beta[2k] interleaved complex (alpha_j = T[j][j],
+ * beta_j = T[j-1][j], beta_0 unused), delta[k] (delta_j = T[j][j-1]).  The
+ * off-diagonal pairs must satisfy |beta_j| = |delta_j| (the TSL's split of
+ * omega); eig[2k] receives the eigenvalues, interleaved complex, unordered.
+ * Method: diagonal similarity to a complex-symmetric tridiagonal and implicit
+ * QL iteration with complex-orthogonal rotations, O(k^2).  Returns OV_OK,
+ * OV_ERR_INVALID_ARG, OV_ERR_NONFINITE (a non-finite entry) or OV_ERR_NOCONV
+ * (no convergence, or a rotation that would break down). */
+int ov_tridiag_eigenvalues(int32_t k, const double *alpha, const double *beta, const double *delta,
+                           double *eig);
+
+/* Host-side fault injection for tests of error propagation (no GPU fault is
+ * caused: the library writes an ordinary value, or fails an allocation, on
+ * the host's initiative).  One-shot: the injection fires once in the next
+ * call that reaches it on this context, then clears.  The paper has no
+ * counterpart.  Kinds: */
+#define OV_INJECT_NONE        0
+#define OV_INJECT_BREAKDOWN   1  /* after the three-term update of Lanczos step `step` (0-based),
+                                    source 0 is flagged as broken down, as the update kernel flags
+                                    |omega| <= 1e-14 ||r|| ||s||; the call returns OV_ERR_BREAKDOWN */
+#define OV_INJECT_NONFINITE   2  /* after the stencil of step `step`, alpha_step of source 0 is set
+                                    to NaN; the update kernel then flags a non-finite omega and the
+                                    call returns OV_ERR_NONFINITE */
+#define OV_INJECT_OOM         3  /* the workspace allocation after the next `step` successful ones
+                                    fails as cudaMalloc would; the call returns OV_ERR_OOM and the
+                                    context stays usable */
+int ov_debug_inject(ov_context *ctx, int32_t kind, int32_t step);
 
 /* Human-readable text for a status code (static storage). */
 const char *ov_strerror(int status);

@@ -33,6 +33,13 @@ The pre-pass vectors are rebuilt from the stored basis and coefficients,
 r_in = r_out + V c, starting from r = delta_{j+1} v_{j+1}.
 
 The contraction of g_H = sum a b^dagger into (dU, dmu) is ``dirac.link_gradient``.
+
+``emulate_fp32`` estimates how far an implementation that keeps its lattice
+vectors in FP32 can be from the FP64 result: as in ``tsl.tsl_forward``, the
+links and every stored or produced lattice vector (here also every cotangent
+vector of the reverse sweep) are rounded to complex64, while the dots, the
+recurrence scalars, the k x k sign and its Frechet adjoint, and the final
+contraction stay in FP64.
 """
 from __future__ import annotations
 
@@ -41,19 +48,21 @@ import numpy as np
 from . import dirac, ksign, tsl as tslmod
 
 
-def tsl_vjp(u, b, mu, m_w, k, xbar, rebiorth=1, passes=2, fwd=None):
+def tsl_vjp(u, b, mu, m_w, k, xbar, rebiorth=1, passes=2, fwd=None, emulate_fp32=False):
     """Return (dU, dmu, fwd) for L = Re <xbar, TSL_k(H(U, mu)) b>."""
     if fwd is None:
-        fwd = tslmod.tsl_forward(u, b, mu, m_w, k, rebiorth=rebiorth, passes=passes)
+        fwd = tslmod.tsl_forward(u, b, mu, m_w, k, rebiorth=rebiorth, passes=passes, emulate_fp32=emulate_fp32)
     v, w = fwd.v, fwd.w
     alpha, beta, delta, y = fwd.alpha, fwd.beta, fwd.delta, fwd.y
     xbar = np.asarray(xbar, dtype=np.complex128)
+    rnd = tslmod._round32 if emulate_fp32 else tslmod._identity
+    uu = rnd(np.asarray(u, dtype=np.complex128))
 
     def h(psi):
-        return dirac.apply_h(u, psi, mu, m_w)
+        return rnd(dirac.apply_h(uu, psi, mu, m_w))
 
     def hdag(psi):
-        return dirac.apply_h_dagger(u, psi, mu, m_w)
+        return rnd(dirac.apply_h_dagger(uu, psi, mu, m_w))
 
     # g_y = V^dagger xbar;  G_F = beta_0 g_y e_1^T;  G_T = L_sgn(T^dagger, G_F)
     g_y = np.array([np.vdot(v[j], xbar) for j in range(k)])
@@ -76,9 +85,9 @@ def tsl_vjp(u, b, mu, m_w, k, xbar, rebiorth=1, passes=2, fwd=None):
     # last index (0-based k-1): only alpha_k = w_k^dagger H v_k
     j = k - 1
     g_a = g_alpha_t[j]
-    g_p = w[j] * g_a
-    gv = np.conj(y[j]) * xbar + hdag(g_p)          # complete gradient of v[k-1]
-    gw = h(v[j]) * np.conj(g_a)                    # complete gradient of w[k-1]
+    g_p = rnd(w[j] * g_a)
+    gv = rnd(np.conj(y[j]) * xbar + hdag(g_p))     # complete gradient of v[k-1]
+    gw = rnd(h(v[j]) * np.conj(g_a))               # complete gradient of w[k-1]
     terms_a.append(g_p)
     terms_b.append(v[j])
 
@@ -102,8 +111,8 @@ def tsl_vjp(u, b, mu, m_w, k, xbar, rebiorth=1, passes=2, fwd=None):
         # omega = s^dagger r with r = d v[j+1], s = conj(bt) w[j+1]
         r_out = d * v[j + 1]
         s_out = np.conj(bt) * w[j + 1]
-        g_r = g_r + s_out * g_w
-        g_s = g_s + r_out * np.conj(g_w)
+        g_r = rnd(g_r + s_out * g_w)
+        g_s = rnd(g_s + r_out * np.conj(g_w))
         # Gram-Schmidt passes of this step, last pass first
         if j in fwd.proj:
             vm, wm = vm_all[:, :j + 1], wm_all[:, :j + 1]
@@ -115,8 +124,8 @@ def tsl_vjp(u, b, mu, m_w, k, xbar, rebiorth=1, passes=2, fwd=None):
                 for i in range(j + 1):
                     acc_v[i] -= g_r * np.conj(c[i]) + s_in * np.conj(e_s[i])
                     acc_w[i] -= r_in * np.conj(e_r[i]) + g_s * np.conj(dd[i])
-                g_r = g_r - (wm @ e_r).reshape(g_r.shape)
-                g_s = g_s - (vm @ e_s).reshape(g_s.shape)
+                g_r = rnd(g_r - (wm @ e_r).reshape(g_r.shape))
+                g_s = rnd(g_s - (vm @ e_s).reshape(g_s.shape))
                 r_out, s_out = r_in, s_in
         # r = p - alpha v[j] - beta[j] v[j-1];  s = q - conj(alpha) w[j] - delta[j] w[j-1]
         g_p = g_r.copy()
@@ -130,16 +139,16 @@ def tsl_vjp(u, b, mu, m_w, k, xbar, rebiorth=1, passes=2, fwd=None):
             new_carry_beta = -np.vdot(v[j - 1], g_r)
             new_carry_delta = -np.real(np.vdot(w[j - 1], g_s))
         # alpha = w[j]^dagger p
-        g_p = g_p + w[j] * g_a
+        g_p = rnd(g_p + w[j] * g_a)
         pw = pw + h(v[j]) * np.conj(g_a)
         # p = H v[j], q = H^dagger w[j]; plus the projection terms of later steps
-        gv = pv + np.conj(y[j]) * xbar + hdag(g_p) + acc_v[j]
-        gw = pw + h(g_q) + acc_w[j]
+        gv = rnd(pv + np.conj(y[j]) * xbar + hdag(g_p) + acc_v[j])
+        gw = rnd(pw + h(g_q) + acc_w[j])
         terms_a += [g_p, w[j]]
         terms_b += [v[j], g_q]
         if j > 0:
             pv, pw = new_pv, new_pw
             carry_beta, carry_delta = new_carry_beta, new_carry_delta
 
-    du, dmu = dirac.link_gradient(np.stack(terms_a), np.stack(terms_b), u, mu, m_w)
+    du, dmu = dirac.link_gradient(np.stack(terms_a), np.stack(terms_b), uu, mu, m_w)
     return du, dmu, fwd

@@ -35,7 +35,7 @@ class OVError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("dense", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("diagnostics", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class TuneReport(ctypes.Structure):
@@ -47,11 +47,14 @@ class TuneReport(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("k_reached", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
                 ("newton_iters_adj", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("min_abs_re_ritz", ctypes.c_double), ("t_ms", ctypes.c_double * 8)]
+                ("min_abs_re_ritz", ctypes.c_double), ("t_ms", ctypes.c_double * 8),
+                ("biorth_loss", ctypes.c_double), ("t_norm", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {"k_reached": self.k_reached, "newton_iters": self.newton_iters,
-                "newton_iters_adj": self.newton_iters_adj, "t_ms": list(self.t_ms)}
+                "newton_iters_adj": self.newton_iters_adj, "t_ms": list(self.t_ms),
+                "min_abs_re_ritz": self.min_abs_re_ritz, "biorth_loss": self.biorth_loss,
+                "t_norm": self.t_norm}
 
 
 class Problem(ctypes.Structure):
@@ -64,7 +67,7 @@ class Problem(ctypes.Structure):
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
-           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_strerror"]
+           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -102,6 +105,8 @@ def load(path: str = LIB_PATH):
     lib.ov_profile_read.argtypes = [P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(D), I32]
     lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
     lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
+    lib.ov_tridiag_eigenvalues.argtypes = [I32, P, P, P, P]
+    lib.ov_debug_inject.argtypes = [P, I32, I32]
     lib.ov_launch_count.argtypes = [P]
     lib.ov_launch_count.restype = ctypes.c_int64
     lib.ov_strerror.argtypes = [ctypes.c_int]
@@ -132,13 +137,55 @@ def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=
     return _contexts[key]
 
 
+_extra = {}   # per cached context: the options not in its key (dense, diagnostics)
+
+
+def _set_extra(precision, rebiorth, passes, segment, **kw):
+    ctx = context(precision, rebiorth, passes, segment=segment)
+    key = (precision, rebiorth, passes, segment, ctx.value)
+    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0})
+    ex.update({k: int(v) for k, v in kw.items()})
+    opt = Options(_PREC[precision], rebiorth, passes, segment, ex["dense"], ex["diagnostics"])
+    _check(load().ov_context_set_options(ctx, ctypes.byref(opt)), "ov_context_set_options")
+    return ctx
+
+
 def dense_mode(mode: int, precision: str = "fp64", rebiorth: int = 1, passes: int = 2, segment: int = 0):
     """How the k x k inversions run on the cached context for these options:
     0 one cooperative launch per inversion where the rows fit on chip (default),
     1 one launch per Gauss-Jordan step replayed as a graph (identical results)."""
+    _set_extra(precision, rebiorth, passes, segment, dense=mode)
+
+
+def diagnostics_mode(on: bool, precision: str = "fp64", rebiorth: int = 1, passes: int = 2, segment: int = 0):
+    """Run diagnostics (biorthogonality loss, Ritz values, ill-posed sign check) on the
+    cached context for these options; results appear in the calls' info."""
+    _set_extra(precision, rebiorth, passes, segment, diagnostics=on)
+
+
+def debug_inject(kind: str, step: int = 0, precision: str = "fp64", rebiorth: int = 1, passes: int = 2,
+                 segment: int = 0):
+    """One-shot host-side fault injection on the cached context: 'breakdown' or
+    'nonfinite' at Lanczos step `step`, or 'oom' after `step` successful allocations."""
+    kinds = {"none": 0, "breakdown": 1, "nonfinite": 2, "oom": 3}
     ctx = context(precision, rebiorth, passes, segment=segment)
-    opt = Options(_PREC[precision], rebiorth, passes, segment, int(mode))
-    _check(load().ov_context_set_options(ctx, ctypes.byref(opt)), "ov_context_set_options")
+    _check(load().ov_debug_inject(ctx, kinds[kind], int(step)), "ov_debug_inject")
+
+
+def tridiag_eigenvalues(alpha, beta, delta):
+    """Eigenvalues of the TSL tridiagonal (host numpy arrays as tsl_coefficients returns
+    them: complex alpha[k], complex beta[k] with beta[0] unused, real delta[k])."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128))
+    b = np.ascontiguousarray(np.asarray(beta, dtype=np.complex128))
+    d = np.ascontiguousarray(np.asarray(delta, dtype=np.float64))
+    k = a.shape[0]
+    if b.shape != (k,) or d.shape != (k,):
+        raise ValueError("alpha, beta, delta must have length k")
+    out = np.empty(k, dtype=np.complex128)
+    _check(load().ov_tridiag_eigenvalues(k, a.ctypes.data, b.ctypes.data, d.ctypes.data, out.ctypes.data),
+           "ov_tridiag_eigenvalues")
+    return out
 
 
 def _dims(u: torch.Tensor):

@@ -62,11 +62,19 @@ bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15
 
 extern "C" int ov_apply_H_noalloc(const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
                                   const void* in, void* out, int32_t dagger, void* stream) {
-  if (!dims || !aligned16(U) || !aligned16(in) || !aligned16(out) || nsrc < 1) return OV_ERR_INVALID_ARG;
+  // a launch error left pending by earlier, unrelated work on this thread is
+  // cleared here, so that the status returned below belongs to this call
+  cudaGetLastError();
+  if (!dims || !aligned16(U) || !aligned16(in) || !aligned16(out) || nsrc < 1 || nsrc > 4096)
+    return OV_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i)
     if (dims[i] < 1 || dims[i] > 4096) return OV_ERR_INVALID_ARG;
   if (!(std::isfinite(mu) && std::isfinite(m_w)) || 2.0 * m_w + 8.0 == 0.0) return OV_ERR_INVALID_ARG;
   const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+  // Every site costs at least 72 + 2 * 24 doubles (576 bytes) of scratch, so this
+  // bound alone keeps V small enough that `need` below cannot overflow (V <= 58254,
+  // nsrc <= 4096) and every grid size fits its launch type.
+  if (V > (int64_t)(OV_NOALLOC_SCRATCH_BYTES / 576u)) return OV_ERR_SCRATCH_LIMIT;
   // scratch: internal links (72 V doubles), packed input and output (24 V doubles per source, padded)
   const int64_t vs = ((24 * V + 63) / 64) * 64;
   const int64_t need = (72 * V + 2 * (int64_t)nsrc * vs) * (int64_t)sizeof(double);

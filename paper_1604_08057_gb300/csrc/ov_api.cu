@@ -75,6 +75,10 @@ struct ov_context {
   int tuned_pair[2] = {0, 0};
   bool owns_stream = false;     // worker contexts of ov_tsl_batch own theirs
   std::vector<ov_context*> workers;
+  // one-shot host-side fault injection (ov_debug_inject)
+  int inj_kind = OV_INJECT_NONE, inj_step = 0;
+  int inj_word[2] = {0, 0};     // host copy of the error word written by an injected breakdown
+  double inj_nan[2] = {0.0, 0.0};
 };
 
 namespace {
@@ -111,6 +115,12 @@ void run(ov_context* c, int kind, int64_t nl, F&& f) {
 void* ws(ov_context* c, int id, size_t bytes, bool zero = false) {
   if (bytes == 0) bytes = 16;
   if (c->cap[id] < bytes) {
+    if (c->inj_kind == OV_INJECT_OOM) {
+      if (c->inj_step-- <= 0) {
+        c->inj_kind = OV_INJECT_NONE;
+        throw Status{OV_ERR_OOM};
+      }
+    }
     if (c->buf[id]) CK(cudaFree(c->buf[id]));
     c->buf[id] = nullptr;
     c->cap[id] = 0;
@@ -218,6 +228,25 @@ int scalar_status(const std::vector<SrcScal>& h, int* k_reached, int k) {
   return st;
 }
 
+// Host-side fault injection (ov_debug_inject): after the stencil of step j, a NaN
+// in alpha_j of source 0; after the update of step j, source 0 flagged as broken
+// down exactly as the update kernel flags it.  Plain copies of ordinary values.
+template <typename R>
+void inject_after_stencil(ov_context* c, const Lat<R>& L, int j) {
+  if (c->inj_kind != OV_INJECT_NONFINITE || c->inj_step != j) return;
+  c->inj_kind = OV_INJECT_NONE;
+  c->inj_nan[0] = c->inj_nan[1] = std::nan("");
+  CK(cudaMemcpyAsync(L.alpha + j, c->inj_nan, sizeof(zd), cudaMemcpyHostToDevice, c->st));
+}
+template <typename R>
+void inject_after_update(ov_context* c, const Lat<R>& L, int j) {
+  if (c->inj_kind != OV_INJECT_BREAKDOWN || c->inj_step != j) return;
+  c->inj_kind = OV_INJECT_NONE;
+  c->inj_word[0] = ERRB_BREAKDOWN;
+  c->inj_word[1] = j + 1;
+  CK(cudaMemcpyAsync(&L.sc[0].err, c->inj_word, 2 * sizeof(int), cudaMemcpyHostToDevice, c->st));
+}
+
 // Forward Krylov recurrence for all sources; bases, coefficients stay on device.
 template <typename R>
 void forward_krylov(ov_context* c, Lat<R>& L) {
@@ -228,6 +257,7 @@ void forward_krylov(ov_context* c, Lat<R>& L) {
   run(c, OV_KIND_UPDATE, 1, [&] { tsl_init(L, c->st); });
   for (int j = 0; j < k; ++j) {
     run(c, OV_KIND_STENCIL_PAIR, 1, [&] { tsl_stencil(L, j, j < k - 1, c->st, c->tuned_pair[c->opt.precision]); });
+    inject_after_stencil(c, L, j);
     if (j == k - 1) break;
     const int reb = rebiorth_at(j + 1, c->opt.rebiorth);
     run(c, OV_KIND_UPDATE, 1, [&] { tsl_update(L, j, !reb, c->st); });
@@ -238,8 +268,79 @@ void forward_krylov(ov_context* c, Lat<R>& L) {
             [&] { proj_update(L, j, 0, L.r, L.s, L.vs, coef, ps == c->opt.passes - 1, c->st, ps > 0); });
       }
     }
+    inject_after_update(c, L, j);
   }
   launch_check();
+}
+
+// Run diagnostics (options.diagnostics) after a forward recurrence whose
+// coefficients are all valid: the sampled loss of biorthogonality of the stored
+// bases (dots of the last basis pair with every basis vector; not with
+// segments) and the Ritz values of each source's T_k on the host.  Returns
+// OV_ERR_SIGN_ILLPOSED when a Ritz value lies within 1e-14 ||T_k||_inf of the
+// imaginary axis (where sgn is undefined), OV_ERR_NOCONV when the eigenvalue
+// iteration fails, else OV_OK.
+template <typename R>
+int run_diagnostics(ov_context* c, const Lat<R>& L, bool segments, ov_tsl_info* info) {
+  const int k = L.k, nsrc = L.nsrc;
+  double loss = -1.0;
+  if (!segments) {
+    const int64_t nsb = (L.g.V + 127) / 128;
+    zd* coef = wsT<zd>(c, B_COEF, (int64_t)nsrc * 2 * k);
+    zd* cpart = wsT<zd>(c, B_CPART, (int64_t)nsrc * 2 * k * nsb);
+    run(c, OV_KIND_PROJ_DOTS, 2, [&] {
+      proj_dots(L, k - 1, 0, L.basis_v(0, k - 1), L.basis_w(0, k - 1), (int64_t)L.kcap * L.vs, coef, cpart,
+                c->st);
+    });
+    launch_check();
+    std::vector<zd> h((size_t)nsrc * 2 * k);
+    CK(cudaMemcpyAsync(h.data(), coef, sizeof(zd) * h.size(), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    loss = 0.0;
+    for (int src = 0; src < nsrc; ++src)
+      for (int i = 0; i < k; ++i)
+        for (int side = 0; side < 2; ++side) {
+          zd z = h[(size_t)src * 2 * k + 2 * i + side];
+          if (i == k - 1) z.re -= 1.0;
+          const double a = std::sqrt(z.re * z.re + z.im * z.im);
+          loss = std::isfinite(a) ? std::max(loss, a) : INFINITY;
+        }
+  }
+  std::vector<double> a(2 * (size_t)nsrc * k), b(2 * (size_t)nsrc * k), d((size_t)nsrc * k), e(2 * (size_t)k);
+  CK(cudaMemcpyAsync(a.data(), L.alpha, sizeof(double) * a.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(b.data(), L.beta, sizeof(double) * b.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(d.data(), L.delta, sizeof(double) * d.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double min_re = INFINITY, tnorm = 0.0;
+  int st = OV_OK;
+  for (int src = 0; src < nsrc; ++src) {
+    const double* as = a.data() + (size_t)src * 2 * k;
+    const double* bs = b.data() + (size_t)src * 2 * k;
+    const double* ds = d.data() + (size_t)src * k;
+    double nrm = 0.0;   // infinity norm: largest absolute row sum
+    for (int j = 0; j < k; ++j) {
+      double row = std::hypot(as[2 * j], as[2 * j + 1]);
+      if (j > 0) row += ds[j];
+      if (j + 1 < k) row += std::hypot(bs[2 * (j + 1)], bs[2 * (j + 1) + 1]);
+      nrm = std::max(nrm, row);
+    }
+    const int es = ov_tridiag_eigenvalues(k, as, bs, ds, e.data());
+    if (es != OV_OK) {
+      st = es;
+      continue;
+    }
+    double m = INFINITY;
+    for (int j = 0; j < k; ++j) m = std::min(m, std::fabs(e[2 * j]));
+    min_re = std::min(min_re, m);
+    tnorm = std::max(tnorm, nrm);
+    if (m <= 1e-14 * nrm && st == OV_OK) st = OV_ERR_SIGN_ILLPOSED;
+  }
+  if (info) {
+    info->biorth_loss = loss;
+    info->min_abs_re_ritz = min_re;
+    info->t_norm = tnorm;
+  }
+  return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -301,8 +402,10 @@ void seg_steps(ov_context* c, Lat<R>& L, int j0, int j1, bool next) {
   const int jend = next ? j1 + 1 : j1;
   for (int j = j0; j < jend; ++j) {
     run(c, OV_KIND_STENCIL_PAIR, 1, [&] { tsl_stencil(L, j, j < k - 1, c->st, c->tuned_pair[c->opt.precision]); });
+    inject_after_stencil(c, L, j);
     if (j == k - 1 || j == j1) break;
     run(c, OV_KIND_UPDATE, 1, [&] { tsl_update(L, j, true, c->st); });
+    inject_after_update(c, L, j);
   }
 }
 // pass 1: the recurrence over all segments, checkpointing each segment start
@@ -577,6 +680,10 @@ int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   c->last_nsrc = nsrc;
   if (info) info->k_reached = kr;
   if (st != OV_OK) return st;
+  if (c->opt.diagnostics) {
+    st = run_diagnostics(c, L, S > 0, info);
+    if (st != OV_OK) return st;
+  }
   zd* y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
   int iters = 0;
   st = sign_all(c, L, hsc, y, &iters);
@@ -641,6 +748,10 @@ int block_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, d
   c->last_nsrc = nsrc;
   if (info) info->k_reached = kr;
   if (st != OV_OK) return st;
+  if (c->opt.diagnostics) {
+    st = run_diagnostics(c, L, false, info);
+    if (st != OV_OK) return st;
+  }
   zd* y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
   int iters = 0;
   st = sign_all(c, L, hsc, y, &iters);
@@ -772,6 +883,10 @@ int vjp_forward(ov_context* c, const int32_t dims[4], const void* U, double mu, 
   c->last_nsrc = nsrc;
   if (info) info->k_reached = kr;
   if (st != OV_OK) return st;
+  if (c->opt.diagnostics) {
+    st = run_diagnostics(c, L, S > 0, info);
+    if (st != OV_OK) return st;
+  }
   const int64_t n = (int64_t)k * k;
   F.y = wsT<zd>(c, B_Y, (int64_t)nsrc * k);
   F.rec_inv = wsT<zd>(c, B_REC, (int64_t)nsrc * NREC * n);
@@ -1189,7 +1304,8 @@ int guarded(F&& f) {
 
 bool valid_options(const ov_options* o) {
   return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4 &&
-         o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0) && (o->dense == 0 || o->dense == 1);
+         o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0) && (o->dense == 0 || o->dense == 1) &&
+         (o->diagnostics == 0 || o->diagnostics == 1);
 }
 
 // x = V_k y from a forward state (a second pass over the segments if there are any)
@@ -1604,13 +1720,23 @@ int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, do
   });
 }
 
+int ov_debug_inject(ov_context* c, int32_t kind, int32_t step) {
+  if (!c || kind < OV_INJECT_NONE || kind > OV_INJECT_OOM || step < 0) return OV_ERR_INVALID_ARG;
+  c->inj_kind = kind;
+  c->inj_step = step;
+  return OV_OK;
+}
+
 const char* ov_strerror(int s) {
   switch (s) {
     case OV_OK: return "success";
     case OV_ERR_INVALID_ARG: return "invalid argument";
     case OV_ERR_OOM: return "device workspace allocation failed";
     case OV_ERR_BREAKDOWN: return "Lanczos breakdown (|omega| <= 1e-14 ||r|| ||s||)";
-    case OV_ERR_SIGN_ILLPOSED: return "k x k Newton sign iteration failed (singular or non-convergent)";
+    case OV_ERR_SIGN_ILLPOSED:
+      return "k x k sign ill-posed (singular or non-convergent Newton iterate, or a Ritz value on the "
+             "imaginary axis)";
+    case OV_ERR_NOCONV: return "the Ritz-value iteration of the run diagnostics did not converge";
     case OV_ERR_CUDA: return "CUDA runtime error";
     case OV_ERR_NONFINITE: return "non-finite recurrence coefficient";
     case OV_ERR_SCRATCH_LIMIT: return "problem too large for the fixed 32 MiB scratch of ov_apply_H_noalloc";

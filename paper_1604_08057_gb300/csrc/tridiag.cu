@@ -1,0 +1,116 @@
+// Eigenvalues of the TSL tridiagonal T_k on the host (the Ritz values), for the
+// run diagnostics: min |Re lambda(T_k)| tells how close the k x k sign problem
+// is to ill-posed (sgn is undefined on the imaginary axis, Sec. 2 Eq.
+// spectral_form).
+//
+// T_k has diagonal alpha_j, superdiagonal beta_{j+1} and subdiagonal delta_{j+1}
+// with |beta_{j+1}| = |delta_{j+1}| (delta = sqrt|omega|, beta = omega / delta).
+// A diagonal similarity with unimodular entries therefore turns it into the
+// complex-symmetric tridiagonal S with off-diagonal e_j = sqrt(beta_{j+1} delta_{j+1})
+// and the same eigenvalues, without any growth from the scaling.  S is reduced
+// by the implicit QL iteration with a Wilkinson-type shift (Bowdler, Martin,
+// Reinsch and Wilkinson, Numer. Math. 11 (1968) 293), run in complex arithmetic
+// with complex-orthogonal plane rotations (c^2 + s^2 = 1), which keep S complex
+// symmetric and tridiagonal (Cullum and Willoughby, "A QL procedure for
+// computing the eigenvalues of complex symmetric tridiagonal matrices", SIAM J.
+// Matrix Anal. Appl. 17 (1996) 83).  Each iteration costs O(k), the whole
+// spectrum O(k^2).  Complex-orthogonal rotations are not unitary: a rotation
+// whose normaliser sqrt(f^2 + g^2) nearly vanishes is reported as a failure
+// instead of being taken.
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "ov.h"
+
+namespace {
+
+using cx = std::complex<double>;
+
+// sqrt(a^2 + b^2) for complex a, b, scaled against overflow; the branch is
+// immaterial (it only flips the sign of a rotation)
+cx hyp(cx a, cx b) {
+  const double m = std::max(std::abs(a), std::abs(b));
+  if (m == 0.0) return cx(0.0, 0.0);
+  const cx x = a / m, y = b / m;
+  return m * std::sqrt(x * x + y * y);
+}
+
+// Eigenvalues of the complex-symmetric tridiagonal (d, e) in place (d), e[n-1] unused.
+// Returns false when the iteration does not converge or a rotation breaks down.
+bool ql_complex_symmetric(std::vector<cx>& d, std::vector<cx>& e) {
+  const int n = (int)d.size();
+  const double eps = 2.220446049250313e-16;
+  if (n <= 1) return true;
+  e[n - 1] = 0.0;
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    for (;;) {
+      // the first negligible off-diagonal entry at or after l splits the matrix
+      int m = l;
+      for (; m < n - 1; ++m) {
+        const double dd = std::abs(d[m]) + std::abs(d[m + 1]);
+        if (std::abs(e[m]) <= eps * dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 60) return false;
+      // shift: the eigenvalue of the leading 2 x 2 block [[d_l, e_l], [e_l, d_{l+1}]]
+      // nearer to d_l, expressed through g = (d_{l+1} - d_l) / (2 e_l)
+      cx g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      cx r = hyp(g, cx(1.0, 0.0));
+      const cx gp = (std::abs(g + r) >= std::abs(g - r)) ? g + r : g - r;
+      g = d[m] - d[l] + e[l] / gp;
+      if (iter == 20 || iter == 40) g = d[m] - d[l] + std::abs(e[l]) * cx(0.75, 0.25);   // exceptional shift
+      cx s(1.0, 0.0), c(1.0, 0.0), p(0.0, 0.0);
+      int i = m - 1;
+      for (; i >= l; --i) {
+        const cx f = s * e[i];
+        const cx b = c * e[i];
+        r = hyp(f, g);
+        e[i + 1] = r;
+        if (std::abs(r) <= 1e-300 + 1e-12 * (std::abs(f) + std::abs(g))) {
+          if (std::abs(f) == 0.0 && std::abs(g) == 0.0) {   // exact split: deflate and restart
+            d[i + 1] -= p;
+            e[m] = 0.0;
+            break;
+          }
+          return false;                                     // f = +-i g: the rotation breaks down
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        p = s * r;
+        d[i + 1] = g + p;
+        g = c * r - b;
+      }
+      if (i >= l) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  for (const cx& z : d)
+    if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" int ov_tridiag_eigenvalues(int32_t k, const double* alpha, const double* beta, const double* delta,
+                                      double* eig) {
+  if (k < 1 || !alpha || !delta || !eig || (k > 1 && !beta)) return OV_ERR_INVALID_ARG;
+  std::vector<cx> d(k), e(k, cx(0.0, 0.0));
+  for (int j = 0; j < k; ++j) d[j] = cx(alpha[2 * j], alpha[2 * j + 1]);
+  for (int j = 0; j + 1 < k; ++j) e[j] = std::sqrt(cx(beta[2 * (j + 1)], beta[2 * (j + 1) + 1]) * delta[j + 1]);
+  for (int j = 0; j < k; ++j)
+    if (!std::isfinite(d[j].real()) || !std::isfinite(d[j].imag()) || !std::isfinite(e[j].real()) ||
+        !std::isfinite(e[j].imag()))
+      return OV_ERR_NONFINITE;
+  if (!ql_complex_symmetric(d, e)) return OV_ERR_NOCONV;
+  for (int j = 0; j < k; ++j) {
+    eig[2 * j] = d[j].real();
+    eig[2 * j + 1] = d[j].imag();
+  }
+  return OV_OK;
+}

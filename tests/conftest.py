@@ -11,6 +11,27 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built extension")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    config.addinivalue_line("markers", "oracle_cases(*names): oracle references computed in background "
+                                       "processes (tests/oracle_jobs.py)")
+
+
+def pytest_collection_finish(session):
+    """Start the background oracle jobs of the selected tests before any of them runs,
+    so that they overlap with the rest of the session."""
+    names = []
+    for item in session.items:
+        m = item.get_closest_marker("oracle_cases")
+        if m:
+            names += [n for n in m.args if n not in names]
+    if names:
+        import oracle_jobs
+        oracle_jobs.submit(names)
+
+
+def pytest_sessionfinish(session, exitstatus):
+    mod = sys.modules.get("oracle_jobs")
+    if mod is not None:
+        mod.shutdown()
 
 
 @pytest.fixture(scope="session")

@@ -1,0 +1,137 @@
+"""Oracle references for the parity tests at sizes that reach the full-size code
+paths, computed in background processes while other tests run.
+
+Each case is one lattice, one physics point and one re-biorthogonalisation
+schedule; each source of a case is its own job (forward TSL and reverse-mode
+VJP of the FP64 oracle), so the jobs of all cases run in parallel on the host
+cores.  The pool uses the ``spawn`` start method: a process forked after the
+parent has initialised CUDA can hang.  Only ``oracle/`` and the input
+generator run in the children.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import dataclasses
+import multiprocessing as mp
+import os
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Case:
+    dims: tuple
+    eps: float
+    seed: int
+    mu: float
+    m_w: float
+    k: int
+    rebiorth: int
+    passes: int
+    nsrc: int
+
+
+# Lattices of at least 152 blocks of 128 sites (19 456 sites) run the force
+# contraction's single-pass branch, the one the 14x14^3 and 6x18^3 workloads
+# take; k = 130 at period 60 includes the projection steps 59, 60, 119 and 120.
+# The 4x4^3 case at k = 800 runs the k x k stage at the benchmark's k (the
+# cooperative inversion over 25 row blocks, the dense Frechet iterations); at
+# n = 3072 and k = 800 projections every 60 steps leave the map chaotic (its
+# rounding floor in dU is O(1)), every 20 steps well conditioned.  The 8x8^3
+# case is the four-source workload at its own k.
+CASES = {
+    "w12_mw1": Case((12, 12, 12, 12), 0.2, 1012, 0.3, -1.0, 130, 60, 1, 2),
+    "w12_mw2": Case((12, 12, 12, 12), 0.2, 1012, 0.3, -2.0, 130, 60, 1, 2),
+    "k800_mw1": Case((4, 4, 4, 4), 0.3, 3, 0.3, -1.0, 800, 20, 1, 1),
+    "c1_8": Case((8, 8, 8, 8), 0.25, 1001, 0.2, -2.0, 400, 60, 1, 4),
+}
+
+
+def case_inputs(case: Case):
+    """(links, sources, cotangents) of a case, drawn in the order links, sources, cotangents."""
+    from paper_1604_08057_gb300 import inputs
+    rng = np.random.default_rng(case.seed)
+    u = inputs.su3_links(case.dims, case.eps, rng)
+    b = inputs.gaussian_spinors(case.dims, case.nsrc, rng)
+    xbar = inputs.gaussian_spinors(case.dims, case.nsrc, rng)
+    return u, b, xbar
+
+
+def oracle_case_source(name: str, src: int, emulate: bool = False):
+    """Oracle forward result x and (dU, dmu) of one source of a case (runs in a
+    child); with ``emulate``, the oracle's FP32-vector emulation."""
+    from oracle import tsl, vjp
+    case = CASES[name]
+    u, b, xbar = case_inputs(case)
+    fwd = tsl.tsl_forward(u, b[src], case.mu, case.m_w, case.k, rebiorth=case.rebiorth, passes=case.passes,
+                          emulate_fp32=emulate)
+    du, dmu, _ = vjp.tsl_vjp(u, b[src], case.mu, case.m_w, case.k, xbar[src], rebiorth=case.rebiorth,
+                             passes=case.passes, fwd=fwd, emulate_fp32=emulate)
+    return fwd.x, du, dmu
+
+
+_pool = None
+_jobs = {}
+
+
+def _parse(name: str):
+    """'case' or 'case:fp32' (the FP32 emulation) -> (case name, emulate)."""
+    base, _, kind = name.partition(":")
+    return base, kind == "fp32"
+
+
+def submit(names) -> None:
+    """Start the jobs of the named cases (once each); 'case:fp32' names the
+    oracle's FP32-vector emulation of a case."""
+    global _pool
+    todo = [(n, s) for n in names for s in range(CASES[_parse(n)[0]].nsrc) if (n, s) not in _jobs]
+    if not todo:
+        return
+    if _pool is None:
+        workers = max(1, min(len(todo), (os.cpu_count() or 2) - 1, 12))
+        # one BLAS thread per child: the jobs themselves are the parallelism
+        saved = {v: os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"
+        try:
+            _pool = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+            # children start here, with the environment above
+            for n, s in todo:
+                _jobs[(n, s)] = _pool.submit(oracle_case_source, *_split(n, s))
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
+        return
+    for n, s in todo:
+        _jobs[(n, s)] = _pool.submit(oracle_case_source, *_split(n, s))
+
+
+def _split(name: str, src: int):
+    base, emulate = _parse(name)
+    return base, src, emulate
+
+
+def shutdown() -> None:
+    """Cancel pending jobs and stop the children (a failing run must not wait for them)."""
+    global _pool
+    if _pool is None:
+        return
+    procs = list(getattr(_pool, "_processes", {}).values())
+    _pool.shutdown(wait=False, cancel_futures=True)
+    for p in procs:
+        if p.is_alive():
+            p.terminate()
+    for p in procs:
+        p.join(timeout=10)
+    _pool = None
+    _jobs.clear()
+
+
+def result(name: str, src: int, timeout: float = 3600.0):
+    """(x, dU, dmu) of the oracle for one source of a case ('case' or
+    'case:fp32'), waiting for its job."""
+    submit([name])
+    return _jobs[(name, src)].result(timeout=timeout)

@@ -8,8 +8,9 @@ at any size:
   map along a direction supported on 16 random links, and along mu;
 * a batched call over several sources equals the per-source calls;
 * sampled outputs of H psi against the oracle's operator at those sites;
-* the benchmark's period (60) against a period of 20: the same x to 1e-8, dU
-  to 2e-3 and the same error estimate eps_A.
+* the benchmark's period (60) against projections at every step: x, dU and
+  dmu each within its own bound, the same error estimate eps_A, and a small
+  sampled loss of biorthogonality.
 """
 import numpy as np
 import pytest
@@ -101,18 +102,29 @@ def test_apply_h_sampled_sites_full_size(data):
         assert np.abs(got[site] - want[site]).max() <= 1e-13 * np.abs(want).max()
 
 
-def test_period_60_agrees_with_period_20(data):
-    """At this point every period from 10 to 100 gives x within ~1e-9 and dU within
-    ~4e-4 of the result with re-biorthogonalisation at every step, with the same eps_A
-    (the Krylov truncation error, ~1e-2, dominates); the benchmark's period against 20."""
+def test_period_60_against_projections_at_every_step(data):
+    """The benchmark's schedule (projections every 60 steps, one pass) against
+    projections at every step (P = 1, the most the method can do), per result:
+    x within 1e-8 (measured 1.0e-9), dU within 5e-4 (measured 9.9e-5) and dmu
+    within 5% (measured 2.0%: at k = 800 the mu-derivative of the k-step map moves
+    by several per cent under any change of rounding order, see the mu check
+    above), the same error estimate eps_A; with the run diagnostics on, the
+    sampled loss of biorthogonality of the P = 60 bases stays far below O(1)
+    (a period whose bases lose biorthogonality shows it there)."""
     u, b, xbar = data
     ut, bt, xt = (torch.tensor(a, device="cuda") for a in (u, b[0], xbar[0]))
     out = {}
-    for period in (20, 60):
-        du, dmu, x = binding.tsl_sign_vjp(ut, WL.mu, WL.m_w, bt, WL.k, xt, "fp64", period, 1)
+    for period in (1, 60):
+        binding.diagnostics_mode(True, "fp64", period, 1)
+        try:
+            du, dmu, x, info = binding.tsl_sign_vjp(ut, WL.mu, WL.m_w, bt, WL.k, xt, "fp64", period, 1,
+                                                    return_info=True)
+        finally:
+            binding.diagnostics_mode(False, "fp64", period, 1)
         eps = float(np.ravel(binding.tsl_eps(ut, WL.mu, WL.m_w, bt, WL.k, "fp64", period, 1))[0])
-        out[period] = (x, du, eps)
+        out[period] = (x, du, dmu, eps, info["biorth_loss"])
     rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
-    assert rel(out[60][0], out[20][0]) <= 1e-8
-    assert rel(out[60][1], out[20][1]) <= 2e-3
-    assert abs(out[60][2] - out[20][2]) <= 1e-6 * out[20][2]
+    errs = (rel(out[60][0], out[1][0]), rel(out[60][1], out[1][1]), abs(out[60][2] - out[1][2]) / abs(out[1][2]),
+            abs(out[60][3] - out[1][3]) / out[1][3], out[1][4], out[60][4])
+    assert errs[0] <= 1e-8 and errs[1] <= 5e-4 and errs[2] <= 5e-2 and errs[3] <= 1e-6, errs
+    assert errs[4] <= 1e-10 and errs[5] <= 1e-3, errs

@@ -124,3 +124,24 @@ def test_vjp_matches_torch_autograd_dense():
     gu = ut.grad.numpy()
     assert np.linalg.norm(gu - du) <= 1e-8 * np.linalg.norm(du)
     assert abs(mut.grad.item() - dmu) <= 1e-8 * abs(dmu)
+
+
+def test_vjp_fp32_emulation_is_at_the_fp32_level():
+    """The FP32-vector emulation rounds the reverse sweep as well as the forward one:
+    at a well-conditioned point its gradient differs from the FP64 gradient by
+    roughly the FP32 rounding unit (6e-8) times a modest amplification -- neither
+    zero (nothing rounded) nor O(1) (a dropped term)."""
+    dims = (3, 3, 3, 3)
+    u, b, xbar, _ = _setup(dims, 0.3, 43)
+    mu, m_w, k = 0.3, -1.0, 40
+    du, dmu, fwd = vjp.tsl_vjp(u, b, mu, m_w, k, xbar)
+    du32, dmu32, fwd32 = vjp.tsl_vjp(u, b, mu, m_w, k, xbar, emulate_fp32=True)
+    rel_x = np.linalg.norm(fwd32.x - fwd.x) / np.linalg.norm(fwd.x)
+    rel_du = np.linalg.norm(du32 - du) / np.linalg.norm(du)
+    assert 1e-9 < rel_x < 1e-5, rel_x
+    assert 1e-9 < rel_du < 1e-4, rel_du
+    assert abs(dmu32 - dmu) < 1e-4 * abs(dmu)
+    # the reverse sweep itself is rounded: the same FP32 forward with an FP64 reverse
+    # sweep gives a different gradient
+    du_mixed, _, _ = vjp.tsl_vjp(u, b, mu, m_w, k, xbar, fwd=fwd32)
+    assert np.linalg.norm(du_mixed - du32) > 1e-10 * np.linalg.norm(du)

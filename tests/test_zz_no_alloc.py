@@ -63,3 +63,11 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     st, _ = _call(f, u, 0.1, -1.0, psi, 0)
     assert st == SCRATCH_LIMIT
     assert b"scratch" in lib.ov_strerror(st)
+    # more sources than any call accepts: rejected before the scratch bound is computed
+    # (the arrays are never read: the check comes first)
+    small = torch.zeros((2, 2, 2, 2, 4, 3, 3), dtype=torch.complex128, device="cuda")
+    one = torch.zeros((1, 2, 2, 2, 2, 4, 3), dtype=torch.complex128, device="cuda")
+    dims4 = (ctypes.c_int32 * 4)(2, 2, 2, 2)
+    st = f(dims4, ctypes.c_void_p(small.data_ptr()), 0.1, -1.0, 4097, ctypes.c_void_p(one.data_ptr()),
+           ctypes.c_void_p(one.data_ptr()), 0, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == -1
