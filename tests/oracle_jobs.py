@@ -38,12 +38,13 @@ class Case:
 # cooperative inversion over 25 row blocks, the dense Frechet iterations); at
 # n = 3072 and k = 800 projections every 60 steps leave the map chaotic (its
 # rounding floor in dU is O(1)), every 20 steps well conditioned.  The 8x8^3
-# case is the four-source workload at its own k.
+# case is the four-source workload at its own k, with projections every 20
+# steps (every 60 leaves its map chaotic as well: dU floor 0.3).
 CASES = {
     "w12_mw1": Case((12, 12, 12, 12), 0.2, 1012, 0.3, -1.0, 130, 60, 1, 2),
     "w12_mw2": Case((12, 12, 12, 12), 0.2, 1012, 0.3, -2.0, 130, 60, 1, 2),
     "k800_mw1": Case((4, 4, 4, 4), 0.3, 3, 0.3, -1.0, 800, 20, 1, 1),
-    "c1_8": Case((8, 8, 8, 8), 0.25, 1001, 0.2, -2.0, 400, 60, 1, 4),
+    "c1_8": Case((8, 8, 8, 8), 0.25, 1001, 0.2, -2.0, 400, 20, 1, 4),
 }
 
 

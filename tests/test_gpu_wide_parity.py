@@ -13,7 +13,9 @@ full-size workloads, element by element through the C ABI.
   leaves the k-step map chaotic (oracle rounding floor of dU ~1), so this case
   uses 20 (floors x 1.8e-13, dU 5.0e-10, dmu 3.4e-10).
 * 8x8^3 with four sources at k = 400 (the four-source workload's own lattice,
-  couplings and k; period 60, one pass).
+  couplings and k; period 20, one pass).  This map is ill-conditioned at any
+  period: the oracle's rounding floor of dU is 0.3 at period 60, 4.2e-4 at 20
+  and 1.6e-4 at 10.
 
 Bars (relative 2-norm for x and dU, relative for dmu).  At m_w = -1 the map is
 well conditioned (oracle rounding floors 6e-15 for x, 2e-12 for dU, 2e-11 for
@@ -21,7 +23,7 @@ dmu at 12x12^3) and the bars are 1e-11 (x) and 1e-9 (dU, dmu).  At m_w = -2 the
 floor was measured with the oracle itself, by perturbing b by 1e-16 relative
 (which any change of summation order does); the bar is 10x that floor:
   12x12^3, k = 130: floor x 8.2e-12, dU 3.8e-8, dmu 9.1e-8 -> 1e-10, 4e-7, 1e-6
-  8x8^3,   k = 400: floor x 2.7e-11, dU 4.2e-7, dmu 1.1e-6 -> 3e-10, 5e-6, 1.2e-5
+  8x8^3,   k = 400: floor x 1.8e-8, dU 4.2e-4, dmu 1.3e-3 -> 2e-7, 5e-3, 1.5e-2
 
 The oracle references run in background processes (tests/oracle_jobs.py),
 started when the session's tests have been collected.
@@ -96,7 +98,7 @@ def test_k800_sign_and_frechet_stage(dense):
 
 @pytest.mark.oracle_cases("c1_8")
 def test_four_sources_8x8x8x8_k400():
-    gpu_vs_oracle("c1_8", (3e-10, 5e-6, 1.2e-5))
+    gpu_vs_oracle("c1_8", (2e-7, 5e-3, 1.5e-2))
 
 
 # ---------------------------------------------------------------------------
