@@ -303,7 +303,14 @@ def run_ours(args, rank, world, local_rank):
                     "fp64_gemm_measured_tflops": round(fp64_peak(dev) / 1e3, 3),
                     "hbm_view": {"achieved_GB_s": round(gbs, 1), "peak": hbm, "frac": round(gbs / hbm, 3)},
                     **per_launch}
-        if dom == "proj_dots":
+        if dom == "rev_stencil":
+            # ncu: DRAM bytes of k_rev_stencil launches at 14x14^3, k = 120 = 0.845 x their
+            # algorithmic bytes; launches differ only in how many fields they stream
+            roofline["traffic"] = int(REV_STENCIL_TRAFFIC_RATIO * per_launch["algorithmic_bytes_per_launch"])
+            roofline["traffic_source"] = ("ncu dram bytes of two k_rev_stencil launches at 14x14^3, k=120 "
+                                          f"(ratio {REV_STENCIL_TRAFFIC_RATIO} to algorithmic), scaled to this "
+                                          "launch average")
+        elif dom == "proj_dots":
             # ncu: DRAM bytes of a two-sided k_proj_dots launch = 1.050 x its algorithmic
             # bytes (14x14^3, k = 120, nb = 101); traffic grows with the fields streamed
             roofline["traffic"] = int(PROJ_DOTS_TRAFFIC_RATIO * per_launch["algorithmic_bytes_per_launch"])
@@ -345,6 +352,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 PROJ_DOTS_TRAFFIC_RATIO = 1.050
+REV_STENCIL_TRAFFIC_RATIO = 0.845
 
 
 def hbm_peak():

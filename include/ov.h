@@ -86,7 +86,15 @@ typedef struct {
                         * ov_tridiag_eigenvalues), and return OV_ERR_SIGN_ILLPOSED, with info
                         * filled, when min |Re lambda(T_k)| <= 1e-14 ||T_k||_inf (sgn is not
                         * defined on the imaginary axis, Sec. 2 Eq. spectral_form). */
-  int32_t reserved[2];
+  int32_t newton;      /* rules of the scaled Newton iteration for the k x k sign (Higham,
+                        * "Functions of Matrices", ch. 5; the Frechet adjoint reuses the forward's
+                        * scalings): 0 (default): Frobenius-norm scaling
+                        * g = (||X^{-1}||_F / ||X||_F)^{1/2} and a stop one iteration after the
+                        * quadratic model s_{i+1} ~ s_i^3 / s_{i-1}^2 predicts a relative step
+                        * <= 1e-12; 1: determinant scaling |det X|^{-1/k} and a stop when the
+                        * relative step is <= 1e-14 or no longer halves.  Scaling ends once the
+                        * step is below 1e-2 in both. */
+  int32_t reserved[1];
 } ov_options;
 
 typedef struct {

@@ -35,7 +35,7 @@ class OVError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("dense", ctypes.c_int32),
-                ("diagnostics", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("diagnostics", ctypes.c_int32), ("newton", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class TuneReport(ctypes.Structure):
@@ -137,15 +137,15 @@ def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=
     return _contexts[key]
 
 
-_extra = {}   # per cached context: the options not in its key (dense, diagnostics)
+_extra = {}   # per cached context: the options not in its key (dense, diagnostics, newton)
 
 
 def _set_extra(precision, rebiorth, passes, segment, **kw):
     ctx = context(precision, rebiorth, passes, segment=segment)
     key = (precision, rebiorth, passes, segment, ctx.value)
-    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0})
+    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0, "newton": 0})
     ex.update({k: int(v) for k, v in kw.items()})
-    opt = Options(_PREC[precision], rebiorth, passes, segment, ex["dense"], ex["diagnostics"])
+    opt = Options(_PREC[precision], rebiorth, passes, segment, ex["dense"], ex["diagnostics"], ex["newton"])
     _check(load().ov_context_set_options(ctx, ctypes.byref(opt)), "ov_context_set_options")
     return ctx
 
@@ -161,6 +161,12 @@ def diagnostics_mode(on: bool, precision: str = "fp64", rebiorth: int = 1, passe
     """Run diagnostics (biorthogonality loss, Ritz values, ill-posed sign check) on the
     cached context for these options; results appear in the calls' info."""
     _set_extra(precision, rebiorth, passes, segment, diagnostics=on)
+
+
+def newton_rules(rules: str, precision: str = "fp64", rebiorth: int = 1, passes: int = 2, segment: int = 0):
+    """Rules of the k x k Newton sign on the cached context: "norm" (Frobenius-norm
+    scaling, predicted stop; the default) or "det" (determinant scaling, stagnation stop)."""
+    _set_extra(precision, rebiorth, passes, segment, newton={"norm": 0, "det": 1}[rules])
 
 
 def debug_inject(kind: str, step: int = 0, precision: str = "fp64", rebiorth: int = 1, passes: int = 2,

@@ -853,6 +853,45 @@ __global__ void __launch_bounds__(256) k_newton_combine(const zd* __restrict__ x
     }
   }
 }
+// Frobenius-norm scaling of the Newton step (Higham, "Functions of Matrices",
+// ch. 5): g = (||X^{-1}||_F / ||X||_F)^{1/2}.  The combine kernel takes its scale
+// as exp(-ld / k) (the determinant form), so the norm form is written as the
+// equivalent ld = -(k / 4) log(||X^{-1}||_F^2 / ||X||_F^2).  Per problem p
+// (blockIdx.y): NSB blocks sum |x|^2 and |xi|^2 over strided entries, the last
+// block to arrive adds the partials in block order (deterministic).
+constexpr int NSB = 64;
+__global__ void __launch_bounds__(256) k_norm_scale(const zd* __restrict__ x, const zd* __restrict__ xi, int64_t n,
+                                                    int k, double* ld, int ld_stride, zd* part, unsigned* cnt,
+                                                    const int* __restrict__ act) {
+  __shared__ zd scratch[32];
+  const int p = blockIdx.y;
+  if (act && !act[p]) return;
+  x += p * n;
+  xi += p * n;
+  part += (int64_t)p * NSB;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    a += norm2(x[i]);
+    b += norm2(xi[i]);
+  }
+  zd v[1] = {mk(a, b)};
+  block_sum<1>(v, scratch);
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+  if (arrive_last(cnt + p, gridDim.x)) {
+    if (threadIdx.x == 0) {
+      zd t = mk(0.0, 0.0);
+      for (unsigned q = 0; q < gridDim.x; ++q) t = t + ld_cg(part + q);
+      ld[(int64_t)p * ld_stride] = -0.25 * k * log(t.im / t.re);
+    }
+  }
+}
+void dense_norm_scale(const zd* x, const zd* xi, int k, int nb, const int* act, double* ld, int ld_stride, zd* part,
+                      unsigned* cnt, cudaStream_t st) {
+  const int64_t n = (int64_t)k * k;
+  const unsigned g = std::min<unsigned>(NSB, nblk(n, 256));
+  k_norm_scale<<<dim3(g, nb), 256, 0, st>>>(x, xi, n, k, ld, ld_stride, part, cnt, act);
+}
+
 void dense_newton_combine(const zd* x, const zd* xi, zd* xn, int k, const double* logdet, int scaling,
                           double s, double w, double* stats, zd* part, unsigned* cnt, cudaStream_t st) {
   const int64_t n = (int64_t)k * k;

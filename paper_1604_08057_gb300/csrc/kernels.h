@@ -177,6 +177,11 @@ void dense_newton_combine_batch(const zd* X, const zd* Xi, zd* Xn, int k, int nb
                                 const double* logdet, int ld_stride, const int* scal, int scal_stride, double s,
                                 double w, double* stats, zd* part, int64_t part_stride, unsigned* cnt,
                                 cudaStream_t st);
+// Frobenius-norm Newton scaling g = (||Xi||_F / ||X||_F)^{1/2} written as the equivalent
+// ld[p * ld_stride] = -(k/4) log(||Xi||_F^2 / ||X||_F^2) (so that exp(-ld / k) = g), for
+// nb problems at stride k*k; part: 64 zd and cnt: one ticket (zero) per problem.
+void dense_norm_scale(const zd* X, const zd* Xi, int k, int nb, const int* act, double* ld, int ld_stride, zd* part,
+                      unsigned* cnt, cudaStream_t st);
 void dense_set_column0(zd* E, const zd* gy, int64_t gy_stride, double beta0, int k, cudaStream_t st);
 void dense_extract_y(const zd* F, double beta0, int k, zd* y, cudaStream_t st);
 void dense_extract_tri(const zd* E, int k, zd* ga, zd* gb, double* gd, cudaStream_t st);

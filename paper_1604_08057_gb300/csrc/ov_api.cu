@@ -21,7 +21,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, NBUF
 };
 
 struct Status {
@@ -482,10 +482,13 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
   unsigned long long* keys = wsT<unsigned long long>(c, B_PROW, (int64_t)(k + 1) * GJ_KEY_SLOTS);
   zd* w0 = wsT<zd>(c, B_W0, n);
   zd* w1 = wsT<zd>(c, B_W1, n);
-  double* dstat = wsT<double>(c, B_DSTAT, 4);   // [0] diff^2, [1] norm^2, [2] log|det|
+  double* dstat = wsT<double>(c, B_DSTAT, 4);   // [0] diff^2, [1] norm^2, [2] log|det| (or its norm form)
   zd* dpart = wsT<zd>(c, B_DPART, (n + 255) / 256 + 64);
   unsigned* dcnt = wsT<unsigned>(c, B_DCNT, 4);
-  bool scaling = true;
+  zd* npart = wsT<zd>(c, B_NSPART, 64);
+  unsigned* ncnt = wsT<unsigned>(c, B_NSCNT, 1);
+  const bool norm_rules = c->opt.newton == 0;
+  bool scaling = true, last = false;
   double prev = INFINITY;
   int cur = 0, it = 0;
   double hs[3];
@@ -495,6 +498,8 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
       c->launches += dense_inverse(a[cur], ai, w0, w1, k, 1, nullptr, ipiv, used, keys, dstat + 2, 0, err_dev,
                                    c->opt.dense, c->st);
     });
+    if (norm_rules && scaling)
+      run(c, OV_KIND_DENSE, 1, [&] { dense_norm_scale(a[cur], ai, k, 1, nullptr, dstat + 2, 0, npart, ncnt, c->st); });
     if (rec) {
       const int slot = it - 1;
       if (slot < rec->cap) {
@@ -525,8 +530,10 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
     cur = 1 - cur;
     const double step = std::sqrt(hs[0] / hs[1]);
     if (!std::isfinite(step)) return -1;
-    if (step <= 1e-14) break;
+    if (last || step <= 1e-14) break;
+    const bool was_unscaled = !scaling;
     if (step < 1e-2) scaling = false;
+    if (norm_rules && was_unscaled && step * step * step / (prev * prev) <= 1e-12) last = true;
     if (it > 6 && !scaling && step >= 0.5 * prev) break;
     prev = step;
   }
@@ -556,7 +563,10 @@ int newton_batch(ov_context* c, zd* a[2], int k, int nb, int* err_dev, std::vect
   unsigned* dcnt = wsT<unsigned>(c, B_DCNT, 4 * (int64_t)nb);
   int* act_dev = wsT<int>(c, B_ACT, nb);
   int* scal_dev = wsT<int>(c, B_SCAL, nb);
-  std::vector<int> act(nb, 1), scaling(nb, 1);
+  zd* npart = wsT<zd>(c, B_NSPART, 64 * (int64_t)nb);
+  unsigned* ncnt = wsT<unsigned>(c, B_NSCNT, nb);
+  const bool norm_rules = c->opt.newton == 0;
+  std::vector<int> act(nb, 1), scaling(nb, 1), last(nb, 0);
   std::vector<double> prev(nb, INFINITY), hs(4 * (size_t)nb);
   which.assign(nb, 0);
   iters.assign(nb, 0);
@@ -572,6 +582,8 @@ int newton_batch(ov_context* c, zd* a[2], int k, int nb, int* err_dev, std::vect
       c->launches += dense_inverse(a[cur], ai, w0, w1, k, nb, act_dev, ipiv, used, keys, dstat + 2, 4, err_dev,
                                    c->opt.dense, c->st);
     });
+    if (norm_rules && std::find(scaling.begin(), scaling.end(), 1) != scaling.end())
+      run(c, OV_KIND_DENSE, 1, [&] { dense_norm_scale(a[cur], ai, k, nb, act_dev, dstat + 2, 4, npart, ncnt, c->st); });
     if (rec_inv) {
       const int slot = it - 1;
       for (int p = 0; p < nb; ++p) {
@@ -603,11 +615,13 @@ int newton_batch(ov_context* c, zd* a[2], int k, int nb, int* err_dev, std::vect
       which[p] = cur;
       itmax = std::max(itmax, it);
       if (!std::isfinite(step)) return -1;
-      if (step <= 1e-14) {
+      if (last[p] || step <= 1e-14) {
         act[p] = 0;
         continue;
       }
+      const bool was_unscaled = !scaling[p];
       if (step < 1e-2) scaling[p] = 0;
+      if (norm_rules && was_unscaled && step * step * step / (prev[p] * prev[p]) <= 1e-12) last[p] = 1;
       if (it > 6 && !scaling[p] && step >= 0.5 * prev[p]) {
         act[p] = 0;
         continue;
@@ -1305,7 +1319,7 @@ int guarded(F&& f) {
 bool valid_options(const ov_options* o) {
   return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4 &&
          o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0) && (o->dense == 0 || o->dense == 1) &&
-         (o->diagnostics == 0 || o->diagnostics == 1);
+         (o->diagnostics == 0 || o->diagnostics == 1) && (o->newton == 0 || o->newton == 1);
 }
 
 // x = V_k y from a forward state (a second pass over the segments if there are any)

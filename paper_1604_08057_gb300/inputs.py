@@ -23,7 +23,7 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-__all__ = ["gell_mann", "su3_links", "gaussian_spinors", "Workload", "WORKLOADS",
+__all__ = ["gell_mann", "su3_links", "gaussian_spinors", "z2_noise", "Workload", "WORKLOADS",
            "make_inputs", "n_sites", "lattice_shape"]
 
 
@@ -86,6 +86,14 @@ def gaussian_spinors(dims, nsrc: int, rng: np.random.Generator) -> np.ndarray:
     re = rng.standard_normal(shape)
     im = rng.standard_normal(shape)
     return (re + 1j * im) / np.sqrt(2.0)
+
+
+def z2_noise(dims, n: int, rng: np.random.Generator) -> np.ndarray:
+    """n Z2 noise vectors: every spinor component +1 or -1 with equal probability
+    (real), so that the mean of eta eta^dagger is the identity.  Shape
+    (n, Nt, Nz, Ny, Nx, 4, 3), complex128."""
+    shape = (n,) + lattice_shape(dims) + (4, 3)
+    return (2.0 * rng.integers(0, 2, size=shape) - 1.0).astype(np.complex128)
 
 
 @dataclasses.dataclass(frozen=True)
