@@ -346,6 +346,7 @@ def run_ours(args, rank, world, local_rank):
         out["mixed_path"] = mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar)
         out["schedule_compare"] = schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x)
         out["diagnostics"] = diagnostics_leg(args, ut, bt, xt, wl, k, ms_total / args.steps)
+        out["basis_in_host_memory"] = host_basis_leg(args, ut, bt, xt, wl, k, du, dmu, x)
         if world == 1:
             out["cpu_baseline"], out["parity"] = cpu_leg(args, k, ut)
     return out
@@ -428,6 +429,28 @@ def schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x, periods=(20,)):
         except RuntimeError as exc:   # e.g. device memory: the headline line must still print
             res[f"P={period}"] = f"error: {exc}"
     return res
+
+
+def host_basis_leg(args, ut, bt, xt, wl, k, du, dmu, x):
+    """The headline call with the Krylov bases in pinned host memory (read over the
+    CPU-GPU link instead of HBM): seconds per call and whether the results equal
+    the headline's bit for bit."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    opts = (args.precision, args.rebiorth, args.passes)
+    binding.basis_memory("host", *opts, segment=args.segment)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        du2, dmu2, x2 = binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, *opts, segment=args.segment)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return {"s_per_call": round(dt, 4), "basis_bytes": 2 * k * 24 * 8 * wl.volume,
+                "identical_to_headline": bool(torch.equal(du2, du) and torch.equal(x2, x) and dmu2 == dmu)}
+    except (binding.OVError, RuntimeError) as exc:
+        return {"error": str(exc)}
+    finally:
+        binding.basis_memory("device", *opts, segment=args.segment)
 
 
 def diagnostics_leg(args, ut, bt, xt, wl, k, ms_step):

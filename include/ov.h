@@ -50,7 +50,8 @@ extern "C" {
 #define OV_ERR_SCRATCH_LIMIT  -7  /* the problem does not fit the fixed scratch of ov_apply_H_noalloc */
 #define OV_ERR_TIMEOUT        -8  /* a device-side wait between blocks ran past its limit (2 s); the
                                      blocks stop and the context stays usable */
-#define OV_ERR_NOCONV         -9  /* the eigenvalue iteration of the Ritz diagnostic did not converge */
+#define OV_ERR_NOCONV         -9  /* an iteration did not converge: the Ritz values of the run
+                                     diagnostics, or ov_overlap_solve within maxit */
 
 /* Precision of lattice vectors, links and stencil arithmetic.
  * OV_FP64 : everything in FP64.
@@ -94,7 +95,11 @@ typedef struct {
                         * <= 1e-12; 1: determinant scaling |det X|^{-1/k} and a stop when the
                         * relative step is <= 1e-14 or no longer halves.  Scaling ends once the
                         * step is below 1e-2 in both. */
-  int32_t reserved[1];
+  int32_t basis_memory; /* where the Krylov bases V_k, W_k live: 0 (default) device memory;
+                        * 1 pinned host memory mapped into the device address space, read and
+                        * written by the kernels over the CPU-GPU link (NVLink-C2C on a GB300),
+                        * for bases larger than device memory.  Same kernels and results, bit
+                        * for bit, with any re-biorthogonalisation schedule. */
 } ov_options;
 
 typedef struct {
@@ -209,7 +214,8 @@ typedef struct {
   int32_t apply_variant;    /* chosen variant of the ov_apply_H stencil */
   int32_t pair_variant;     /* chosen variant of the TSL stencil pair */
   int32_t n_apply, n_pair;  /* number of variants timed */
-  float apply_us[16];       /* device microseconds per launch, per variant */
+  float apply_us[16];       /* device microseconds per launch, per variant (apply variants 9, 10,
+                               11 stage 1, 2 or 4 z-planes of the FP32 input in shared memory) */
   float pair_us[16];
 } ov_tune_report;
 int ov_autotune(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
@@ -327,6 +333,48 @@ int64_t ov_launch_count(ov_context *ctx);
 #define OV_NOALLOC_SCRATCH_BYTES (32u << 20)
 int ov_apply_H_noalloc(const int32_t dims[4], const void *U, double mu, double m_w, int32_t nsrc,
                        const void *in, void *out, int32_t dagger, void *stream);
+
+/* Overlap Dirac operator (Sec. 1, Eq. overlap, lattice spacing 1):
+ *   dagger = 0: out = D_ov b = b + gamma5 sgn(H(mu)) b
+ *   dagger = 1: out = D_ov^dagger b = b + sgn(H(-mu)) gamma5 b
+ * (H(mu)^dagger = H(-mu) by gamma5-hermiticity of Eq. WD_op; sgn(H)^dagger =
+ * sgn(H^dagger) since sgn(lambda) = sgn(Re lambda) is real), the sign applied
+ * by the k-step TSL of ov_tsl_sign with the context's options.  b and out:
+ * nsrc spinor fields (device, complex128, user layout); out may equal b.
+ * info as ov_tsl_sign (of the TSL run).  Errors as ov_tsl_sign. */
+int ov_overlap_apply(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                     int32_t nsrc, const void *b, int32_t k, int32_t dagger, void *out, ov_tsl_info *info);
+
+/* Solve D_ov x = rhs (dagger = 0) or D_ov^dagger x = rhs (dagger = 1) for each of
+ * nsrc right-hand sides by restarted GMRES(30) from x = 0, each operator
+ * application an ov_overlap_apply with k TSL steps.  The k-step TSL is linear in
+ * its vector only up to its approximation error, which bounds the attainable
+ * residual.  Stops when ||rhs - D_ov x|| <= tol ||rhs|| (the true residual,
+ * recomputed at every restart) or after maxit applications; *iters (largest
+ * count over the sources) and *resid (largest final relative residual) may be
+ * NULL.  Returns OV_ERR_NOCONV when a source ends above tol (x holds the last
+ * iterate), else the errors of ov_tsl_sign. */
+int ov_overlap_solve(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                     int32_t nsrc, const void *rhs, int32_t k, int32_t dagger, double tol, int32_t maxit,
+                     void *x, int32_t *iters, double *resid);
+
+/* Stochastic estimator of the U(1) vector currents (Sec. 4.3, Eq. lat_vec_cur)
+ *   j_{x,nu} = Tr(D_ov^{-1} dD_ov/dTheta_{x,nu})
+ * over nnoise noise vectors eta (device, nnoise spinor fields, complex128; Z2
+ * noise in the paper): for each, chi = D_ov^{-dagger} eta by ov_overlap_solve
+ * (tol, maxit), then eta^dagger D_ov^{-1} (dD_ov/dTheta) eta =
+ * <gamma5 chi, d(sgn(H) eta)/dTheta> for all links at once from one forward TSL
+ * and two reverse sweeps (the VJP of ov_tsl_sign_vjp with cotangents gamma5 chi
+ * and i gamma5 chi), where Theta enters as U_nu(x) -> e^{i Theta_{x,nu}} U_nu(x).
+ * j: device array [V][4] of complex128 (direction order x, y, z, t), the mean
+ * over the noise vectors.  trace_mu (host double[2], may be NULL): the same
+ * estimator of Tr(D_ov^{-1} dD_ov/dmu) (real, imaginary part).  The divergence
+ * sum_nu (j_{x,nu} - j_{x-nu,nu}) of the exact trace vanishes (Eq.
+ * divergence_def); the estimator reaches it on average.  Errors as
+ * ov_overlap_solve. */
+int ov_u1_current(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w, int32_t nnoise,
+                  const void *eta, int32_t k, double tol, int32_t maxit, void *j, double *trace_mu,
+                  ov_tsl_info *info);
 
 /* Eigenvalues of one TSL tridiagonal T_k (the Ritz values), on the host: no
  * GPU and no context needed.  Host arrays as ov_tsl_coefficients writes them:

@@ -35,7 +35,8 @@ class OVError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("dense", ctypes.c_int32),
-                ("diagnostics", ctypes.c_int32), ("newton", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("diagnostics", ctypes.c_int32), ("newton", ctypes.c_int32),
+                ("basis_memory", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -67,7 +68,8 @@ class Problem(ctypes.Structure):
 EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", "ov_apply_H",
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
-           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_strerror"]
+           "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_overlap_apply", "ov_overlap_solve", "ov_u1_current",
+           "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -106,6 +108,10 @@ def load(path: str = LIB_PATH):
     lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
     lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
     lib.ov_tridiag_eigenvalues.argtypes = [I32, P, P, P, P]
+    lib.ov_overlap_apply.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, P, ctypes.POINTER(Info)]
+    lib.ov_overlap_solve.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, D, I32, P, ctypes.POINTER(I32),
+                                     ctypes.POINTER(D)]
+    lib.ov_u1_current.argtypes = [P, dims_t, P, D, D, I32, P, I32, D, I32, P, ctypes.POINTER(D), ctypes.POINTER(Info)]
     lib.ov_debug_inject.argtypes = [P, I32, I32]
     lib.ov_launch_count.argtypes = [P]
     lib.ov_launch_count.restype = ctypes.c_int64
@@ -137,15 +143,16 @@ def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=
     return _contexts[key]
 
 
-_extra = {}   # per cached context: the options not in its key (dense, diagnostics, newton)
+_extra = {}   # per cached context: the options not in its key (dense, diagnostics, newton, basis memory)
 
 
 def _set_extra(precision, rebiorth, passes, segment, **kw):
     ctx = context(precision, rebiorth, passes, segment=segment)
     key = (precision, rebiorth, passes, segment, ctx.value)
-    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0, "newton": 0})
+    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0, "newton": 0, "basis_memory": 0})
     ex.update({k: int(v) for k, v in kw.items()})
-    opt = Options(_PREC[precision], rebiorth, passes, segment, ex["dense"], ex["diagnostics"], ex["newton"])
+    opt = Options(_PREC[precision], rebiorth, passes, segment, ex["dense"], ex["diagnostics"], ex["newton"],
+                  ex["basis_memory"])
     _check(load().ov_context_set_options(ctx, ctypes.byref(opt)), "ov_context_set_options")
     return ctx
 
@@ -169,6 +176,12 @@ def newton_rules(rules: str, precision: str = "fp64", rebiorth: int = 1, passes:
     _set_extra(precision, rebiorth, passes, segment, newton={"norm": 0, "det": 1}[rules])
 
 
+def basis_memory(where: str, precision: str = "fp64", rebiorth: int = 1, passes: int = 2, segment: int = 0):
+    """Where the cached context keeps the Krylov bases: "device" (default) or "host"
+    (pinned host memory the kernels read over the CPU-GPU link)."""
+    _set_extra(precision, rebiorth, passes, segment, basis_memory={"device": 0, "host": 1}[where])
+
+
 def debug_inject(kind: str, step: int = 0, precision: str = "fp64", rebiorth: int = 1, passes: int = 2,
                  segment: int = 0):
     """One-shot host-side fault injection on the cached context: 'breakdown' or
@@ -176,6 +189,53 @@ def debug_inject(kind: str, step: int = 0, precision: str = "fp64", rebiorth: in
     kinds = {"none": 0, "breakdown": 1, "nonfinite": 2, "oom": 3}
     ctx = context(precision, rebiorth, passes, segment=segment)
     _check(load().ov_debug_inject(ctx, kinds[kind], int(step)), "ov_debug_inject")
+
+
+def overlap_apply(u, mu, m_w, b, k, dagger=False, precision="fp64", rebiorth=1, passes=2):
+    """D_ov b = b + gamma5 sgn(H) b (or D_ov^dagger b), the sign by k-step TSL."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    out = torch.empty_like(bb)
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_overlap_apply(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
+                                int(bool(dagger)), _ptr(out), None), "ov_overlap_apply")
+    return out[0] if single else out
+
+
+def overlap_solve(u, mu, m_w, rhs, k, dagger=False, tol=1e-10, maxit=300, precision="fp64", rebiorth=1,
+                  passes=2, check=True):
+    """x with D_ov x = rhs (or D_ov^dagger x = rhs) by restarted GMRES; returns
+    (x, iterations, relative residual)."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(rhs, u)
+    x = torch.empty_like(bb)
+    it = ctypes.c_int32(0)
+    res = ctypes.c_double(0.0)
+    ctx = context(precision, rebiorth, passes)
+    st = lib.ov_overlap_solve(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
+                              int(bool(dagger)), float(tol), int(maxit), _ptr(x), ctypes.byref(it), ctypes.byref(res))
+    if check:
+        _check(st, "ov_overlap_solve")
+    return (x[0] if single else x), it.value, res.value
+
+
+def u1_current(u, mu, m_w, eta, k, tol=1e-10, maxit=300, precision="fp64", rebiorth=1, passes=2):
+    """Z2-noise estimator of j_{x,nu} = Tr(D_ov^{-1} dD_ov/dTheta_{x,nu}) for all links,
+    shape (Nt, Nz, Ny, Nx, 4) complex128, and of Tr(D_ov^{-1} dD_ov/dmu)."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    ee, _ = _spinors(eta, u)
+    j = torch.empty(tuple(u.shape[:5]), dtype=torch.complex128, device=u.device)
+    tr = (ctypes.c_double * 2)()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_u1_current(ctx, dims, _ptr(u), float(mu), float(m_w), ee.shape[0], _ptr(ee), int(k), float(tol),
+                             int(maxit), _ptr(j), tr, None), "ov_u1_current")
+    return j, complex(tr[0], tr[1])
 
 
 def tridiag_eigenvalues(alpha, beta, delta):

@@ -89,8 +89,10 @@ template <typename R> void pack_links(const double* src_aos, R* dst, int64_t V, 
 // launch variants of the two stencil kernels (chosen by the autotuner; 0 = default)
 int apply_h_variants();
 int tsl_stencil_variants();
+// err (may be null): the staged variants set ERRB_TIMEOUT there when their bounded
+// wait on the shared-memory copies runs out
 template <typename R> void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st,
-                                   int variant = 0);
+                                   int variant = 0, int* err = nullptr);
 
 template <typename R> void tsl_init(const Lat<R>& L, cudaStream_t st);
 template <typename R> void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st, int variant = 0);
@@ -177,6 +179,23 @@ void dense_newton_combine_batch(const zd* X, const zd* Xi, zd* Xn, int k, int nb
                                 const double* logdet, int ld_stride, const int* scal, int scal_stride, double s,
                                 double w, double* stats, zd* part, int64_t part_stride, unsigned* cnt,
                                 cudaStream_t st);
+// ---- overlap operator, its Krylov solver and the U(1) current (user layout, complex128) ----
+// out = b + gamma5 x (g5 != 0) or b + x, n complex elements (12 per site)
+void ov_combine(const double* b, const double* x, double* out, int64_t n, int g5, cudaStream_t st);
+// out = f gamma5 in, f = fr + i fi
+void gamma5_scale(const double* in, double* out, int64_t n, double fr, double fi, cudaStream_t st);
+// out[i] = basis_i^dag w for i < nvec (basis_i at basis + i * stride doubles); partial: 152 * nvec zd
+void vec_dots(const double* basis, int64_t stride, int nvec, const double* w, int64_t n, zd* out, zd* partial,
+              cudaStream_t st);
+// w += s sum_i coef_i basis_i (coef on the device)
+void vec_update(double* w, const double* basis, int64_t stride, int nvec, const zd* coef, double s, int64_t n,
+                cudaStream_t st);
+void vec_scale(const double* in, double* out, double fr, double fi, int64_t n, cudaStream_t st);
+void vec_sub(const double* a, const double* b, double* out, int64_t n, cudaStream_t st);
+// j[l] (+)= scale (-Im sum conj(g_re) U + i (-Im sum conj(g_im) U)) per link l < nlinks (9 entries each)
+void theta_current(const double* u, const double* g_re, const double* g_im, double* j, int64_t nlinks, double scale,
+                   int accumulate, cudaStream_t st);
+
 // Frobenius-norm Newton scaling g = (||Xi||_F / ||X||_F)^{1/2} written as the equivalent
 // ld[p * ld_stride] = -(k/4) log(||Xi||_F^2 / ||X||_F^2) (so that exp(-ld / k) = g), for
 // nb problems at stride k*k; part: 64 zd and cnt: one ticket (zero) per problem.

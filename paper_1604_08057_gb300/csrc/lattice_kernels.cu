@@ -6,6 +6,7 @@
 // Thread mapping: one thread per lattice site (blockIdx.y = source) unless a
 // kernel says otherwise.  All reductions are deterministic: per-block partials
 // are summed in block order by the last block to finish.
+#include <algorithm>
 #include <type_traits>
 
 #include "dslash.cuh"
@@ -166,8 +167,11 @@ __global__ void __launch_bounds__(BSZ) k_apply_h(Lat<R> L, const R* __restrict__
 // launch variants (sources per thread, threads per block, site map); 0 is the default.
 // Plane variants fall back to consecutive sites when an x-y plane has fewer than
 // 64 sites or more than the variant's thread bound.
+// Variants 9, 10, 11 (FP32 only; others run variant 0) stage 1, 2 or 4 z-planes of
+// the input in shared memory (k_apply_h_staged, below).
 static const int kApplyVariants[][3] = {{1, 128, 0}, {1, 64, 0}, {1, 256, 0}, {2, 64, 0}, {2, 128, 0},
-                                        {4, 64, 0}, {4, 128, 0}, {1, 512, 1}, {2, 256, 1}};
+                                        {4, 64, 0}, {4, 128, 0}, {1, 512, 1}, {2, 256, 1},
+                                        {1, 1, 2},   {1, 2, 2},   {1, 4, 2}};
 int apply_h_variants() { return (int)(sizeof(kApplyVariants) / sizeof(kApplyVariants[0])); }
 
 template <typename R, int NS, int BSZ, int MAP>
@@ -185,9 +189,167 @@ static void launch_apply(const Lat<R>& L, const R* in, R* out, int dagger, cudaS
     k_apply_h<R, NS, BSZ, MAP><<<dim3(gx, (L.nsrc + NS - 1) / NS), bs, 0, st>>>(L, in, out, dagger, L.nsrc);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 H psi with the x-y-z neighbourhood staged in shared memory.
+// A block owns tz consecutive z-planes (whole x-y planes) of one time slice and
+// one source.  Those planes and the two z-halo planes (periodic) of all six
+// float4 chunks of the input field are copied into shared memory by bulk
+// asynchronous copies (cp.async.bulk, one per chunk and plane: a contiguous run
+// of Nx*Ny 16-byte chunks at a 16-byte-aligned address, completing on one
+// mbarrier), so each staged spinor crosses from global memory once and every
+// x, y and z neighbour is read from shared memory at conflict-free consecutive
+// addresses; the t neighbours and the links are loaded directly.  One thread
+// per site of the owned planes, at most 512 per block (tz is reduced until the
+// planes fit, and the form is not used where one x-y plane has more sites).  The wait on the copies is bounded (2 s): a
+// block that runs out sets ERRB_TIMEOUT in *err, waits once more (bounded) for
+// its copies, and writes nothing.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kStageWaitNs = 2000000000ull;
+constexpr int kStageMaxSmem = 227 * 1024;
+
+__device__ __forceinline__ unsigned long long stage_clock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool stage_wait(uint32_t mb, unsigned long long limit_ns) {
+  const unsigned long long t0 = stage_clock();
+  for (;;) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(mb), "r"(0u)
+        : "memory");
+    if (done) return true;
+    if (stage_clock() - t0 > limit_ns) return false;
+  }
+}
+
+// psi(s) from the staged planes when s lies in them, else from global memory
+struct StagedLoad {
+  const float4* stg;     // [6][tz + 2][P]
+  const float* f;        // the field (global)
+  int64_t V;
+  int P, nz, t, zlo, np, stride;   // stride = (tz + 2) * P
+  __device__ void operator()(int64_t s, Spinor<float>& o) const {
+    const int64_t tz_site = s / P;             // t * nz + z
+    const int tt = (int)(tz_site / nz), zz = (int)(tz_site % nz);
+    int i = zz - zlo;
+    if (i < 0) i += nz;
+    if (tt == t && i < np) {
+      const float4* q = stg + (int64_t)i * P + (s - tz_site * P);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const float4 v = q[(int64_t)c * stride];
+        o.c[2 * c] = mk(v.x, v.y);
+        o.c[2 * c + 1] = mk(v.z, v.w);
+      }
+      return;
+    }
+    load_spinor_ro(f, V, s, o);
+  }
+};
+
+__global__ void __launch_bounds__(512) k_apply_h_staged(Lat<float> L, const float* __restrict__ in,
+                                                         float* __restrict__ out, int dagger, int tz, int* err) {
+  extern __shared__ __align__(128) float4 stg[];
+  __shared__ __align__(8) unsigned long long mbar;
+  const Geom& g = L.g;
+  const int P = g.nx * g.ny;
+  const int nzb = (g.nz + tz - 1) / tz;
+  const int t = blockIdx.x / nzb, z0 = (blockIdx.x % nzb) * tz;
+  const int src = blockIdx.y;
+  const int tzb = min(tz, g.nz - z0);      // planes this block owns
+  const int np = tzb + 2;                   // planes staged (owned + two halo planes)
+  const int stride = (tz + 2) * P;
+  const float* f = in + (int64_t)src * L.vs;
+  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = (uint32_t)P * 16u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes * 6u * (uint32_t)np)
+                 : "memory");
+    const float4* f4 = reinterpret_cast<const float4*>(f);
+    for (int c = 0; c < 6; ++c)
+      for (int i = 0; i < np; ++i) {
+        int z = z0 - 1 + i;
+        z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
+        const float4* sp = f4 + (int64_t)c * g.V + ((int64_t)t * g.nz + z) * P;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(stg + (int64_t)c * stride + (int64_t)i * P);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         dst),
+                     "l"(sp), "r"(bytes), "r"(mb)
+                     : "memory");
+      }
+  }
+  const bool ok = stage_wait(mb, kStageWaitNs);
+  if (!ok) {
+    if (threadIdx.x == 0 && err) atomicOr(err, ERRB_TIMEOUT);
+    stage_wait(mb, kStageWaitNs);   // the copies still target this block's shared memory
+    return;
+  }
+  const int zi = threadIdx.x / P, p = threadIdx.x - zi * P;
+  if (zi >= tzb) return;
+  const int64_t s = ((int64_t)t * g.nz + z0 + zi) * P + p;
+  int zlo = z0 - 1;
+  if (zlo < 0) zlo += g.nz;
+  const StagedLoad ld{stg, f, g.V, P, g.nz, t, zlo, np, stride};
+  Spinor<float> o;
+  const float ft = dagger ? L.efinv : L.ef, fti = dagger ? L.ef : L.efinv;
+  h_site_ld(ld, L.u, g, s, L.kappa, ft, fti, o);
+  store_spinor(out + (int64_t)src * L.vs, g.V, s, o);
+}
+
+// planes per block of the staged variants; 0 when the lattice does not fit the form
+static int stage_planes(const Geom& g, int want) {
+  const int P = g.nx * g.ny;
+  int tz = std::min(want, g.nz);
+  while (tz > 1 && ((int64_t)P * tz > 512 || (int64_t)6 * (tz + 2) * P * 16 > kStageMaxSmem)) --tz;
+  if ((int64_t)P * tz > 512 || (int64_t)6 * (tz + 2) * P * 16 > kStageMaxSmem) return 0;
+  return tz;
+}
 template <typename R>
-void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st, int variant) {
+static void launch_apply_staged(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st, int want,
+                                int* err) {
+  if constexpr (std::is_same<R, float>::value) {
+    const int tz = stage_planes(L.g, want);
+    int dev = 0, optin = 0;
+    if (tz > 0 && !L.block && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
+      const int P = L.g.nx * L.g.ny;
+      const size_t smem = (size_t)6 * (tz + 2) * P * 16;
+      // the opt-in limit covers the dynamic part plus the kernel's own 8-byte mbarrier
+      bool fits = smem + 64 <= (size_t)optin;
+      if (fits && smem > 48 * 1024 &&
+          cudaFuncSetAttribute(k_apply_h_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        fits = false;
+      }
+      if (fits) {
+        const unsigned threads = (unsigned)((P * tz + 31) / 32 * 32);
+        const unsigned gx = (unsigned)(L.g.nt * ((L.g.nz + tz - 1) / tz));
+        k_apply_h_staged<<<dim3(gx, L.nsrc), threads, smem, st>>>(L, in, out, dagger, tz, err);
+        return;
+      }
+    }
+    cudaGetLastError();
+  }
+  launch_apply<R, 1, 128, 0>(L, in, out, dagger, st);
+}
+
+template <typename R>
+void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st, int variant, int* err) {
   switch (variant) {
+    case 9: launch_apply_staged<R>(L, in, out, dagger, st, 1, err); break;
+    case 10: launch_apply_staged<R>(L, in, out, dagger, st, 2, err); break;
+    case 11: launch_apply_staged<R>(L, in, out, dagger, st, 4, err); break;
     case 1: launch_apply<R, 1, 64, 0>(L, in, out, dagger, st); break;
     case 2: launch_apply<R, 1, 256, 0>(L, in, out, dagger, st); break;
     case 3: launch_apply<R, 2, 64, 0>(L, in, out, dagger, st); break;
@@ -1228,7 +1390,7 @@ void eps_norms(const double* a_top, const double* a_bot, const double* b, int ns
                                     cudaStream_t);                                                       \
   template void unpack_spinors<R>(const R*, double*, int, int64_t, int64_t, cudaStream_t);               \
   template void pack_links<R>(const double*, R*, int64_t, cudaStream_t);                                 \
-  template void apply_h<R>(const Lat<R>&, const R*, R*, int, cudaStream_t, int);                         \
+  template void apply_h<R>(const Lat<R>&, const R*, R*, int, cudaStream_t, int, int*);                   \
   template void tsl_init<R>(const Lat<R>&, cudaStream_t);                                                \
   template void tsl_stencil<R>(const Lat<R>&, int, bool, cudaStream_t, int);                             \
   template void tsl_update<R>(const Lat<R>&, int, bool, cudaStream_t);                                   \

@@ -2,6 +2,7 @@
 // host-side driver that enqueues the kernels of the forward two-sided Lanczos
 // recurrence, the k x k sign, the reverse sweep and the force contraction.
 #include <cmath>
+#include <complex>
 #include <cstddef>
 #include <algorithm>
 #include <atomic>
@@ -21,7 +22,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, NBUF
 };
 
 struct Status {
@@ -66,6 +67,7 @@ struct ov_context {
   ov_options opt{};
   void* buf[NBUF] = {};
   size_t cap[NBUF] = {};
+  bool host_buf[NBUF] = {};     // allocated as mapped pinned host memory (options.basis_memory)
   // coefficients of the last forward pass (for ov_tsl_coefficients)
   int last_k = 0, last_nsrc = 0;
   cudaEvent_t ev[8] = {};
@@ -112,19 +114,52 @@ void run(ov_context* c, int kind, int64_t nl, F&& f) {
   c->launches += nl;
 }
 
+void free_buf(ov_context* c, int id) {
+  if (!c->buf[id]) return;
+  if (c->host_buf[id]) {
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaFreeHost(c->buf[id]));
+  } else {
+    CK(cudaFree(c->buf[id]));
+  }
+  c->buf[id] = nullptr;
+  c->cap[id] = 0;
+  c->host_buf[id] = false;
+}
+
 void* ws(ov_context* c, int id, size_t bytes, bool zero = false) {
   if (bytes == 0) bytes = 16;
-  if (c->cap[id] < bytes) {
+  const bool host = (id == B_BV || id == B_BW) && c->opt.basis_memory == 1;
+  if (c->cap[id] < bytes || c->host_buf[id] != host) {
     if (c->inj_kind == OV_INJECT_OOM) {
       if (c->inj_step-- <= 0) {
         c->inj_kind = OV_INJECT_NONE;
         throw Status{OV_ERR_OOM};
       }
     }
-    if (c->buf[id]) CK(cudaFree(c->buf[id]));
-    c->buf[id] = nullptr;
-    c->cap[id] = 0;
+    free_buf(c, id);
     size_t nb = (bytes + 255) & ~(size_t)255;
+    if (host) {
+      // pinned host memory mapped into the device's address space: the kernels reach it
+      // through its device alias; it is cleared on the host before the device sees it
+      void* hp = nullptr;
+      void* dp = nullptr;
+      if (cudaHostAlloc(&hp, nb, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        throw Status{OV_ERR_OOM};
+      }
+      std::memset(hp, 0, nb);
+      if (cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess || dp != hp) {
+        // the library relies on one address for host and device (unified addressing)
+        cudaGetLastError();
+        cudaFreeHost(hp);
+        throw Status{OV_ERR_CUDA};
+      }
+      c->buf[id] = hp;
+      c->cap[id] = nb;
+      c->host_buf[id] = true;
+      return hp;
+    }
     cudaError_t e = cudaMalloc(&c->buf[id], nb);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -1250,21 +1285,252 @@ int tsl_vjp_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   return vjp_reverse<R>(c, F, xbar, x, dU, dmu, info);
 }
 
+// ---------------------------------------------------------------------------
+// Overlap operator D_ov = 1 + gamma5 sgn(H(mu)) (Sec. 1, Eq. overlap, a = 1) on
+// the user layout: D_ov b = b + gamma5 x with x the TSL approximation of
+// sgn(H(mu)) b; D_ov^dag b = b + sgn(H(-mu)) gamma5 b (H(mu)^dag = H(-mu) by
+// gamma5-hermiticity, and sgn(H)^dag = sgn(H^dag) since sgn(lambda) is real).
+// ---------------------------------------------------------------------------
+template <typename R>
+int overlap_apply_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                       const void* b, int k, int dagger, void* out, ov_tsl_info* info) {
+  check_ptr(b);
+  check_ptr(out);
+  const Geom g = make_geom(dims);
+  if (nsrc < 1 || nsrc > 4096) throw Status{OV_ERR_INVALID_ARG};
+  const int64_t n = (int64_t)nsrc * 12 * g.V;   // complex elements
+  const double* bd = static_cast<const double*>(b);
+  double* od = static_cast<double*>(out);
+  double* xs = wsT<double>(c, B_OVX, 2 * n);
+  int st;
+  if (!dagger) {
+    st = tsl_sign_impl<R>(c, dims, U, mu, m_w, nsrc, b, k, xs, info);
+    if (st != OV_OK) return st;
+    run(c, OV_KIND_COMBINE, 1, [&] { ov_combine(bd, xs, od, n, 1, c->st); });
+  } else {
+    double* g5b = wsT<double>(c, B_OVB, 2 * n);
+    run(c, OV_KIND_COMBINE, 1, [&] { gamma5_scale(bd, g5b, n, 1.0, 0.0, c->st); });
+    st = tsl_sign_impl<R>(c, dims, U, -mu, m_w, nsrc, g5b, k, xs, info);
+    if (st != OV_OK) return st;
+    run(c, OV_KIND_COMBINE, 1, [&] { ov_combine(bd, xs, od, n, 0, c->st); });
+  }
+  launch_check();
+  CK(cudaStreamSynchronize(c->st));
+  return OV_OK;
+}
+
+// Restarted GMRES(m) (Saad and Schultz 1986) for D_ov x = rhs (or D_ov^dag x = rhs),
+// one right-hand side, x_0 = 0: Arnoldi with classical Gram-Schmidt applied
+// twice (dots and updates on the device), complex Givens rotations and the
+// triangular solve on the host, the true residual recomputed at every restart.
+// The operator applies the k-step TSL, which is linear in its vector only to
+// its approximation error, so the attainable residual is of that order.
+// Returns OV_ERR_NOCONV when the relative residual is still above tol after
+// maxit operator applications (*iters, *resid report where it stopped).
+constexpr int GMRES_M = 30;
+template <typename R>
+int overlap_solve_one(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, const double* rhs,
+                      int k, int dagger, double tol, int maxit, double* x, int* iters, double* resid) {
+  const Geom g = make_geom(dims);
+  const int64_t n = 12 * g.V, n2 = 2 * n;
+  const int m = std::max(1, std::min(maxit, GMRES_M));
+  double* Vb = wsT<double>(c, B_GMV, (int64_t)(m + 1) * n2);
+  double* r = wsT<double>(c, B_GMR, n2);
+  double* ax = wsT<double>(c, B_GMW, n2);
+  zd* hd = wsT<zd>(c, B_GMH, 2 * (int64_t)(m + 1));
+  zd* part = wsT<zd>(c, B_GMP, 152 * (int64_t)(m + 1));
+  auto apply = [&](const double* in, double* out) {
+    const int st = overlap_apply_impl<R>(c, dims, U, mu, m_w, 1, in, k, dagger, out, nullptr);
+    if (st != OV_OK) throw Status{st};
+  };
+  auto dots = [&](const double* basis, int nvec, const double* w, std::vector<zd>& out) {
+    run(c, OV_KIND_COMBINE, 2, [&] { vec_dots(basis, n2, nvec, w, n, hd, part, c->st); });
+    out.resize(nvec);
+    CK(cudaMemcpyAsync(out.data(), hd, sizeof(zd) * nvec, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  };
+  std::vector<zd> tmp;
+  dots(rhs, 1, rhs, tmp);
+  const double bnorm = std::sqrt(tmp[0].re);
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n2, c->st));
+  *iters = 0;
+  *resid = 0.0;
+  if (!(bnorm > 0.0)) return std::isfinite(bnorm) ? OV_OK : OV_ERR_NONFINITE;
+  CK(cudaMemcpyAsync(r, rhs, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->st));
+  double rn = bnorm;
+  int it = 0;
+  while (rn > tol * bnorm && it < maxit) {
+    run(c, OV_KIND_COMBINE, 1, [&] { vec_scale(r, Vb, 1.0 / rn, 0.0, n, c->st); });
+    std::vector<std::complex<double>> H((size_t)(m + 1) * m, 0.0), gv(m + 1, 0.0), sn(m, 0.0);
+    std::vector<double> cs(m, 0.0);
+    gv[0] = rn;
+    int j = 0;
+    while (j < m && it < maxit) {
+      double* w = Vb + (int64_t)(j + 1) * n2;
+      apply(Vb + (int64_t)j * n2, w);
+      std::vector<std::complex<double>> hc(j + 2, 0.0);
+      for (int pass = 0; pass < 2; ++pass) {
+        run(c, OV_KIND_COMBINE, 3, [&] {
+          vec_dots(Vb, n2, j + 1, w, n, hd, part, c->st);
+          vec_update(w, Vb, n2, j + 1, hd, -1.0, n, c->st);
+        });
+        std::vector<zd> hh(j + 1);
+        CK(cudaMemcpyAsync(hh.data(), hd, sizeof(zd) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int i = 0; i <= j; ++i) hc[i] += std::complex<double>(hh[i].re, hh[i].im);
+      }
+      dots(w, 1, w, tmp);
+      const double hn = std::sqrt(tmp[0].re);
+      if (!std::isfinite(hn)) return OV_ERR_NONFINITE;
+      hc[j + 1] = hn;
+      if (hn > 0.0) run(c, OV_KIND_COMBINE, 1, [&] { vec_scale(w, w, 1.0 / hn, 0.0, n, c->st); });
+      // previous rotations, then the one that zeroes H[j+1][j]
+      for (int i = 0; i < j; ++i) {
+        const std::complex<double> a = hc[i], b2 = hc[i + 1];
+        hc[i] = cs[i] * a + sn[i] * b2;
+        hc[i + 1] = -std::conj(sn[i]) * a + cs[i] * b2;
+      }
+      const std::complex<double> a = hc[j], b2 = hc[j + 1];
+      const double rho = std::hypot(std::abs(a), std::abs(b2));
+      if (std::abs(a) == 0.0) {
+        cs[j] = 0.0;
+        sn[j] = 1.0;
+      } else {
+        cs[j] = std::abs(a) / rho;
+        sn[j] = (a / std::abs(a)) * std::conj(b2) / rho;
+      }
+      hc[j] = cs[j] * a + sn[j] * b2;
+      hc[j + 1] = 0.0;
+      gv[j + 1] = -std::conj(sn[j]) * gv[j];
+      gv[j] = cs[j] * gv[j];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hc[i];
+      ++j;
+      ++it;
+      if (std::abs(gv[j]) <= tol * bnorm) break;
+    }
+    // y = R^{-1} g by back substitution, x += V y
+    std::vector<std::complex<double>> y(j, 0.0);
+    for (int i = j - 1; i >= 0; --i) {
+      std::complex<double> t = gv[i];
+      for (int q = i + 1; q < j; ++q) t -= H[(size_t)i * m + q] * y[q];
+      y[i] = t / H[(size_t)i * m + i];
+    }
+    std::vector<zd> yd(j);
+    for (int i = 0; i < j; ++i) yd[i] = mk(y[i].real(), y[i].imag());
+    CK(cudaMemcpyAsync(hd, yd.data(), sizeof(zd) * j, cudaMemcpyHostToDevice, c->st));
+    run(c, OV_KIND_COMBINE, 1, [&] { vec_update(x, Vb, n2, j, hd, 1.0, n, c->st); });
+    // true residual
+    apply(x, ax);
+    run(c, OV_KIND_COMBINE, 1, [&] { vec_sub(rhs, ax, r, n, c->st); });
+    dots(r, 1, r, tmp);
+    rn = std::sqrt(tmp[0].re);
+    if (!std::isfinite(rn)) return OV_ERR_NONFINITE;
+  }
+  *iters = it;
+  *resid = rn / bnorm;
+  return rn <= tol * bnorm ? OV_OK : OV_ERR_NOCONV;
+}
+
+template <typename R>
+int overlap_solve_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                       const void* rhs, int k, int dagger, double tol, int maxit, void* x, int32_t* iters,
+                       double* resid) {
+  check_ptr(rhs);
+  check_ptr(x);
+  if (nsrc < 1 || nsrc > 4096 || !(tol > 0.0) || maxit < 1) throw Status{OV_ERR_INVALID_ARG};
+  const Geom g = make_geom(dims);
+  const int64_t n2 = 24 * g.V;
+  int worst = OV_OK, itmax = 0;
+  double rmax = 0.0;
+  for (int s = 0; s < nsrc; ++s) {
+    int it = 0;
+    double rr = 0.0;
+    const int st = overlap_solve_one<R>(c, dims, U, mu, m_w, static_cast<const double*>(rhs) + s * n2, k, dagger,
+                                        tol, maxit, static_cast<double*>(x) + s * n2, &it, &rr);
+    if (st != OV_OK && st != OV_ERR_NOCONV) return st;
+    if (st == OV_ERR_NOCONV) worst = st;
+    itmax = std::max(itmax, it);
+    rmax = std::max(rmax, rr);
+  }
+  if (iters) *iters = itmax;
+  if (resid) *resid = rmax;
+  return worst;
+}
+
+// U(1) current estimator (Sec. 4.3, Eq. lat_vec_cur) over nnoise noise vectors:
+//   j_{x,nu} = (1/N) sum_eta < gamma5 chi, d(sgn(H) eta)/dTheta_{x,nu} >,  chi = D_ov^{-dag} eta,
+// from one forward TSL on eta and two reverse sweeps (cotangents gamma5 chi and
+// i gamma5 chi: the real and imaginary parts), each link gradient turned into a
+// Theta derivative with dU = i U dTheta.  trace_mu (may be null) receives the
+// same estimator of Tr(D_ov^{-1} dD_ov/dmu) from the two sweeps' mu derivatives.
+template <typename R>
+int u1_current_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nnoise,
+                    const void* eta, int k, double tol, int maxit, void* j, double* trace_mu, ov_tsl_info* info) {
+  check_ptr(eta);
+  check_ptr(j);
+  check_ptr(U);
+  if (nnoise < 1 || nnoise > 4096) throw Status{OV_ERR_INVALID_ARG};
+  const Geom g = make_geom(dims);
+  const int64_t n = 12 * g.V, n2 = 2 * n;
+  double* chi = wsT<double>(c, B_CHI, n2);
+  double* xb1 = wsT<double>(c, B_CURX1, n2);
+  double* xb2 = wsT<double>(c, B_CURX2, n2);
+  double* g1 = wsT<double>(c, B_CURG1, 72 * g.V);
+  double* g2 = wsT<double>(c, B_CURG2, 72 * g.V);
+  double tr_re = 0.0, tr_im = 0.0;
+  for (int s = 0; s < nnoise; ++s) {
+    const double* es = static_cast<const double*>(eta) + s * n2;
+    int it = 0;
+    double rr = 0.0;
+    int st = overlap_solve_one<R>(c, dims, U, mu, m_w, es, k, 1, tol, maxit, chi, &it, &rr);
+    if (st != OV_OK) return st;
+    run(c, OV_KIND_COMBINE, 2, [&] {
+      gamma5_scale(chi, xb1, n, 1.0, 0.0, c->st);
+      gamma5_scale(chi, xb2, n, 0.0, 1.0, c->st);
+    });
+    FwdState<R> F;
+    st = vjp_forward<R>(c, dims, U, mu, m_w, 1, es, k, F, info);
+    if (st != OV_OK) return st;
+    double d1 = 0.0, d2 = 0.0;
+    st = vjp_reverse<R>(c, F, xb1, nullptr, g1, &d1, nullptr);
+    if (st != OV_OK) return st;
+    st = vjp_reverse<R>(c, F, xb2, nullptr, g2, &d2, nullptr);
+    if (st != OV_OK) return st;
+    run(c, OV_KIND_COMBINE, 1, [&] {
+      theta_current(static_cast<const double*>(U), g1, g2, static_cast<double*>(j), 4 * g.V, 1.0 / nnoise, s > 0,
+                    c->st);
+    });
+    tr_re += d1 / nnoise;
+    tr_im += d2 / nnoise;
+  }
+  launch_check();
+  CK(cudaStreamSynchronize(c->st));
+  if (trace_mu) {
+    trace_mu[0] = tr_re;
+    trace_mu[1] = tr_im;
+  }
+  return OV_OK;
+}
+
 template <typename R>
 int apply_h_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
                  const void* in, void* out, int dagger) {
   check_ptr(in);
   check_ptr(out);
   Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, 1, false);
+  int* aerr = wsT<int>(c, B_AERR, 1, true);
   run(c, OV_KIND_LAYOUT, 1,
       [&] { pack_spinors<R>(static_cast<const double*>(in), L.r, nsrc, L.g.V, L.vs, c->st); });
-  run(c, OV_KIND_APPLY_H, 1, [&] { apply_h(L, L.r, L.p, dagger, c->st, c->tuned_apply[c->opt.precision]); });
+  run(c, OV_KIND_APPLY_H, 1,
+      [&] { apply_h(L, L.r, L.p, dagger, c->st, c->tuned_apply[c->opt.precision], aerr); });
   run(c, OV_KIND_LAYOUT, 1,
       [&] { unpack_spinors<R>(L.p, static_cast<double*>(out), nsrc, L.g.V, L.vs, c->st); });
   launch_check();
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, aerr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   prof_collect(c);
-  return OV_OK;
+  return (herr & ERRB_TIMEOUT) ? OV_ERR_TIMEOUT : OV_OK;
 }
 
 template <typename R>
@@ -1287,8 +1553,9 @@ int autotune_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   ov_tune_report r{};
   r.n_apply = apply_h_variants();
   r.n_pair = tsl_stencil_variants();
+  int* aerr = wsT<int>(c, B_AERR, 1, true);
   for (int v = 0; v < r.n_apply && v < 16; ++v)
-    r.apply_us[v] = time_us([&] { apply_h(L, L.r, L.p, 0, c->st, v); });
+    r.apply_us[v] = time_us([&] { apply_h(L, L.r, L.p, 0, c->st, v, aerr); });
   for (int v = 0; v < r.n_pair && v < 16; ++v)
     r.pair_us[v] = time_us([&] { tsl_stencil(L, 0, true, c->st, v); });
   // a variant replaces the current choice only when it is more than 2% faster: the
@@ -1298,6 +1565,10 @@ int autotune_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
     if (r.apply_us[v] < 0.98f * r.apply_us[r.apply_variant]) r.apply_variant = v;
   for (int v = 1; v < r.n_pair && v < 16; ++v)
     if (r.pair_us[v] < 0.98f * r.pair_us[r.pair_variant]) r.pair_variant = v;
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, aerr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (herr & ERRB_TIMEOUT) return OV_ERR_TIMEOUT;
   c->tuned_apply[c->opt.precision] = r.apply_variant;
   c->tuned_pair[c->opt.precision] = r.pair_variant;
   c->launches += 6 * (r.n_apply + r.n_pair);
@@ -1319,7 +1590,8 @@ int guarded(F&& f) {
 bool valid_options(const ov_options* o) {
   return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4 &&
          o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0) && (o->dense == 0 || o->dense == 1) &&
-         (o->diagnostics == 0 || o->diagnostics == 1) && (o->newton == 0 || o->newton == 1);
+         (o->diagnostics == 0 || o->diagnostics == 1) && (o->newton == 0 || o->newton == 1) &&
+         (o->basis_memory == 0 || o->basis_memory == 1);
 }
 
 // x = V_k y from a forward state (a second pass over the segments if there are any)
@@ -1385,8 +1657,13 @@ int ov_context_destroy(ov_context* c) {
   for (ov_context* w : c->workers) ov_context_destroy(w);
   c->workers.clear();
   cudaStreamSynchronize(c->st);
-  for (int i = 0; i < NBUF; ++i)
-    if (c->buf[i]) cudaFree(c->buf[i]);
+  for (int i = 0; i < NBUF; ++i) {
+    if (!c->buf[i]) continue;
+    if (c->host_buf[i])
+      cudaFreeHost(c->buf[i]);
+    else
+      cudaFree(c->buf[i]);
+  }
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->prof) {
@@ -1734,6 +2011,40 @@ int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, do
   });
 }
 
+int ov_overlap_apply(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                     const void* b, int32_t k, int32_t dagger, void* out, ov_tsl_info* info) {
+  if (!c || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? overlap_apply_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, dagger, out, info)
+               : overlap_apply_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, dagger, out, info);
+  });
+}
+
+int ov_overlap_solve(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                     const void* rhs, int32_t k, int32_t dagger, double tol, int32_t maxit, void* x, int32_t* iters,
+                     double* resid) {
+  if (!c || k < 2 || k > 4096) return OV_ERR_INVALID_ARG;
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? overlap_solve_impl<float>(c, dims, U, mu, m_w, nsrc, rhs, k, dagger, tol, maxit, x, iters, resid)
+               : overlap_solve_impl<double>(c, dims, U, mu, m_w, nsrc, rhs, k, dagger, tol, maxit, x, iters, resid);
+  });
+}
+
+int ov_u1_current(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nnoise,
+                  const void* eta, int32_t k, double tol, int32_t maxit, void* j, double* trace_mu,
+                  ov_tsl_info* info) {
+  if (!c || k < 2 || k > 4096 || !(tol > 0.0) || maxit < 1) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? u1_current_impl<float>(c, dims, U, mu, m_w, nnoise, eta, k, tol, maxit, j, trace_mu, info)
+               : u1_current_impl<double>(c, dims, U, mu, m_w, nnoise, eta, k, tol, maxit, j, trace_mu, info);
+  });
+}
+
 int ov_debug_inject(ov_context* c, int32_t kind, int32_t step) {
   if (!c || kind < OV_INJECT_NONE || kind > OV_INJECT_OOM || step < 0) return OV_ERR_INVALID_ARG;
   c->inj_kind = kind;
@@ -1750,7 +2061,8 @@ const char* ov_strerror(int s) {
     case OV_ERR_SIGN_ILLPOSED:
       return "k x k sign ill-posed (singular or non-convergent Newton iterate, or a Ritz value on the "
              "imaginary axis)";
-    case OV_ERR_NOCONV: return "the Ritz-value iteration of the run diagnostics did not converge";
+    case OV_ERR_NOCONV:
+      return "an iteration did not converge (the Ritz values of the diagnostics, or the overlap solver)";
     case OV_ERR_CUDA: return "CUDA runtime error";
     case OV_ERR_NONFINITE: return "non-finite recurrence coefficient";
     case OV_ERR_SCRATCH_LIMIT: return "problem too large for the fixed 32 MiB scratch of ov_apply_H_noalloc";
