@@ -168,10 +168,11 @@ __global__ void __launch_bounds__(BSZ) k_apply_h(Lat<R> L, const R* __restrict__
 // Plane variants fall back to consecutive sites when an x-y plane has fewer than
 // 64 sites or more than the variant's thread bound.
 // Variants 9, 10, 11 (FP32 only; others run variant 0) stage 1, 2 or 4 z-planes of
-// the input in shared memory (k_apply_h_staged, below).
+// the input in shared memory (k_apply_h_staged, below); variant 12 (FP32 only)
+// sweeps runs of z-planes through a ring of plane slots (k_apply_h_sweep).
 static const int kApplyVariants[][3] = {{1, 128, 0}, {1, 64, 0}, {1, 256, 0}, {2, 64, 0}, {2, 128, 0},
                                         {4, 64, 0}, {4, 128, 0}, {1, 512, 1}, {2, 256, 1},
-                                        {1, 1, 2},   {1, 2, 2},   {1, 4, 2}};
+                                        {1, 1, 2},   {1, 2, 2},   {1, 4, 2},   {1, 0, 3}};
 int apply_h_variants() { return (int)(sizeof(kApplyVariants) / sizeof(kApplyVariants[0])); }
 
 template <typename R, int NS, int BSZ, int MAP>
@@ -306,6 +307,134 @@ __global__ void __launch_bounds__(512) k_apply_h_staged(Lat<float> L, const floa
   store_spinor(out + (int64_t)src * L.vs, g.V, s, o);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 H psi by a pipelined sweep along z.  A block owns a run of z-planes
+// [zb, ze) of one time slice and one source and walks it plane by plane,
+// keeping a ring of four plane slots in shared memory: planes z-1, z, z+1 are
+// resident while plane z is computed and plane z+2 is in flight, so each plane
+// is copied once per run (bulk asynchronous copies, one per chunk, completing
+// on the slot's mbarrier) and the copies overlap the arithmetic.  One thread
+// per site of a plane (planes of at most 256 sites; three blocks per SM).  x, y and z neighbours come from shared memory, t
+// neighbours and links from global memory.  Every wait is bounded (2 s); on a
+// timeout the block flags ERRB_TIMEOUT, waits (bounded) for the copies it has
+// in flight, and stops.
+// ---------------------------------------------------------------------------
+constexpr int kRing = 4;
+
+struct SweepLoad {
+  const float4* stg;       // [kRing][6][P]
+  const float* f;
+  int64_t V;
+  int P, nz, t, z, sm, s0, sp;   // current plane z; slots of planes z-1, z, z+1
+  __device__ void operator()(int64_t s, Spinor<float>& o) const {
+    const int64_t tz_site = s / P;
+    const int tt = (int)(tz_site / nz), zz = (int)(tz_site % nz);
+    int slot = -1;
+    if (tt == t) {
+      if (zz == z) slot = s0;
+      else if (zz == (z + 1 == nz ? 0 : z + 1)) slot = sp;
+      else if (zz == (z == 0 ? nz - 1 : z - 1)) slot = sm;
+    }
+    if (slot >= 0) {
+      const float4* q = stg + (int64_t)slot * 6 * P + (s - tz_site * P);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const float4 v = q[(int64_t)c * P];
+        o.c[2 * c] = mk(v.x, v.y);
+        o.c[2 * c + 1] = mk(v.z, v.w);
+      }
+      return;
+    }
+    load_spinor_ro(f, V, s, o);
+  }
+};
+
+__global__ void __launch_bounds__(256, 3) k_apply_h_sweep(Lat<float> L, const float* __restrict__ in,
+                                                       float* __restrict__ out, int dagger, int nzc, int* err) {
+  extern __shared__ __align__(128) float4 ring[];
+  __shared__ __align__(8) unsigned long long mbar[kRing];
+  const Geom& g = L.g;
+  const int P = g.nx * g.ny;
+  const int zc = blockIdx.x % nzc, t = blockIdx.x / nzc;
+  const int zb = (int)((int64_t)zc * g.nz / nzc), ze = (int)((int64_t)(zc + 1) * g.nz / nzc);
+  const int src = blockIdx.y;
+  const float* f = in + (int64_t)src * L.vs;
+  const float4* f4 = reinterpret_cast<const float4*>(f);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kRing; ++q) {
+      const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[q]);
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  // plane index i = zg - (zb - 1) for zg in [zb - 1, ze]; slot i % kRing, fill (i / kRing)
+  const int nplanes = ze - zb + 2;
+  auto issue = [&](int i) {   // thread 0 only
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[i % kRing]);
+    const uint32_t bytes = (uint32_t)P * 16u;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes * 6u) : "memory");
+    int zg = zb - 1 + i;
+    zg = zg < 0 ? zg + g.nz : (zg >= g.nz ? zg - g.nz : zg);
+    const float4* sp = f4 + ((int64_t)t * g.nz + zg) * P;
+    float4* dst = ring + (int64_t)(i % kRing) * 6 * P;
+    for (int c = 0; c < 6; ++c) {
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + (int64_t)c * P);
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                   "l"(sp + (int64_t)c * g.V), "r"(bytes), "r"(mb)
+                   : "memory");
+    }
+  };
+  int issued = min(kRing, nplanes);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < issued; ++i) issue(i);
+  int waited = 0;   // planes 0 .. waited-1 have been observed complete by every thread
+  auto wait_plane = [&](int i) -> bool {
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[i % kRing]);
+    const uint32_t parity = (uint32_t)((i / kRing) & 1);
+    const unsigned long long t0 = stage_clock();
+    for (;;) {
+      uint32_t done = 0;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(mb), "r"(parity)
+          : "memory");
+      if (done) return true;
+      if (stage_clock() - t0 > kStageWaitNs) return false;
+    }
+  };
+  bool ok = true;
+  const float ft = dagger ? L.efinv : L.ef, fti = dagger ? L.ef : L.efinv;
+  for (int z = zb; z < ze; ++z) {
+    const int i0 = z - zb + 1;   // plane index of z
+    bool okw = true;
+    for (; waited <= i0 + 1; ++waited)
+      if (okw) okw = wait_plane(waited);
+    ok = __syncthreads_and(okw) != 0;   // one decision for the whole block
+    if (!ok) break;
+    if (threadIdx.x < P) {
+      const int64_t s = ((int64_t)t * g.nz + z) * P + threadIdx.x;
+      const SweepLoad ld{ring, f, g.V, P, g.nz, t, z, (i0 - 1) % kRing, i0 % kRing, (i0 + 1) % kRing};
+      Spinor<float> o;
+      h_site_ld(ld, L.u, g, s, L.kappa, ft, fti, o);
+      store_spinor(out + (int64_t)src * L.vs, g.V, s, o);
+    }
+    __syncthreads();   // the slot of plane z - 1 is free again
+    if (threadIdx.x == 0 && issued < nplanes) issue(issued);
+    ++issued;
+  }
+  if (!ok) {
+    if (threadIdx.x == 0 && err) atomicOr(err, ERRB_TIMEOUT);
+    // copies still in flight target this block's shared memory: only the latest fill of
+    // each slot can be pending (a slot is refilled only after its previous fill was
+    // observed), so wait (bounded) for those
+    const int last = min(issued, nplanes);
+    for (int i = max(0, last - kRing); i < last; ++i) wait_plane(i);
+  }
+}
+
 // planes per block of the staged variants; 0 when the lattice does not fit the form
 static int stage_planes(const Geom& g, int want) {
   const int P = g.nx * g.ny;
@@ -345,8 +474,41 @@ static void launch_apply_staged(const Lat<R>& L, const R* in, R* out, int dagger
 }
 
 template <typename R>
+static void launch_apply_sweep(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st, int* err) {
+  if constexpr (std::is_same<R, float>::value) {
+    const int P = L.g.nx * L.g.ny;
+    const size_t smem = (size_t)kRing * 6 * P * 16;
+    int dev = 0, optin = 0;
+    if (!L.block && P <= 256 && L.g.nz >= 1 && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        smem + 128 <= (size_t)optin) {
+      bool fits = true;
+      if (smem > 48 * 1024 &&
+          cudaFuncSetAttribute(k_apply_h_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+              cudaSuccess)
+        fits = false;
+      if (fits)
+        cudaFuncSetAttribute(k_apply_h_sweep, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaGetLastError();
+      if (fits) {
+        // z runs per (t, source) row: about three blocks per SM in all, as few runs (as
+        // long a pipeline) as that allows, each run at least two planes
+        const int64_t rows = (int64_t)L.g.nt * L.nsrc;
+        int nzc = (int)std::min<int64_t>((3 * 152 + rows / 2) / rows, std::max(1, L.g.nz / 2));
+        if (nzc < 1) nzc = 1;
+        const unsigned threads = (unsigned)((P + 31) / 32 * 32);
+        k_apply_h_sweep<<<dim3((unsigned)(L.g.nt * nzc), L.nsrc), threads, smem, st>>>(L, in, out, dagger, nzc, err);
+        return;
+      }
+    }
+  }
+  launch_apply<R, 1, 128, 0>(L, in, out, dagger, st);
+}
+
+template <typename R>
 void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st, int variant, int* err) {
   switch (variant) {
+    case 12: launch_apply_sweep<R>(L, in, out, dagger, st, err); break;
     case 9: launch_apply_staged<R>(L, in, out, dagger, st, 1, err); break;
     case 10: launch_apply_staged<R>(L, in, out, dagger, st, 2, err); break;
     case 11: launch_apply_staged<R>(L, in, out, dagger, st, 4, err); break;

@@ -99,6 +99,26 @@ def test_every_stencil_variant(dims, precision, tol_h, tol_x):
     binding.set_stencil_variants(rep["apply_variant"], rep["pair_variant"], precision)
 
 
+@pytest.mark.parametrize("variant", [9, 10, 11, 12])
+def test_shared_memory_stencil_variants_long_runs(variant):
+    """The FP32 variants that stage the input in shared memory, on a lattice whose
+    per-block runs of z-planes are long enough that the sweep variant (12) refills
+    its ring of four plane slots (runs of 4-5 planes: 6-7 staged planes), with
+    periodic wrap in z and t, against the oracle's operator."""
+    dims, mu, m_w = (3, 4, 9, 40), 0.3, -2.0
+    u, b, _ = case(dims, 0.3, 17, 6)
+    ut, bt = T(u), T(b)
+    binding.set_stencil_variants(variant, 0, "mixed")
+    try:
+        for dagger in (False, True):
+            got = binding.apply_H(ut, mu, m_w, bt, dagger=dagger, precision="mixed").cpu().numpy()
+            for s in range(6):
+                want = (dirac.apply_h_dagger if dagger else dirac.apply_h)(u, b[s], mu, m_w)
+                assert rel(got[s], want) <= 2e-6, (variant, dagger, s, rel(got[s], want))
+    finally:
+        binding.set_stencil_variants(0, 0, "mixed")
+
+
 # ---------------------------------------------------------------------------
 # forward TSL
 # ---------------------------------------------------------------------------
