@@ -301,8 +301,10 @@ def run_ours(args, rank, world, local_rank):
                     "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 3),
                     "peak_source": f"derived: 152 SMs x 4 FP64 flop/clk x {sm_mhz:.0f} MHz (sampled)",
                     "fp64_gemm_measured_tflops": round(fp64_peak(dev) / 1e3, 3),
+                    "frac_of_fp64_gemm": None,
                     "hbm_view": {"achieved_GB_s": round(gbs, 1), "peak": hbm, "frac": round(gbs / hbm, 3)},
                     **per_launch}
+        roofline["frac_of_fp64_gemm"] = round(achieved / roofline["fp64_gemm_measured_tflops"], 3)
         if dom == "rev_stencil":
             # ncu: DRAM bytes of k_rev_stencil launches at 14x14^3, k = 120 = 0.845 x their
             # algorithmic bytes; launches differ only in how many fields they stream
@@ -347,6 +349,7 @@ def run_ours(args, rank, world, local_rank):
         out["schedule_compare"] = schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x)
         out["diagnostics"] = diagnostics_leg(args, ut, bt, xt, wl, k, ms_total / args.steps)
         out["basis_in_host_memory"] = host_basis_leg(args, ut, bt, xt, wl, k, du, dmu, x)
+        out["other_workloads"] = other_workloads_leg(args)
         if world == 1:
             out["cpu_baseline"], out["parity"] = cpu_leg(args, k, ut)
     return out
@@ -428,6 +431,37 @@ def schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x, periods=(20,)):
             res[f"P={period}"] = f"status {exc.status}"
         except RuntimeError as exc:   # e.g. device memory: the headline line must still print
             res[f"P={period}"] = f"error: {exc}"
+    return res
+
+
+def other_workloads_leg(args, reps=3):
+    """Seconds per forward + VJP call on the 4x4^3 (k = 200, one source) and 8x8^3
+    (k = 400, four sources) workloads, FP64, projections every 20 steps, one pass,
+    after autotuning and one warm-up call (device time over `reps` calls)."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    res = {}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for name in ("4x4^3", "8x8^3"):
+        wl = inputs.WORKLOADS[name]
+        u, b, xbar = inputs.make_inputs(wl)
+        ut, bt, xt = (torch.tensor(a, device=dev) for a in (u, b, xbar))
+        opts = ("fp64", 20, 1)
+        try:
+            binding.autotune(ut, wl.mu, wl.m_w, b.shape[0], *opts)
+            binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, wl.k, xt, *opts)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, wl.k, xt, *opts)
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = {"s_per_call": round(e0.elapsed_time(e1) / 1e3 / reps, 4), "k": wl.k,
+                         "sources": int(b.shape[0]), "rebiorth_period": 20}
+        except binding.OVError as exc:
+            res[name] = {"status": exc.status, "error": str(exc)}
     return res
 
 

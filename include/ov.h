@@ -100,6 +100,14 @@ typedef struct {
                         * written by the kernels over the CPU-GPU link (NVLink-C2C on a GB300),
                         * for bases larger than device memory.  Same kernels and results, bit
                         * for bit, with any re-biorthogonalisation schedule. */
+  int32_t graphs;      /* 1 (the default when ov_context_create gets no options): when a call
+                        * on the context repeats the previous call's shape, buffers and schedule
+                        * (k, sources, lattice, mu, m_w, options), its forward Lanczos sweep and
+                        * its reverse sweep are captured as CUDA graphs, and later calls with that
+                        * shape replay them, which removes the host's per-kernel launch cost (the
+                        * sweeps launch ~10 kernels per step); results are bit for bit those of
+                        * direct launches.  Not used while per-kernel profiling or a fault
+                        * injection is active, or with segments.  0: direct launches. */
 } ov_options;
 
 typedef struct {

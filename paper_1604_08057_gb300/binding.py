@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("dense", ctypes.c_int32),
                 ("diagnostics", ctypes.c_int32), ("newton", ctypes.c_int32),
-                ("basis_memory", ctypes.c_int32)]
+                ("basis_memory", ctypes.c_int32), ("graphs", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -135,6 +135,7 @@ def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=
     key = (dev.index, stream, precision, rebiorth, passes, segment)
     if key not in _contexts:
         opt = Options(_PREC[precision], rebiorth, passes, segment)
+        opt.graphs = 1
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             _check(lib.ov_context_create(ctypes.byref(h), ctypes.byref(opt), ctypes.c_void_p(stream)),
@@ -143,16 +144,16 @@ def context(precision: str = "fp64", rebiorth: int = 1, passes: int = 2, device=
     return _contexts[key]
 
 
-_extra = {}   # per cached context: the options not in its key (dense, diagnostics, newton, basis memory)
+_extra = {}   # per cached context: the options not in its key (dense, diagnostics, newton, basis memory, graphs)
 
 
 def _set_extra(precision, rebiorth, passes, segment, **kw):
     ctx = context(precision, rebiorth, passes, segment=segment)
     key = (precision, rebiorth, passes, segment, ctx.value)
-    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0, "newton": 0, "basis_memory": 0})
+    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0, "newton": 0, "basis_memory": 0, "graphs": 1})
     ex.update({k: int(v) for k, v in kw.items()})
     opt = Options(_PREC[precision], rebiorth, passes, segment, ex["dense"], ex["diagnostics"], ex["newton"],
-                  ex["basis_memory"])
+                  ex["basis_memory"], ex["graphs"])
     _check(load().ov_context_set_options(ctx, ctypes.byref(opt)), "ov_context_set_options")
     return ctx
 
@@ -180,6 +181,12 @@ def basis_memory(where: str, precision: str = "fp64", rebiorth: int = 1, passes:
     """Where the cached context keeps the Krylov bases: "device" (default) or "host"
     (pinned host memory the kernels read over the CPU-GPU link)."""
     _set_extra(precision, rebiorth, passes, segment, basis_memory={"device": 0, "host": 1}[where])
+
+
+def sweep_graphs(on: bool, precision: str = "fp64", rebiorth: int = 1, passes: int = 2, segment: int = 0):
+    """Capture and replay the Krylov sweeps as CUDA graphs on the cached context (on by
+    default) or launch every kernel directly; the results are the same bit for bit."""
+    _set_extra(precision, rebiorth, passes, segment, graphs=int(bool(on)))
 
 
 def debug_inject(kind: str, step: int = 0, precision: str = "fp64", rebiorth: int = 1, passes: int = 2,

@@ -19,6 +19,14 @@ constexpr int NB = 8;     // basis vectors per block in the projection dots
 
 static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// Threads per block of the per-step site kernels: a lattice with fewer than 152
+// blocks of 128 sites would leave most SMs idle (the FP64 work per site keeps a
+// block busy for ~100 us on the 4x4^3 workload), so below that it runs one warp
+// per block and spreads over four times as many SMs.  The per-source partial-sum
+// buffer (Lat::part) is sized for 32-thread blocks.
+constexpr int64_t kSmallV = 152 * 128;
+static inline int site_bs(int64_t V) { return V < kSmallV ? 32 : BS; }
+
 // Site of this thread.  MAP 0: consecutive sites.  MAP 1 ("plane" tiles): block b
 // owns the whole x-y plane b (Nx*Ny sites), so the +-x and +-y neighbours and their
 // links are read by threads of the same block and are served by L1.
@@ -616,7 +624,7 @@ __global__ void __launch_bounds__(BS) k_tsl_init(Lat<R> L) {
 }
 template <typename R>
 void tsl_init(const Lat<R>& L, cudaStream_t st) {
-  k_tsl_init<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L);
+  k_tsl_init<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L);
 }
 
 // ---------------------------------------------------------------------------
@@ -765,8 +773,8 @@ static void launch_pair(const Lat<R>& L, int j, int q, cudaStream_t st) {
     launch_pair<R, PAIR, 128, 0>(L, j, q, st);
     return;
   }
-  const unsigned bs = MAP == 1 ? plane_threads(L.g) : BSZ;
-  const unsigned gx = MAP == 1 ? (unsigned)(L.g.V / (L.g.nx * L.g.ny)) : nblocks(L.g.V, BSZ);
+  const unsigned bs = MAP == 1 ? plane_threads(L.g) : (unsigned)std::min(BSZ, site_bs(L.g.V));
+  const unsigned gx = MAP == 1 ? (unsigned)(L.g.V / (L.g.nx * L.g.ny)) : nblocks(L.g.V, (int)bs);
   k_tsl_stencil<R, PAIR, BSZ, MAP><<<dim3(gx, L.nsrc), bs, 0, st>>>(L, j, q);
 }
 
@@ -840,7 +848,7 @@ __global__ void __launch_bounds__(BS) k_tsl_update(Lat<R> L, int j, int finalize
 }
 template <typename R>
 void tsl_update(const Lat<R>& L, int j, bool finalize, cudaStream_t st) {
-  k_tsl_update<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, j, finalize ? 1 : 0);
+  k_tsl_update<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L, j, finalize ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1013,12 +1021,13 @@ void proj_dots(const Lat<R>& L, int j, int mode, const R* a, const R* b, int64_t
 template <typename R>
 void proj_update(const Lat<R>& L, int j, int mode, R* a, R* b, int64_t ab_stride, const zd* coef, bool finalize,
                  cudaStream_t st, bool small) {
-  const dim3 grid(nblocks(L.g.V, BS), L.nsrc);
+  const int bs = site_bs(L.g.V);
+  const dim3 grid(nblocks(L.g.V, bs), L.nsrc);
   if (small && sizeof(R) == 8)
-    k_proj_update<R, true><<<grid, BS, 0, st>>>(L, j + 1, mode, a, b, ab_stride, coef, 2 * (int64_t)L.k, j,
+    k_proj_update<R, true><<<grid, bs, 0, st>>>(L, j + 1, mode, a, b, ab_stride, coef, 2 * (int64_t)L.k, j,
                                                 finalize ? 1 : 0);
   else
-    k_proj_update<R, false><<<grid, BS, 0, st>>>(L, j + 1, mode, a, b, ab_stride, coef, 2 * (int64_t)L.k, j,
+    k_proj_update<R, false><<<grid, bs, 0, st>>>(L, j + 1, mode, a, b, ab_stride, coef, 2 * (int64_t)L.k, j,
                                                  finalize ? 1 : 0);
 }
 
@@ -1081,7 +1090,7 @@ __global__ void __launch_bounds__(BS) k_combine(Lat<R> L, int j0, int nvec, cons
 }
 template <typename R>
 void combine_range(const Lat<R>& L, int j0, int nvec, const zd* y, double* out, bool acc, cudaStream_t st) {
-  k_combine<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, j0, nvec, y, out, acc ? 1 : 0);
+  k_combine<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L, j0, nvec, y, out, acc ? 1 : 0);
 }
 template <typename R>
 void combine(const Lat<R>& L, int nvec, const zd* y, double* out, cudaStream_t st) {
@@ -1141,7 +1150,7 @@ __global__ void __launch_bounds__(BS) k_rev_dots(Lat<R> L, Rev<R> B, int j) {
 }
 template <typename R>
 void rev_dots(const Lat<R>& L, const Rev<R>& B, int j, cudaStream_t st) {
-  k_rev_dots<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j);
+  k_rev_dots<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L, B, j);
 }
 
 // D1 = v_j^dag g_r, D2 = w_j^dag g_s, D3 = v_{j-1}^dag g_r, D4 = w_{j-1}^dag g_s -> g_alpha, carries
@@ -1213,7 +1222,8 @@ __global__ void __launch_bounds__(BS) k_rev_form(Lat<R> L, Rev<R> B, int j, int 
 }
 template <typename R>
 void rev_form(const Lat<R>& L, const Rev<R>& B, int j, int slot, bool with_dots, cudaStream_t st) {
-  k_rev_form<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j, slot, with_dots ? 1 : 0);
+  k_rev_form<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L, B, j, slot,
+                                                                                   with_dots ? 1 : 0);
 }
 
 // the four dots after the projection adjoint has been applied to g_r, g_s
@@ -1243,7 +1253,7 @@ __global__ void __launch_bounds__(BS) k_rev_alpha_dots(Lat<R> L, Rev<R> B, int j
 }
 template <typename R>
 void rev_alpha_dots(const Lat<R>& L, const Rev<R>& B, int j, int slot, cudaStream_t st) {
-  k_rev_alpha_dots<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j, slot);
+  k_rev_alpha_dots<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L, B, j, slot);
 }
 
 // Lazy projection-adjoint coefficients of recorded projection m (at step j):
@@ -1316,7 +1326,7 @@ __global__ void __launch_bounds__(BS) k_rev_combine(Lat<R> L, Rev<R> B, int j, i
 }
 template <typename R>
 void rev_combine(const Lat<R>& L, const Rev<R>& B, int j, int slot, cudaStream_t st) {
-  k_rev_combine<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j, slot);
+  k_rev_combine<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L, B, j, slot);
 }
 
 // R3b: complete gradients of v_j and w_j
@@ -1375,7 +1385,8 @@ __global__ void __launch_bounds__(BS) k_rev_stencil(Lat<R> L, Rev<R> B, int j, i
 }
 template <typename R>
 void rev_stencil(const Lat<R>& L, const Rev<R>& B, int j, int slot, int prev_slot, int nrec, cudaStream_t st) {
-  k_rev_stencil<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, B, j, slot, prev_slot, nrec);
+  k_rev_stencil<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L, B, j, slot,
+                                                                                      prev_slot, nrec);
 }
 
 // ---------------------------------------------------------------------------

@@ -77,6 +77,16 @@ struct ov_context {
   int tuned_pair[2] = {0, 0};
   bool owns_stream = false;     // worker contexts of ov_tsl_batch own theirs
   std::vector<ov_context*> workers;
+  // captured sweeps (options.graphs): key of the captured call shape, executable graph,
+  // kernels it launches; the capture stream and the events ordering it with `st`
+  struct SweepGraph {
+    std::vector<unsigned char> key;    // shape of the captured graph
+    std::vector<unsigned char> seen;   // shape of the last call launched directly
+    cudaGraphExec_t exec = nullptr;
+    int64_t nlaunch = 0;
+  } gfwd, grev;
+  cudaStream_t cap_st = nullptr;
+  cudaEvent_t cap_ev[2] = {nullptr, nullptr};
   // one-shot host-side fault injection (ov_debug_inject)
   int inj_kind = OV_INJECT_NONE, inj_step = 0;
   int inj_word[2] = {0, 0};     // host copy of the error word written by an injected breakdown
@@ -125,6 +135,69 @@ void free_buf(ov_context* c, int id) {
   c->buf[id] = nullptr;
   c->cap[id] = 0;
   c->host_buf[id] = false;
+}
+
+// Append the bytes of a plain value to a graph key.
+template <typename T>
+void key_add(std::vector<unsigned char>& key, const T& v) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+  key.insert(key.end(), p, p + sizeof(T));
+}
+
+// Run `enqueue` (kernel launches on c->st only, no allocation, no host copy, no
+// synchronisation) directly, or through a CUDA graph: a key seen for the first time
+// runs directly; when the next call repeats it, that call is captured (so a shape
+// used once never pays for a capture), and later calls with the key replay the
+// graph.  The capture runs on a private non-blocking stream (the legacy default
+// stream cannot be captured), ordered with c->st by events; a replay costs one
+// graph launch instead of one launch per kernel.
+template <typename F>
+void captured(ov_context* c, ov_context::SweepGraph& g, const std::vector<unsigned char>& key, F&& enqueue) {
+  const bool can = c->opt.graphs && !(c->prof && c->prof->on) && c->inj_kind == OV_INJECT_NONE;
+  if (!can || (!(g.exec && g.key == key) && g.seen != key)) {
+    if (can) g.seen = key;
+    enqueue();
+    return;
+  }
+  if (!c->cap_st) {
+    CK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->cap_ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->cap_ev[1], cudaEventDisableTiming));
+  }
+  if (!(g.exec && g.key == key)) {
+    if (g.exec) {
+      CK(cudaGraphExecDestroy(g.exec));
+      g.exec = nullptr;
+    }
+    cudaStream_t user = c->st;
+    const int64_t l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
+    c->st = c->cap_st;
+    cudaGraph_t graph = nullptr;
+    try {
+      enqueue();
+    } catch (...) {
+      c->st = user;
+      cudaStreamEndCapture(c->cap_st, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      throw;
+    }
+    c->st = user;
+    CK(cudaStreamEndCapture(c->cap_st, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    g.key = key;
+    g.nlaunch = c->launches - l0;
+    c->launches = l0;
+  }
+  CK(cudaEventRecord(c->cap_ev[0], c->st));
+  CK(cudaStreamWaitEvent(c->cap_st, c->cap_ev[0], 0));
+  CK(cudaGraphLaunch(g.exec, c->cap_st));
+  CK(cudaEventRecord(c->cap_ev[1], c->cap_st));
+  CK(cudaStreamWaitEvent(c->st, c->cap_ev[1], 0));
+  c->launches += g.nlaunch;
 }
 
 void* ws(ov_context* c, int id, size_t bytes, bool zero = false) {
@@ -236,7 +309,9 @@ Lat<R> setup(ov_context* c, const int32_t dims[4], const void* U, double mu, dou
   L.alpha = wsT<zd>(c, B_ALPHA, (int64_t)nsrc * k);
   L.beta = wsT<zd>(c, B_BETA, (int64_t)nsrc * k);
   L.delta = wsT<double>(c, B_DELTA, (int64_t)nsrc * k);
-  const int64_t nblk = (Vf + 127) / 128;
+  // room for up to 8 partial values per block of the site kernels (blocks of 32
+  // threads on small lattices)
+  const int64_t nblk = (Vf + 31) / 32;
   L.part_stride = 8 * (nblk < 64 ? 64 : nblk);
   L.part = wsT<zd>(c, B_PART, nsrc * L.part_stride);
   L.cnt = wsT<unsigned>(c, B_CNT, (int64_t)nsrc * 16);
@@ -289,23 +364,32 @@ void forward_krylov(ov_context* c, Lat<R>& L) {
   const int64_t nsb = (L.g.V + 127) / 128;
   zd* coef = wsT<zd>(c, B_COEF, (int64_t)L.nsrc * 2 * k);
   zd* cpart = wsT<zd>(c, B_CPART, (int64_t)L.nsrc * 2 * k * nsb);
-  run(c, OV_KIND_UPDATE, 1, [&] { tsl_init(L, c->st); });
-  for (int j = 0; j < k; ++j) {
-    run(c, OV_KIND_STENCIL_PAIR, 1, [&] { tsl_stencil(L, j, j < k - 1, c->st, c->tuned_pair[c->opt.precision]); });
-    inject_after_stencil(c, L, j);
-    if (j == k - 1) break;
-    const int reb = rebiorth_at(j + 1, c->opt.rebiorth);
-    run(c, OV_KIND_UPDATE, 1, [&] { tsl_update(L, j, !reb, c->st); });
-    if (reb) {
-      for (int ps = 0; ps < c->opt.passes; ++ps) {
-        run(c, OV_KIND_PROJ_DOTS, 2, [&] { proj_dots(L, j, 0, L.r, L.s, L.vs, coef, cpart, c->st); });
-        run(c, OV_KIND_PROJ_UPDATE, 1,
-            [&] { proj_update(L, j, 0, L.r, L.s, L.vs, coef, ps == c->opt.passes - 1, c->st, ps > 0); });
+  std::vector<unsigned char> key;
+  key_add(key, L);
+  key_add(key, coef);
+  key_add(key, cpart);
+  key_add(key, c->opt);
+  key_add(key, c->tuned_pair[c->opt.precision]);
+  captured(c, c->gfwd, key, [&] {
+    run(c, OV_KIND_UPDATE, 1, [&] { tsl_init(L, c->st); });
+    for (int j = 0; j < k; ++j) {
+      run(c, OV_KIND_STENCIL_PAIR, 1,
+          [&] { tsl_stencil(L, j, j < k - 1, c->st, c->tuned_pair[c->opt.precision]); });
+      inject_after_stencil(c, L, j);
+      if (j == k - 1) break;
+      const int reb = rebiorth_at(j + 1, c->opt.rebiorth);
+      run(c, OV_KIND_UPDATE, 1, [&] { tsl_update(L, j, !reb, c->st); });
+      if (reb) {
+        for (int ps = 0; ps < c->opt.passes; ++ps) {
+          run(c, OV_KIND_PROJ_DOTS, 2, [&] { proj_dots(L, j, 0, L.r, L.s, L.vs, coef, cpart, c->st); });
+          run(c, OV_KIND_PROJ_UPDATE, 1,
+              [&] { proj_update(L, j, 0, L.r, L.s, L.vs, coef, ps == c->opt.passes - 1, c->st, ps > 0); });
+        }
       }
+      inject_after_update(c, L, j);
     }
-    inject_after_update(c, L, j);
-  }
-  launch_check();
+    launch_check();
+  });
 }
 
 // Run diagnostics (options.diagnostics) after a forward recurrence whose
@@ -1214,6 +1298,7 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
   B.dmu_part = wsT<zd>(c, B_DMUPART, kForceSplitMax * ((V + 127) / 128) + 64);
   B.dmu_cnt = wsT<unsigned>(c, B_DMUCNT, 4);
   zd* coef = wsT<zd>(c, B_COEF, (int64_t)nsrc * 2 * k);
+  auto sweep = [&] {
   run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_init(L, B, c->st); });
   run(c, OV_KIND_REV_SCALAR, 1, [&] { rev_combine(L, B, k - 1, 0, c->st); });
   run(c, OV_KIND_REV_STENCIL, 1, [&] { rev_stencil(L, B, k - 1, 0, -1, 0, c->st); });
@@ -1254,6 +1339,20 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
     ++slot;
   }
   run(c, OV_KIND_FORCE, 4, [&] { force_flush(L, B, nullptr, slot, j0, c->st); });
+  };
+  if (S > 0) {
+    sweep();   // segment replays copy checkpoints between the steps: launched directly
+  } else {
+    std::vector<unsigned char> key;
+    const Rev<R> B0 = B;   // the sweep swaps B's gradient buffers: key on its state at entry
+    key_add(key, L);
+    key_add(key, B0);
+    key_add(key, coef);
+    key_add(key, cpart);
+    key_add(key, c->opt);
+    key_add(key, xb);
+    captured(c, c->grev, key, sweep);
+  }
   CK(cudaEventRecord(c->ev[5], c->st));
   run(c, OV_KIND_LAYOUT, 1, [&] { unpack_force(B.force, static_cast<double*>(dU), V, c->st); });
   launch_check();
@@ -1591,7 +1690,7 @@ bool valid_options(const ov_options* o) {
   return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4 &&
          o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0) && (o->dense == 0 || o->dense == 1) &&
          (o->diagnostics == 0 || o->diagnostics == 1) && (o->newton == 0 || o->newton == 1) &&
-         (o->basis_memory == 0 || o->basis_memory == 1);
+         (o->basis_memory == 0 || o->basis_memory == 1) && (o->graphs == 0 || o->graphs == 1);
 }
 
 // x = V_k y from a forward state (a second pass over the segments if there are any)
@@ -1633,6 +1732,7 @@ int ov_context_create(ov_context** ctx, const ov_options* opt, void* stream) {
   o.precision = OV_FP64;
   o.rebiorth = 1;
   o.passes = 2;
+  o.graphs = 1;
   if (opt) {
     if (!valid_options(opt)) return OV_ERR_INVALID_ARG;
     o = *opt;
@@ -1657,6 +1757,12 @@ int ov_context_destroy(ov_context* c) {
   for (ov_context* w : c->workers) ov_context_destroy(w);
   c->workers.clear();
   cudaStreamSynchronize(c->st);
+  if (c->cap_st) cudaStreamSynchronize(c->cap_st);
+  if (c->gfwd.exec) cudaGraphExecDestroy(c->gfwd.exec);
+  if (c->grev.exec) cudaGraphExecDestroy(c->grev.exec);
+  for (auto& e : c->cap_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   for (int i = 0; i < NBUF; ++i) {
     if (!c->buf[i]) continue;
     if (c->host_buf[i])

@@ -366,6 +366,34 @@ def test_uneven_batch_equals_single_calls():
             assert torch.equal(r["x"], x) and torch.equal(r["dU"], du) and r["dmu"] == dmu
 
 
+def test_uneven_batch_against_the_oracle():
+    """An uneven batch at the workloads' mass (m_w = -2): three lattices, three values
+    of mu, different k and source counts, forward + VJP each, on four workers, every
+    problem against the FP64 oracle (x per source, dU and dmu of the summed loss)
+    within 10x the largest rounding floor the oracle measures for these maps (b
+    perturbed by 1e-16: x 1.7e-11, dU 2.1e-9, dmu 3.3e-9, on the 2x3x4x5 problem)."""
+    specs = [((4, 4, 4, 4), 0.1, 120, 1), ((3, 5, 2, 4), 0.3, 90, 2), ((2, 3, 4, 5), 0.5, 150, 1)]
+    probs, refs = [], []
+    for n, (dims, mu, k, nsrc) in enumerate(specs):
+        u, b, xbar = case(dims, 0.2, 40 + n, nsrc)
+        probs.append(dict(u=T(u), mu=mu, m_w=-2.0, b=T(b), k=k, xbar=T(xbar)))
+        xs, du, dmu = [], np.zeros_like(u), 0.0
+        for s in range(nsrc):
+            f = tsl.tsl_forward(u, b[s], mu, -2.0, k, rebiorth=20, passes=1)
+            d, m, _ = vjp.tsl_vjp(u, b[s], mu, -2.0, k, xbar[s], rebiorth=20, passes=1, fwd=f)
+            xs.append(f.x)
+            du += d
+            dmu += m
+        refs.append((xs, du, dmu))
+    res = binding.tsl_batch(probs, nworkers=4, rebiorth=20, passes=1)
+    for (xs, du, dmu), r in zip(refs, res):
+        assert r["status"] == 0
+        for s, xo in enumerate(xs):
+            assert rel(r["x"][s].cpu().numpy(), xo) <= 2e-10
+        assert rel(r["dU"].cpu().numpy(), du) <= 3e-8
+        assert abs(r["dmu"] - dmu) <= 3e-8 * abs(dmu)
+
+
 def test_uneven_batch_reports_each_problem_status():
     u, b, _ = case((3, 3, 3, 3), 0.3, 23, 1)
     good = dict(u=T(u), mu=0.3, m_w=-1.0, b=T(b[0]), k=30)
