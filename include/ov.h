@@ -108,6 +108,18 @@ typedef struct {
                         * sweeps launch ~10 kernels per step); results are bit for bit those of
                         * direct launches.  Not used while per-kernel profiling or a fault
                         * injection is active, or with segments.  0: direct launches. */
+  int32_t gemm;        /* complex k x k products of the Frechet adjoint's iteration (Theorem 1;
+                        * also the block forward mode of ov_block_tsl_sign / ov_tsl_sign_jvp):
+                        * 0 (default): on the BF16 tensor cores for 128 <= k <= 1024, by an exact
+                        * splitting of each FP64 operand into ten 7-bit integer digits below a
+                        * per-row (left factor) or per-column (right factor) power-of-two scale
+                        * (Ozaki scheme; the 55 digit products with p + q <= 11, summed exactly
+                        * in integers, at most two FP64 roundings per real product: error per
+                        * entry <~ 4u (|L||R|)_ij + 12 k 2^-70 max_l |L_il| max_l |R_lj|, the
+                        * size of FP64 rounding for lines spanning up to ~2^17 in magnitude),
+                        * else FP64 arithmetic; 1: FP64 arithmetic always; 2: the tensor-core
+                        * form wherever k <= 1024.  Needs ~930 k^2 bytes of device workspace
+                        * (0.6 GB at k = 800). */
 } ov_options;
 
 typedef struct {
@@ -396,6 +408,19 @@ int ov_u1_current(ov_context *ctx, const int32_t dims[4], const void *U, double 
  * (no convergence, or a rotation that would break down). */
 int ov_tridiag_eigenvalues(int32_t k, const double *alpha, const double *beta, const double *delta,
                            double *eig);
+
+/* One complex k x k product of the kind the Frechet adjoint's iteration forms
+ * (Theorem 1: X_i^{-H} E X_i^{-H} and sgn(T)^H E sgn(T)^H):
+ * C = op(A) op(B), op = identity (flag 0) or conjugate transpose (flag 1).
+ * A, B, C: device arrays of k x k complex128, row-major, interleaved
+ * (re, im), 16-byte aligned; C must not overlap A or B.  mode 1: FP64
+ * arithmetic; mode 2: the BF16 tensor-core form of options.gemm (exact digit
+ * splitting; k <= 1024).  Runs on the context's stream and returns when the
+ * product is complete.  Returns OV_OK, OV_ERR_INVALID_ARG (k < 1, mode not 1
+ * or 2, mode 2 with k > 1024, a null or misaligned pointer), OV_ERR_OOM
+ * (workspace) or OV_ERR_CUDA (a launch or cuBLAS failure). */
+int ov_kk_gemm(ov_context *ctx, const void *A, int32_t hA, const void *B, int32_t hB, void *C, int32_t k,
+               int32_t mode);
 
 /* Host-side fault injection for tests of error propagation (no GPU fault is
  * caused: the library writes an ordinary value, or fails an allocation, on

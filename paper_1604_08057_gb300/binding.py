@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("dense", ctypes.c_int32),
                 ("diagnostics", ctypes.c_int32), ("newton", ctypes.c_int32),
-                ("basis_memory", ctypes.c_int32), ("graphs", ctypes.c_int32)]
+                ("basis_memory", ctypes.c_int32), ("graphs", ctypes.c_int32), ("gemm", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -69,7 +69,7 @@ EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", 
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
            "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_overlap_apply", "ov_overlap_solve", "ov_u1_current",
-           "ov_strerror"]
+           "ov_kk_gemm", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
                                      ctypes.POINTER(D)]
     lib.ov_u1_current.argtypes = [P, dims_t, P, D, D, I32, P, I32, D, I32, P, ctypes.POINTER(D), ctypes.POINTER(Info)]
     lib.ov_debug_inject.argtypes = [P, I32, I32]
+    lib.ov_kk_gemm.argtypes = [P, P, I32, P, I32, P, I32, I32]
     lib.ov_launch_count.argtypes = [P]
     lib.ov_launch_count.restype = ctypes.c_int64
     lib.ov_strerror.argtypes = [ctypes.c_int]
@@ -150,10 +151,11 @@ _extra = {}   # per cached context: the options not in its key (dense, diagnosti
 def _set_extra(precision, rebiorth, passes, segment, **kw):
     ctx = context(precision, rebiorth, passes, segment=segment)
     key = (precision, rebiorth, passes, segment, ctx.value)
-    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0, "newton": 0, "basis_memory": 0, "graphs": 1})
+    ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0, "newton": 0, "basis_memory": 0, "graphs": 1,
+                                 "gemm": 0})
     ex.update({k: int(v) for k, v in kw.items()})
     opt = Options(_PREC[precision], rebiorth, passes, segment, ex["dense"], ex["diagnostics"], ex["newton"],
-                  ex["basis_memory"], ex["graphs"])
+                  ex["basis_memory"], ex["graphs"], ex["gemm"])
     _check(load().ov_context_set_options(ctx, ctypes.byref(opt)), "ov_context_set_options")
     return ctx
 
@@ -187,6 +189,13 @@ def sweep_graphs(on: bool, precision: str = "fp64", rebiorth: int = 1, passes: i
     """Capture and replay the Krylov sweeps as CUDA graphs on the cached context (on by
     default) or launch every kernel directly; the results are the same bit for bit."""
     _set_extra(precision, rebiorth, passes, segment, graphs=int(bool(on)))
+
+
+def kk_products(mode: str, precision: str = "fp64", rebiorth: int = 1, passes: int = 2, segment: int = 0):
+    """How the cached context forms the k x k products of the Frechet adjoint:
+    "auto" (default: BF16 tensor cores by exact digit splitting for 128 <= k <= 1024,
+    else FP64), "fp64", or "split" (the tensor-core form wherever k <= 1024)."""
+    _set_extra(precision, rebiorth, passes, segment, gemm={"auto": 0, "fp64": 1, "split": 2}[mode])
 
 
 def debug_inject(kind: str, step: int = 0, precision: str = "fp64", rebiorth: int = 1, passes: int = 2,
@@ -259,6 +268,23 @@ def tridiag_eigenvalues(alpha, beta, delta):
     _check(load().ov_tridiag_eigenvalues(k, a.ctypes.data, b.ctypes.data, d.ctypes.data, out.ctypes.data),
            "ov_tridiag_eigenvalues")
     return out
+
+
+def kk_gemm(a, b, ha=False, hb=False, mode="split"):
+    """C = op(a) op(b) for complex128 CUDA k x k matrices (op = conjugate transpose
+    when the flag is set), by FP64 arithmetic ("fp64") or the BF16 tensor-core digit
+    splitting ("split", k <= 1024) of the Frechet adjoint's products."""
+    for m in (a, b):
+        if m.dtype != torch.complex128 or not m.is_cuda or m.dim() != 2 or m.shape[0] != m.shape[1]:
+            raise ValueError("a and b must be square complex128 CUDA matrices")
+    if a.shape != b.shape:
+        raise ValueError("a and b must have the same shape")
+    a, b = a.contiguous(), b.contiguous()
+    c = torch.empty_like(a)
+    ctx = context("fp64", 1, 2, device=a.device.index)
+    _check(load().ov_kk_gemm(ctx, a.data_ptr(), int(bool(ha)), b.data_ptr(), int(bool(hb)), c.data_ptr(),
+                             a.shape[0], {"fp64": 1, "split": 2}[mode]), "ov_kk_gemm")
+    return c
 
 
 def _dims(u: torch.Tensor):

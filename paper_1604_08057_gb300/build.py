@@ -18,7 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libov.so")
-SOURCES = ["lattice_kernels.cu", "dense_kernels.cu", "ov_api.cu", "noalloc.cu", "tridiag.cu", "overlap_kernels.cu"]
+SOURCES = ["lattice_kernels.cu", "dense_kernels.cu", "ov_api.cu", "noalloc.cu", "tridiag.cu", "overlap_kernels.cu",
+           "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]
@@ -59,7 +60,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(res.stdout, res.stderr)
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in sources]
     if force or jobs or _stale(LIB, objs):
-        res = subprocess.run([nvcc, *ARCH, "-shared", "-o", LIB, *objs], capture_output=True, text=True)
+        # cuBLAS (the BF16 digit GEMMs of ozaki.cu), found at run time beside the toolkit
+        cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+        res = subprocess.run([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcublas", "-Xlinker", f"-rpath={cuda_lib}"],
+                             capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
     return LIB

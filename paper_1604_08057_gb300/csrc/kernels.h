@@ -161,6 +161,15 @@ void dense_gemm(const zd* A, const zd* B, zd* C, int k, cudaStream_t st);   // C
 void dense_gemm_op(const zd* A, int hA, const zd* B, int hB, zd* C, int k, cudaStream_t st);
 void dense_gemm_batch(const zd* A, int64_t sA, int hA, const zd* B, int64_t sB, int hB, zd* C, int64_t sC, int k,
                       int nb, const int* act, cudaStream_t st);
+// C = op(A) op(B) for one k x k problem on the BF16 tensor cores by the exact digit
+// splitting of ozaki.cu (k <= OZ_MAX_K); ws holds oz_workspace_bytes(k) device bytes,
+// handle is a cuBLAS handle from oz_create_handle.  Returns the number of own kernels
+// launched, or < 0 (-1 k out of range, -2 launch error, -3 cuBLAS error).
+constexpr int OZ_MAX_K = 1024;
+size_t oz_workspace_bytes(int k);
+int oz_zgemm(void* handle, const zd* A, int hA, const zd* B, int hB, zd* C, int k, void* ws, cudaStream_t st);
+void* oz_create_handle();
+void oz_destroy_handle(void* handle);
 // C (M x N) = op(A) op(B) with leading dimensions (op = conjugate transpose when the flag is set)
 void dense_gemm_rect_batch(const zd* A, int64_t sA, int lda, int hA, const zd* B, int64_t sB, int ldb, int hB, zd* C,
                            int64_t sC, int ldc, int M, int N, int K, int nb, const int* act, cudaStream_t st);

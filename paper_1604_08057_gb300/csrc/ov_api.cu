@@ -22,7 +22,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, NBUF
 };
 
 struct Status {
@@ -91,6 +91,7 @@ struct ov_context {
   int inj_kind = OV_INJECT_NONE, inj_step = 0;
   int inj_word[2] = {0, 0};     // host copy of the error word written by an injected breakdown
   double inj_nan[2] = {0.0, 0.0};
+  void* blas = nullptr;         // cuBLAS handle of the tensor-core k x k products (options.gemm)
 };
 
 namespace {
@@ -122,6 +123,34 @@ void run(ov_context* c, int kind, int64_t nl, F&& f) {
     p->kind[p->n++] = kind;
   }
   c->launches += nl;
+}
+
+void* ws(ov_context* c, int id, size_t bytes, bool zero);
+
+// C_p = op(A_p) op(B_p), k x k complex, for the problems p < nb with act[p] set (all
+// when act is null; act_dev is the device copy): on the BF16 tensor cores by the exact
+// digit splitting (options.gemm), else FP64 arithmetic
+void kk_gemm(ov_context* c, const zd* A, int64_t sA, int hA, const zd* B, int64_t sB, int hB, zd* C, int64_t sC,
+             int k, int nb, const std::vector<int>* act, const int* act_dev) {
+  const bool split = k <= OZ_MAX_K && (c->opt.gemm == 2 || (c->opt.gemm == 0 && k >= 128));
+  if (!split) {
+    run(c, OV_KIND_DENSE_GEMM, 1,
+        [&] { dense_gemm_batch(A, sA, hA, B, sB, hB, C, sC, k, nb, act ? act_dev : nullptr, c->st); });
+    return;
+  }
+  if (!c->blas) {
+    c->blas = oz_create_handle();
+    if (!c->blas) throw Status{OV_ERR_CUDA};
+  }
+  void* w = ws(c, B_OZ, oz_workspace_bytes(k), false);
+  for (int p = 0; p < nb; ++p) {
+    if (act && !(*act)[p]) continue;
+    run(c, OV_KIND_DENSE_GEMM, 0, [&] {
+      const int r = oz_zgemm(c->blas, A + p * sA, hA, B + p * sB, hB, C + p * sC, k, w, c->st);
+      if (r < 0) throw Status{OV_ERR_CUDA};
+      c->launches += r;
+    });
+  }
 }
 
 void free_buf(ov_context* c, int id) {
@@ -630,10 +659,8 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
       }
     }
     if (e) {
-      run(c, OV_KIND_DENSE_GEMM, 2, [&] {
-        dense_gemm(ai, e[cur], t1, k, c->st);
-        dense_gemm(t1, ai, t2, k, c->st);
-      });
+      kk_gemm(c, ai, 0, 0, e[cur], 0, 0, t1, 0, k, 1, nullptr, nullptr);
+      kk_gemm(c, t1, 0, 0, ai, 0, 0, t2, 0, k, 1, nullptr, nullptr);
     }
     // the block determinant is det(A)^2: its 1/(2k)-th root is det(A)^(1/k)
     run(c, OV_KIND_DENSE, e ? 2 : 1, [&] {
@@ -1165,10 +1192,8 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
       for (int src = 0; src < nsrc; ++src) act[src] = F.rec_ok[src] && i < F.iters[src];
       CK(cudaMemcpyAsync(act_dev, act.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, c->st));
       const zd* yi = F.rec_inv + (int64_t)i * n;
-      run(c, OV_KIND_DENSE_GEMM, 2, [&] {
-        dense_gemm_batch(yi, (int64_t)NREC * n, 1, e[ce], n, 0, t1, n, k, nsrc, act_dev, c->st);
-        dense_gemm_batch(t1, n, 0, yi, (int64_t)NREC * n, 1, t2, n, k, nsrc, act_dev, c->st);
-      });
+      kk_gemm(c, yi, (int64_t)NREC * n, 1, e[ce], n, 0, t1, n, k, nsrc, &act, act_dev);
+      kk_gemm(c, t1, n, 0, yi, (int64_t)NREC * n, 1, t2, n, k, nsrc, &act, act_dev);
       run(c, OV_KIND_DENSE, 1, [&] {
         dense_newton_combine_batch(e[ce], t2, e[1 - ce], k, nsrc, act_dev, F.rec_ld + i, NREC, rscal + i, NREC, -1.0,
                                    1.0, dstat, dpart, pstride, dcnt, c->st);
@@ -1186,10 +1211,8 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
       const int ce = (x - 1) & 1;
       CK(cudaMemcpyAsync(act_dev, act.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, c->st));
       CK(cudaMemsetAsync(dstat, 0, sizeof(double) * 4 * nsrc, c->st));
-      run(c, OV_KIND_DENSE_GEMM, 2, [&] {
-        dense_gemm_batch(F.fsign, n, 1, e[ce], n, 0, t1, n, k, nsrc, act_dev, c->st);
-        dense_gemm_batch(t1, n, 0, F.fsign, n, 1, t2, n, k, nsrc, act_dev, c->st);
-      });
+      kk_gemm(c, F.fsign, n, 1, e[ce], n, 0, t1, n, k, nsrc, &act, act_dev);
+      kk_gemm(c, t1, n, 0, F.fsign, n, 1, t2, n, k, nsrc, &act, act_dev);
       run(c, OV_KIND_DENSE, 1, [&] {
         dense_newton_combine_batch(e[ce], t2, e[1 - ce], k, nsrc, act_dev, dstat + 2, 4, nullptr, 0, -1.0, 1.0,
                                    dstat, dpart, pstride, dcnt, c->st);
@@ -1690,7 +1713,8 @@ bool valid_options(const ov_options* o) {
   return o->precision >= 0 && o->precision <= 1 && o->rebiorth >= 0 && o->passes >= 1 && o->passes <= 4 &&
          o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0) && (o->dense == 0 || o->dense == 1) &&
          (o->diagnostics == 0 || o->diagnostics == 1) && (o->newton == 0 || o->newton == 1) &&
-         (o->basis_memory == 0 || o->basis_memory == 1) && (o->graphs == 0 || o->graphs == 1);
+         (o->basis_memory == 0 || o->basis_memory == 1) && (o->graphs == 0 || o->graphs == 1) &&
+         o->gemm >= 0 && o->gemm <= 2;
 }
 
 // x = V_k y from a forward state (a second pass over the segments if there are any)
@@ -1763,6 +1787,7 @@ int ov_context_destroy(ov_context* c) {
   for (auto& e : c->cap_ev)
     if (e) cudaEventDestroy(e);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
+  oz_destroy_handle(c->blas);
   for (int i = 0; i < NBUF; ++i) {
     if (!c->buf[i]) continue;
     if (c->host_buf[i])
@@ -2112,6 +2137,31 @@ int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, do
                        cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemcpyAsync(delta, static_cast<double*>(c->buf[B_DELTA]) + (int64_t)src * k, sizeof(double) * k,
                        cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return OV_OK;
+  });
+}
+
+int ov_kk_gemm(ov_context* c, const void* A, int32_t hA, const void* B, int32_t hB, void* C, int32_t k,
+               int32_t mode) {
+  if (!c || k < 1 || (mode != 1 && mode != 2) || (mode == 2 && k > OZ_MAX_K) || (hA != 0 && hA != 1) ||
+      (hB != 0 && hB != 1))
+    return OV_ERR_INVALID_ARG;
+  return guarded([&] {
+    check_ptr(A);
+    check_ptr(B);
+    check_ptr(C);
+    const int saved = c->opt.gemm;
+    c->opt.gemm = mode;
+    try {
+      kk_gemm(c, static_cast<const zd*>(A), 0, hA, static_cast<const zd*>(B), 0, hB, static_cast<zd*>(C), 0, k, 1,
+              nullptr, nullptr);
+    } catch (...) {
+      c->opt.gemm = saved;
+      throw;
+    }
+    c->opt.gemm = saved;
+    launch_check();
     CK(cudaStreamSynchronize(c->st));
     return OV_OK;
   });
