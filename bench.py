@@ -348,6 +348,7 @@ def run_ours(args, rank, world, local_rank):
         out["mixed_path"] = mixed_leg(args, ut, bt, xt, wl, k, u, b, xbar)
         out["schedule_compare"] = schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x)
         out["diagnostics"] = diagnostics_leg(args, ut, bt, xt, wl, k, ms_total / args.steps)
+        out["kk_products"] = kk_products_leg(args, ut, bt, xt, wl, k, du, dmu, x, ms_total / args.steps)
         out["basis_in_host_memory"] = host_basis_leg(args, ut, bt, xt, wl, k, du, dmu, x)
         out["other_workloads"] = other_workloads_leg(args)
         if world == 1:
@@ -485,6 +486,31 @@ def host_basis_leg(args, ut, bt, xt, wl, k, du, dmu, x):
         return {"error": str(exc)}
     finally:
         binding.basis_memory("device", *opts, segment=args.segment)
+
+
+def kk_products_leg(args, ut, bt, xt, wl, k, du, dmu, x, ms_step):
+    """The headline call with the Frechet adjoint's k x k products in FP64 arithmetic
+    instead of the tensor-core digit splitting: its seconds per call and how far its
+    results lie from the headline's (x is the same: the forward pass forms no
+    products)."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    opts = (args.precision, args.rebiorth, args.passes)
+    binding.kk_products("fp64", *opts, segment=args.segment)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        du2, dmu2, x2 = binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt, k, xt, *opts, segment=args.segment)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+        return {"fp64_products_s_per_call": round(dt, 4), "split_products_s_per_call": round(ms_step / 1e3, 4),
+                "x_identical": bool(torch.equal(x2, x)), "rel_dU_fp64_vs_split": rel(du2, du),
+                "rel_dmu_fp64_vs_split": abs(dmu2 - dmu) / abs(dmu2)}
+    except (binding.OVError, RuntimeError) as exc:
+        return {"error": str(exc)}
+    finally:
+        binding.kk_products("auto", *opts, segment=args.segment)
 
 
 def diagnostics_leg(args, ut, bt, xt, wl, k, ms_step):
