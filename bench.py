@@ -63,9 +63,10 @@ def parse_args():
                     help="two-pass TSL with checkpoints every S steps (needs --rebiorth 0)")
     ap.add_argument("--m-w", type=float, default=None, help="override the workload's Wilson mass")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
-    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch"],
+    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch", "kk"],
                     help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling); "
-                         "batch: the uneven batch of 32 problems (forward + VJP) through ov_tsl_batch")
+                         "batch: the uneven batch of 32 problems (forward + VJP) through ov_tsl_batch; "
+                         "kk: one k x k complex product (ov_kk_gemm), FP64 and split, at the workload's k")
     args = ap.parse_args()
     # P = 60 at 14x14^3, k = 800: x within 1e-9 and dU within 1e-4 of the P = 1 result
     # (P = 20: 2e-10 and 4e-4), the same eps_A; the uneven batch keeps P = 20
@@ -488,6 +489,39 @@ def host_basis_leg(args, ut, bt, xt, wl, k, du, dmu, x):
         binding.basis_memory("device", *opts, segment=args.segment)
 
 
+def kk_leg(args, dev_index, reps=5):
+    """One complex k x k product C = A^H B of the Frechet adjoint's kind through
+    ov_kk_gemm, in FP64 arithmetic and by the tensor-core digit splitting: ms per
+    product (CUDA events, after one warm-up each), the rate in FP64-equivalent
+    TFLOP/s (8 k^3 flop), and the largest difference between the two relative to
+    max |C|."""
+    import torch
+    from paper_1604_08057_gb300 import binding
+    k = args.k or workload_of(args).k
+    g = torch.Generator().manual_seed(7)
+    dev = torch.device("cuda", dev_index)
+    a = torch.randn(k, k, dtype=torch.complex128, generator=g).to(dev)
+    b = torch.randn(k, k, dtype=torch.complex128, generator=g).to(dev)
+    out = {"leg": "kk_product", "k": k, "op": "A^H B, complex128"}
+    res = {}
+    for mode in ("fp64", "split"):
+        if mode == "split" and k > 1024:
+            continue
+        res[mode] = binding.kk_gemm(a, b, True, False, mode)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            binding.kk_gemm(a, b, True, False, mode)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[mode] = {"ms_per_product": round(ms, 4), "tflops_fp64_equivalent": round(8 * k**3 / ms / 1e9, 3)}
+    if len(res) == 2:
+        out["max_rel_diff"] = float((res["split"] - res["fp64"]).abs().max() / res["fp64"].abs().max())
+    return out
+
+
 def kk_products_leg(args, ut, bt, xt, wl, k, du, dmu, x, ms_step):
     """The headline call with the Frechet adjoint's k x k products in FP64 arithmetic
     instead of the tensor-core digit splitting: its seconds per call and how far its
@@ -839,6 +873,11 @@ def main():
         print(json.dumps({"leg": "uneven_batch", "precision": args.precision, "rebiorth_period": args.rebiorth,
                           "segment": args.segment,
                           "gs_passes": args.passes, **batch_leg(args)}))
+        return
+    if args.leg == "kk":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps(kk_leg(args, local_rank)))
         return
     if args.leg == "stencil":
         import torch

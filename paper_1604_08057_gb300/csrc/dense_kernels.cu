@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict_
     keys += (int64_t)pb * (k + 1);
     used += (int64_t)pb * k;
     prows += (int64_t)pb * k;
-    logdet += (int64_t)pb * ld_stride;
+    if (logdet) logdet += (int64_t)pb * ld_stride;
   }
   const int i = blockIdx.x;   // the block's row
   const zd* xr = xin + (int64_t)i * k;
@@ -231,9 +231,9 @@ __global__ void __launch_bounds__(GJ_THREADS, 6) k_gj_step(const zd* __restrict_
   if (threadIdx.x == 0) {
     if (bad && i == 0) atomicOr(err, ERRB_SINGULAR);
     if (i == p) {
-      const double a = sqrt(gj_nrm(piv));
-      if (!(a > 0.0) || !isfinite(a)) atomicOr(err, ERRB_SINGULAR);
-      *logdet += log(a);
+      const double nrm = gj_nrm(piv);   // |pivot| = sqrt(nrm) is positive and finite iff nrm is
+      if (!(nrm > 0.0) || !isfinite(nrm)) atomicOr(err, ERRB_SINGULAR);
+      if (logdet) *logdet += log(sqrt(nrm));
       prows[kk] = p;
       used[p] = 1;
     }
@@ -353,8 +353,20 @@ __device__ unsigned long long warp_wait_slots(const unsigned long long* slots, i
   }
 }
 
+// 16-byte asynchronous copy global -> shared (bypassing L1), and its completion
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // JPT: columns per thread (k <= JPT * GJP_THREADS); the pivot row's entries of
-// the thread's columns are held in registers for the bulk update.
+// the thread's columns are held in registers for the bulk update.  While a step's
+// bulk update runs, warp 0 looks once (without waiting) whether every block has
+// published its candidate for the next step; if so, the next pivot row is copied
+// into shared memory in the background, and the next step starts from it instead
+// of waiting for the keys and loading the row.
 template <int JPT>
 __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict__ a, zd* __restrict__ ainv, int k,
                                                           int R, int bp, zd* pub0, zd* pub1,
@@ -366,9 +378,11 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
   zd* pv = xs + (int64_t)R * k;               // the step's pivot row as it stood before the step
   int* prow = reinterpret_cast<int*>(pv + k); // pivot row of each step
   int* qs = prow + k;                         // inverse permutation (at the end)
+  double* pn = reinterpret_cast<double*>(qs + k);   // |pivot|^2 of each step (block 0, for log|det|)
+  zd* pvn = reinterpret_cast<zd*>(pn + k);          // the next step's pivot row, prefetched
   __shared__ zd ms[GJP_RMAX];                 // row factors X[i][kk] / pivot
   __shared__ int used_s[GJP_RMAX];
-  __shared__ unsigned long long best_s, key_s;
+  __shared__ unsigned long long best_s, key_s, pre_s;
   const int pb = blockIdx.y;
   if (act && !act[pb]) return;
   const int b = blockIdx.x, t = threadIdx.x;
@@ -378,14 +392,13 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
   ainv += pb * n;
   slots += (int64_t)pb * (k + 1) * GJ_KEY_SLOTS;
   ipiv += (int64_t)pb * k;
-  logdet += (int64_t)pb * ld_stride;
+  if (logdet) logdet += (int64_t)pb * ld_stride;
   pub0 += (int64_t)pb * bp * k;
   pub1 += (int64_t)pb * bp * k;
-  double ld = 0.0;
-  if (b == 0 && t == 0) ld = *logdet;
 
   for (int64_t e = t; e < (int64_t)nr * k; e += GJP_THREADS) xs[e] = a[(int64_t)r0 * k + e];
   if (t < GJP_RMAX) used_s[t] = 0;
+  if (t == 0) pre_s = 0ull;
   __syncthreads();
   // offers for column 0: the rows as loaded
   if (t < 32) {
@@ -407,11 +420,18 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
   if (t == 0) st_release_u64(slots + b, best_s + 1ull);
 
   for (int kk = 0; kk < k; ++kk) {
+    const unsigned long long pre = pre_s;   // key of this step when its pivot row was prefetched
     if (t < 32) {
-      const unsigned long long mx = warp_wait_slots(slots + (int64_t)kk * GJ_KEY_SLOTS, bp, err, limit_ns);
-      if (t == 0) key_s = mx;
+      if (pre) {
+        cp_async_wait_all();   // the lanes' copies of the row into pvn
+        if (t == 0) key_s = pre;
+      } else {
+        const unsigned long long mx = warp_wait_slots(slots + (int64_t)kk * GJ_KEY_SLOTS, bp, err, limit_ns);
+        if (t == 0) key_s = mx;
+      }
     }
     __syncthreads();
+    if (t == 0) pre_s = 0ull;
     const unsigned long long mx = key_s;
     if (mx == 0ull) return;                   // a wait gave up: every block leaves
     const unsigned long long key = mx - 1ull;
@@ -425,10 +445,10 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
 #pragma unroll
     for (int q = 0; q < JPT; ++q) {
       const int j = t + q * GJP_THREADS;
-      pvr[q] = j < k ? ld_cg(prg + j) : mk(0.0, 0.0);
+      pvr[q] = j < k ? (pre ? pvn[j] : ld_cg(prg + j)) : mk(0.0, 0.0);
       if (j < k) pv[j] = pvr[q];
     }
-    const zd piv = ld_cg(prg + kk);
+    const zd piv = pre ? pvn[kk] : ld_cg(prg + kk);
     const zd inv = gj_recip(piv);
     const int lp = p - r0;   // local index of the pivot row (in range only in its owner)
     if (t < nr) ms[t] = gj_mul(xs[(int64_t)t * k + kk], inv);
@@ -436,9 +456,11 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
       prow[kk] = p;
       if (lp >= 0 && lp < nr) used_s[lp] = 1;
       if (b == 0) {
-        const double am = sqrt(gj_nrm(piv));
-        if (!(am > 0.0) || !isfinite(am)) atomicOr(err, ERRB_SINGULAR);
-        ld += log(am);
+        // |pivot| = sqrt(nrm) is positive and finite iff nrm is; its logarithm is
+        // summed after the loop, off the steps' latency chain
+        const double nrm = gj_nrm(piv);
+        if (!(nrm > 0.0) || !isfinite(nrm)) atomicOr(err, ERRB_SINGULAR);
+        pn[kk] = nrm;
       }
     }
     __syncthreads();
@@ -486,6 +508,29 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
     }
     // the rest of the block's rows: X[i][j] -= m_i X[p][j] ...
     for (int r = 0; r < nr; ++r) {
+      if (r == (nr >> 1) && t < 32 && kk + 1 < k) {
+        // halfway: are all of the next step's candidates published?  (one look, no wait)
+        const unsigned long long* sl = slots + (int64_t)(kk + 1) * GJ_KEY_SLOTS;
+        bool all = true;
+        unsigned long long m1 = 0ull;
+        for (int q = t; q < bp; q += 32) {
+          const unsigned long long v = ld_acquire_u64(sl + q);
+          all = all && v != 0ull;
+          m1 = v > m1 ? v : m1;
+        }
+        if (__all_sync(0xffffffffu, all)) {
+          m1 = warp_max_u64(m1);
+          const unsigned long long key1 = m1 - 1ull;
+          const int p1 = 4095 - (int)(key1 & 4095ull);
+          if (key1 != 0ull && p1 >= 0 && p1 < k) {   // else the next step takes the waiting path
+            __syncwarp();   // orders the lanes' acquires before every lane's copies
+            const zd* src = (((kk + 1) & 1) ? pub1 : pub0) + (int64_t)(p1 / R) * k;
+            for (int j = t; j < k; j += 32) cp_async16(pvn + j, src + j);
+            cp_async_commit();
+            if (t == 0) pre_s = m1;
+          }
+        }
+      }
       if (r == skip || r == lp) continue;
       const zd m = ms[r];
       zd* row = xs + (int64_t)r * k;
@@ -528,7 +573,17 @@ __global__ void __launch_bounds__(GJP_THREADS) k_gj_persist(const zd* __restrict
   }
   if (b == 0) {
     for (int c = t; c < k; c += GJP_THREADS) ipiv[c] = prow[c];
-    if (t == 0) *logdet = ld;
+    if (logdet) {
+      // log|det| = sum over the steps, in step order, of log |pivot| (the terms in
+      // parallel, the sum by one thread: the same operations as the step form)
+      for (int c = t; c < k; c += GJP_THREADS) pn[c] = log(sqrt(pn[c]));
+      __syncthreads();
+      if (t == 0) {
+        double ld = *logdet;
+        for (int c = 0; c < k; ++c) ld += pn[c];
+        *logdet = ld;
+      }
+    }
   }
 }
 
@@ -571,7 +626,8 @@ static bool gjp_shape(int k, int nb, int* R_out, int* bp_out, size_t* smem_out) 
   if (R > GJP_RMAX) return false;
   const int bp = (k + R - 1) / R;
   if (bp > GJ_KEY_SLOTS) return false;
-  const size_t smem = ((size_t)R * k + k) * sizeof(zd) + 2 * (size_t)k * sizeof(int);
+  const size_t smem =
+      ((size_t)R * k + 2 * (size_t)k) * sizeof(zd) + 2 * (size_t)k * sizeof(int) + (size_t)k * sizeof(double);
   if (smem + 2048 > (size_t)smem_optin) return false;
   // one value for every caller (worker threads may race here)
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - 2048) != cudaSuccess) {

@@ -643,8 +643,9 @@ int newton(ov_context* c, zd* a[2], zd* e[2], int k, int* err_dev, int* which, N
   for (it = 1; it <= 100; ++it) {
     CK(cudaMemsetAsync(dstat, 0, 3 * sizeof(double), c->st));
     run(c, OV_KIND_DENSE, 0, [&] {
-      c->launches += dense_inverse(a[cur], ai, w0, w1, k, 1, nullptr, ipiv, used, keys, dstat + 2, 0, err_dev,
-                                   c->opt.dense, c->st);
+      // log|det| only where the determinant scaling uses it
+      c->launches += dense_inverse(a[cur], ai, w0, w1, k, 1, nullptr, ipiv, used, keys,
+                                   !norm_rules && scaling ? dstat + 2 : nullptr, 0, err_dev, c->opt.dense, c->st);
     });
     if (norm_rules && scaling)
       run(c, OV_KIND_DENSE, 1, [&] { dense_norm_scale(a[cur], ai, k, 1, nullptr, dstat + 2, 0, npart, ncnt, c->st); });
@@ -725,8 +726,10 @@ int newton_batch(ov_context* c, zd* a[2], int k, int nb, int* err_dev, std::vect
     CK(cudaMemcpyAsync(scal_dev, scaling.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemsetAsync(dstat, 0, sizeof(double) * 4 * nb, c->st));
     run(c, OV_KIND_DENSE, 0, [&] {
-      c->launches += dense_inverse(a[cur], ai, w0, w1, k, nb, act_dev, ipiv, used, keys, dstat + 2, 4, err_dev,
-                                   c->opt.dense, c->st);
+      // log|det| only where the determinant scaling uses it
+      const bool want_ld = !norm_rules && std::find(scaling.begin(), scaling.end(), 1) != scaling.end();
+      c->launches += dense_inverse(a[cur], ai, w0, w1, k, nb, act_dev, ipiv, used, keys,
+                                   want_ld ? dstat + 2 : nullptr, 4, err_dev, c->opt.dense, c->st);
     });
     if (norm_rules && std::find(scaling.begin(), scaling.end(), 1) != scaling.end())
       run(c, OV_KIND_DENSE, 1, [&] { dense_norm_scale(a[cur], ai, k, nb, act_dev, dstat + 2, 4, npart, ncnt, c->st); });

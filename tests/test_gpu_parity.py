@@ -553,20 +553,25 @@ def test_profile_select_times_only_selected_kinds():
     assert sum(v[0] for v in all_kinds.values()) > sel["stencil_pair"][0] + sel["proj_dots"][0]
 
 
+@pytest.mark.parametrize("rules", ["norm", "det"])
 @pytest.mark.parametrize("dims,nsrc,k", [((4, 4, 4, 4), 1, 200), ((4, 4, 4, 4), 4, 120), ((4, 4, 4, 4), 1, 700),
                                          ((4, 4, 4, 4), 1, 1100), ((2, 2, 2, 2), 1, 37)])
-def test_dense_modes_identical(dims, nsrc, k):
-    """The cooperative k x k inversion and the per-step form give bitwise equal results (sign and VJP)."""
+def test_dense_modes_identical(dims, nsrc, k, rules):
+    """The cooperative k x k inversion and the per-step form give bitwise equal results
+    (sign and VJP), with either Newton rule (the determinant rule also sums log|det|
+    in both forms; the norm rule skips it)."""
     u, b, xbar = case(dims, 0.3, 21, nsrc)
     ut, bt, xt = (torch.tensor(a, device=DEV) for a in (u, b, xbar))
     out = {}
     for mode in (1, 0):
+        binding.newton_rules(rules, "fp64", 1, 2)
         binding.dense_mode(mode, "fp64", 1, 2)
         try:
             x, info = binding.tsl_sign(ut, 0.3, -2.0, bt, k, "fp64", 1, 2, return_info=True)
             du, dmu, _ = binding.tsl_sign_vjp(ut, 0.3, -2.0, bt, k, xt, "fp64", 1, 2)
         finally:
             binding.dense_mode(0, "fp64", 1, 2)
+            binding.newton_rules("norm", "fp64", 1, 2)
         out[mode] = (x, info["newton_iters"], du, dmu)
     dx = float((out[0][0] - out[1][0]).abs().max() / out[1][0].abs().max())
     ddu = float((out[0][2] - out[1][2]).abs().max() / out[1][2].abs().max())
