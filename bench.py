@@ -526,7 +526,8 @@ def kk_products_leg(args, ut, bt, xt, wl, k, du, dmu, x, ms_step):
     """The headline call with the Frechet adjoint's k x k products in FP64 arithmetic
     instead of the tensor-core digit splitting: its seconds per call and how far its
     results lie from the headline's (x is the same: the forward pass forms no
-    products)."""
+    products); and, for scale, the map's rounding floor with FP64 products: the
+    same call with b scaled by 1 + 2^-52 (one ulp), against the unscaled one."""
     import torch
     from paper_1604_08057_gb300 import binding
     opts = (args.precision, args.rebiorth, args.passes)
@@ -538,9 +539,12 @@ def kk_products_leg(args, ut, bt, xt, wl, k, du, dmu, x, ms_step):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         rel = lambda a, c: float(torch.linalg.vector_norm(a - c) / torch.linalg.vector_norm(c))
+        du3, dmu3, _ = binding.tsl_sign_vjp(ut, wl.mu, wl.m_w, bt * (1.0 + 2.0**-52), k, xt, *opts,
+                                            segment=args.segment)
         return {"fp64_products_s_per_call": round(dt, 4), "split_products_s_per_call": round(ms_step / 1e3, 4),
                 "x_identical": bool(torch.equal(x2, x)), "rel_dU_fp64_vs_split": rel(du2, du),
-                "rel_dmu_fp64_vs_split": abs(dmu2 - dmu) / abs(dmu2)}
+                "rel_dmu_fp64_vs_split": abs(dmu2 - dmu) / abs(dmu2),
+                "fp64_floor_one_ulp_in_b": {"rel_dU": rel(du3, du2), "rel_dmu": abs(dmu3 - dmu2) / abs(dmu2)}}
     except (binding.OVError, RuntimeError) as exc:
         return {"error": str(exc)}
     finally:
