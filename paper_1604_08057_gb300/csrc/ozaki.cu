@@ -45,16 +45,30 @@ __device__ __forceinline__ double oz_entry(const zd* M, int k, int h, int plane,
   return plane == 0 ? v.re : (h ? -v.im : v.im);
 }
 
-// the digits of x 2^{-e} (|x| < 2^e); each step is exact: 128 r is a power-of-two
-// scaling, and 128 r - trunc(128 r) is exact by Sterbenz's lemma or because the digit is 0
+// The digits of r = x 2^{-e} (|x| < 2^e): d_p = sgn(x) (floor(|r| 2^{7p}) mod 128),
+// p = 1 .. D, the base-128 expansion of |r| truncated after D digits (the same digits
+// as repeating r <- 128 r, d = trunc(r), r <- r - d, each step of which is exact).
+// Read off the binary representation in integer arithmetic: |x| = m 2^{E - 1075}
+// with m the 53-bit significand (52 bits and E = 1 for subnormals), so digit p is
+// bits [-sh, 7 - sh) of m with sh = E - 1075 - e + 7p.
 __device__ __forceinline__ void oz_digits(double x, int e, float d[OZ_DIGITS]) {
-  double r = ldexp(x, -e);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const bool neg = (bits >> 63) != 0ull;
+  const int E = (int)((bits >> 52) & 0x7ffull);
+  const unsigned long long frac = bits & ((1ull << 52) - 1ull);
+  const unsigned long long m = E ? (frac | (1ull << 52)) : frac;
+  const int s0 = (E ? E : 1) - 1075 - e;
 #pragma unroll
   for (int p = 0; p < OZ_DIGITS; ++p) {
-    r *= 128.0;
-    const double t = trunc(r);
-    r -= t;
-    d[p] = (float)t;
+    const int sh = s0 + 7 * (p + 1);
+    unsigned long long v = 0ull;
+    if (sh >= 0) {
+      if (sh < 7) v = (m << sh) & 127ull;   // only the low 7 bits matter
+    } else if (sh > -64) {
+      v = (m >> (-sh)) & 127ull;
+    }
+    const float f = (float)(unsigned)v;
+    d[p] = neg ? -f : f;
   }
 }
 
