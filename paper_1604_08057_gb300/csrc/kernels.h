@@ -93,6 +93,16 @@ int tsl_stencil_variants();
 // wait on the shared-memory copies runs out
 template <typename R> void apply_h(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st,
                                    int variant = 0, int* err = nullptr);
+// Variant APPLY_IL of the multi-source FP32 operator: fields with the sources
+// interleaved innermost, float4 (two complex components) at ((x * 6 + cp) * nsrc + src),
+// one thread per (site, source), a warp reading one site's component pair for 32
+// sources as 512 contiguous bytes and its links as one broadcast.  apply_h runs
+// variant 0 for APPLY_IL (its fields are per-source); apply_h_il, pack_spinors_il and
+// unpack_spinors_il are the interleaved form.
+constexpr int APPLY_IL = 13;
+void apply_h_il(const Lat<float>& L, const float* in, float* out, int dagger, cudaStream_t st);
+void pack_spinors_il(const double* aos, float* dst, int nsrc, int64_t V, cudaStream_t st);
+void unpack_spinors_il(const float* f, double* aos, int nsrc, int64_t V, cudaStream_t st);
 
 template <typename R> void tsl_init(const Lat<R>& L, cudaStream_t st);
 template <typename R> void tsl_stencil(const Lat<R>& L, int j, bool need_q, cudaStream_t st, int variant = 0);

@@ -172,15 +172,90 @@ __global__ void __launch_bounds__(BSZ) k_apply_h(Lat<R> L, const R* __restrict__
     if (s0 + i < nsrc) store_spinor(out + (int64_t)(s0 + i) * L.vs, L.g.V, x, o[i]);
 }
 
+// Sources interleaved innermost (variant APPLY_IL, FP32): component pair cp of site x
+// for source src is the float4 at (x * 6 + cp) * nsrc + src.  The per-site arithmetic
+// is h_site_ld's, operation for operation, so the results equal variant 0's.
+struct FieldLoadIL {
+  const float4* f;
+  int64_t ns;
+  int src;
+  OV_HD void operator()(int64_t s, Spinor<float>& o) const {
+    const float4* p = f + s * 6 * ns + src;
+#pragma unroll
+    for (int cp = 0; cp < 6; ++cp) {
+      const float4 t = ldro(p + cp * ns);
+      o.c[2 * cp] = mk(t.x, t.y);
+      o.c[2 * cp + 1] = mk(t.z, t.w);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(256) k_apply_h_il(Lat<float> L, const float4* __restrict__ in,
+                                                    float4* __restrict__ out, int dagger) {
+  const int64_t ns = L.nsrc;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= L.g.V * ns) return;
+  const int64_t x = t / ns;
+  const int src = (int)(t - x * ns);
+  const float f = dagger ? L.efinv : L.ef, fi = dagger ? L.ef : L.efinv;
+  Spinor<float> o;
+  h_site_ld(FieldLoadIL{in, ns, src}, L.u, L.g, x, L.kappa, f, fi, o);
+  float4* po = out + x * 6 * ns + src;
+#pragma unroll
+  for (int cp = 0; cp < 6; ++cp)
+    po[cp * ns] = make_float4(o.c[2 * cp].re, o.c[2 * cp].im, o.c[2 * cp + 1].re, o.c[2 * cp + 1].im);
+}
+void apply_h_il(const Lat<float>& L, const float* in, float* out, int dagger, cudaStream_t st) {
+  const int64_t n = L.g.V * L.nsrc;
+  k_apply_h_il<<<nblocks(n, 256), 256, 0, st>>>(L, reinterpret_cast<const float4*>(in),
+                                                reinterpret_cast<float4*>(out), dagger);
+}
+
+// user spinors [src][site][12] complex128 <-> the interleaved FP32 layout (one thread
+// per (site, source), sources fastest)
+__global__ void k_pack_spinors_il(const double* __restrict__ aos, float4* __restrict__ dst, int64_t V, int64_t ns) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= V * ns) return;
+  const int64_t x = t / ns, src = t - x * ns;
+  const double2* in = reinterpret_cast<const double2*>(aos) + (src * V + x) * 12;
+  float4* o = dst + x * 6 * ns + src;
+#pragma unroll
+  for (int cp = 0; cp < 6; ++cp) {
+    const double2 a = in[2 * cp], b = in[2 * cp + 1];
+    o[cp * ns] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+  }
+}
+__global__ void k_unpack_spinors_il(const float4* __restrict__ f, double* __restrict__ aos, int64_t V, int64_t ns) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= V * ns) return;
+  const int64_t x = t / ns, src = t - x * ns;
+  const float4* p = f + x * 6 * ns + src;
+  double2* out = reinterpret_cast<double2*>(aos) + (src * V + x) * 12;
+#pragma unroll
+  for (int cp = 0; cp < 6; ++cp) {
+    const float4 v = p[cp * ns];
+    out[2 * cp] = make_double2((double)v.x, (double)v.y);
+    out[2 * cp + 1] = make_double2((double)v.z, (double)v.w);
+  }
+}
+void pack_spinors_il(const double* aos, float* dst, int nsrc, int64_t V, cudaStream_t st) {
+  k_pack_spinors_il<<<nblocks(V * nsrc, 256), 256, 0, st>>>(aos, reinterpret_cast<float4*>(dst), V, nsrc);
+}
+void unpack_spinors_il(const float* f, double* aos, int nsrc, int64_t V, cudaStream_t st) {
+  k_unpack_spinors_il<<<nblocks(V * nsrc, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(f), aos, V, nsrc);
+}
+
 // launch variants (sources per thread, threads per block, site map); 0 is the default.
 // Plane variants fall back to consecutive sites when an x-y plane has fewer than
 // 64 sites or more than the variant's thread bound.
 // Variants 9, 10, 11 (FP32 only; others run variant 0) stage 1, 2 or 4 z-planes of
 // the input in shared memory (k_apply_h_staged, below); variant 12 (FP32 only)
-// sweeps runs of z-planes through a ring of plane slots (k_apply_h_sweep).
+// sweeps runs of z-planes through a ring of plane slots (k_apply_h_sweep); variant
+// 13 (APPLY_IL, FP32, its own field layout) is k_apply_h_il above.
 static const int kApplyVariants[][3] = {{1, 128, 0}, {1, 64, 0}, {1, 256, 0}, {2, 64, 0}, {2, 128, 0},
                                         {4, 64, 0}, {4, 128, 0}, {1, 512, 1}, {2, 256, 1},
-                                        {1, 1, 2},   {1, 2, 2},   {1, 4, 2},   {1, 0, 3}};
+                                        {1, 1, 2},   {1, 2, 2},   {1, 4, 2},   {1, 0, 3},
+                                        {1, 256, 4}};
 int apply_h_variants() { return (int)(sizeof(kApplyVariants) / sizeof(kApplyVariants[0])); }
 
 template <typename R, int NS, int BSZ, int MAP>

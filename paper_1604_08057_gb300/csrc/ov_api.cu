@@ -1644,12 +1644,23 @@ int apply_h_impl(ov_context* c, const int32_t dims[4], const void* U, double mu,
   check_ptr(out);
   Lat<R> L = setup<R>(c, dims, U, mu, m_w, nsrc, 1, false);
   int* aerr = wsT<int>(c, B_AERR, 1, true);
-  run(c, OV_KIND_LAYOUT, 1,
-      [&] { pack_spinors<R>(static_cast<const double*>(in), L.r, nsrc, L.g.V, L.vs, c->st); });
-  run(c, OV_KIND_APPLY_H, 1,
-      [&] { apply_h(L, L.r, L.p, dagger, c->st, c->tuned_apply[c->opt.precision], aerr); });
-  run(c, OV_KIND_LAYOUT, 1,
-      [&] { unpack_spinors<R>(L.p, static_cast<double*>(out), nsrc, L.g.V, L.vs, c->st); });
+  const int var = c->tuned_apply[c->opt.precision];
+  if constexpr (std::is_same<R, float>::value) {
+    if (var == APPLY_IL) {   // the sources-interleaved form has its own field layout
+      run(c, OV_KIND_LAYOUT, 1,
+          [&] { pack_spinors_il(static_cast<const double*>(in), L.r, nsrc, L.g.V, c->st); });
+      run(c, OV_KIND_APPLY_H, 1, [&] { apply_h_il(L, L.r, L.p, dagger, c->st); });
+      run(c, OV_KIND_LAYOUT, 1,
+          [&] { unpack_spinors_il(L.p, static_cast<double*>(out), nsrc, L.g.V, c->st); });
+    }
+  }
+  if (!std::is_same<R, float>::value || var != APPLY_IL) {
+    run(c, OV_KIND_LAYOUT, 1,
+        [&] { pack_spinors<R>(static_cast<const double*>(in), L.r, nsrc, L.g.V, L.vs, c->st); });
+    run(c, OV_KIND_APPLY_H, 1, [&] { apply_h(L, L.r, L.p, dagger, c->st, var, aerr); });
+    run(c, OV_KIND_LAYOUT, 1,
+        [&] { unpack_spinors<R>(L.p, static_cast<double*>(out), nsrc, L.g.V, L.vs, c->st); });
+  }
   launch_check();
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, aerr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1680,7 +1691,12 @@ int autotune_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   r.n_pair = tsl_stencil_variants();
   int* aerr = wsT<int>(c, B_AERR, 1, true);
   for (int v = 0; v < r.n_apply && v < 16; ++v)
-    r.apply_us[v] = time_us([&] { apply_h(L, L.r, L.p, 0, c->st, v, aerr); });
+    r.apply_us[v] = time_us([&] {
+      if constexpr (std::is_same<R, float>::value) {
+        if (v == APPLY_IL) return apply_h_il(L, L.r, L.p, 0, c->st);   // same buffers, its own layout
+      }
+      apply_h(L, L.r, L.p, 0, c->st, v, aerr);
+    });
   for (int v = 0; v < r.n_pair && v < 16; ++v)
     r.pair_us[v] = time_us([&] { tsl_stencil(L, 0, true, c->st, v); });
   // a variant replaces the current choice only when it is more than 2% faster: the

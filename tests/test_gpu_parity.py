@@ -99,7 +99,29 @@ def test_every_stencil_variant(dims, precision, tol_h, tol_x):
     binding.set_stencil_variants(rep["apply_variant"], rep["pair_variant"], precision)
 
 
-@pytest.mark.parametrize("variant", [9, 10, 11, 12])
+@pytest.mark.parametrize("nsrc", [32, 33, 1])
+def test_sources_interleaved_variant_equals_variant_0(nsrc):
+    """The FP32 variant with the sources interleaved innermost (13) runs the same
+    per-site arithmetic as variant 0 on its own field layout: bitwise equal results,
+    for a full warp of sources per site, a source count that makes warps straddle
+    sites, and a lone source."""
+    dims, mu, m_w = (4, 4, 6, 8), 0.3, -2.0
+    u, b, _ = case(dims, 0.3, 23, nsrc)
+    ut, bt = T(u), T(b)
+    out = {}
+    try:
+        for v in (0, 13):
+            binding.set_stencil_variants(v, 0, "mixed")
+            out[v] = [binding.apply_H(ut, mu, m_w, bt, dagger=d, precision="mixed") for d in (False, True)]
+    finally:
+        binding.set_stencil_variants(0, 0, "mixed")
+    for d in range(2):
+        assert torch.equal(out[13][d], out[0][d]), d
+    want = dirac.apply_h(u, b[0], mu, m_w)
+    assert rel(out[13][0].cpu().numpy()[0], want) <= 2e-6
+
+
+@pytest.mark.parametrize("variant", [9, 10, 11, 12, 13])
 def test_shared_memory_stencil_variants_long_runs(variant):
     """The FP32 variants that stage the input in shared memory, on a lattice whose
     per-block runs of z-planes are long enough that the sweep variant (12) refills
