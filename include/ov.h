@@ -268,6 +268,41 @@ int ov_tsl_sign_jvp(ov_context *ctx, const int32_t dims[4], const void *U, doubl
                     int32_t nsrc, const void *b, int32_t k, const void *E, double m_dir, void *dx,
                     void *x, ov_tsl_info *info);
 
+/* Deflation (Sec. 3).  l eigen-triples of H(U, mu) are supplied by the caller:
+ * lam (host double[2l], complex interleaved), R and L (device arrays of l
+ * spinor fields each, complex128 user layout: right and left eigenvectors,
+ * H R_i = lambda_i R_i, L_i^dag H = lambda_i L_i^dag, L_i^dag R_j = delta_ij).
+ * The library computes no eigenvectors (the paper obtains them by Arnoldi).
+ *
+ * ov_tsl_sign_deflated: standard deflation of sgn(H) b,
+ *   x = TSL_k(H, Pbar b) + sum_i sgn(Re lambda_i) R_i (L_i^dag b),
+ *   Pbar b = b - sum_i R_i (L_i^dag b)
+ * (the k-step TSL of ov_tsl_sign on the projected source; b and x: device
+ * arrays of nsrc spinor fields).  An eigenvalue with Re lambda_i = 0 exactly
+ * is rejected (OV_ERR_SIGN_ILLPOSED).  l = 0 is the plain ov_tsl_sign.  Other
+ * errors as ov_tsl_sign; OV_ERR_INVALID_ARG for l < 0, l > 4096, a null or
+ * misaligned array (R, L may be NULL only when l = 0). */
+int ov_tsl_sign_deflated(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                         int32_t nsrc, const void *b, int32_t k, int32_t l, const double *lam,
+                         const void *R, const void *L, void *x, ov_tsl_info *info);
+
+/* ov_tsl_sign_jvp_deflated: the generalised deflation of Theorem 1's block
+ * matrix B = [[H, dH], [0, H]] (Sec. 3, Eqs. x_final, xinv_final,
+ * projector_1, final_res), dH along (E, m_dir) as in ov_block_tsl_sign, for
+ * the start (0, b): with a_i = L_i^dag b and c_i = dL_i^dag b,
+ *   (top', bottom') = (-sum_i (R_i c_i + dR_i a_i), b - sum_i R_i a_i),
+ *   (dx, x) = ov_block_tsl_sign(top', bottom')
+ *             + sum_i sgn(Re lambda_i) (R_i c_i + dR_i a_i, R_i a_i),
+ * the mixing term d sgn(lambda_i) of Eq. final_res being zero.  dR, dL:
+ * device arrays of l spinor fields, the derivatives of the eigenvectors along
+ * the same direction, normalised by L_i^dag dR_i = 0 and dL_i^dag R_i = 0
+ * (App. B).  dx ~ (d sgn(H)) b and x ~ sgn(H) b.  Errors as
+ * ov_tsl_sign_deflated and ov_block_tsl_sign. */
+int ov_tsl_sign_jvp_deflated(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                             int32_t nsrc, const void *b, int32_t k, const void *E, double m_dir, int32_t l,
+                             const double *lam, const void *R, const void *L, const void *dR, const void *dL,
+                             void *dx, void *x, ov_tsl_info *info);
+
 /* A-posteriori error estimates of Sec. 4.1.  The sign is applied twice, each
  * time by its own k-step TSL (the second starts from the first's result), and
  * eps[src] (host array of nsrc doubles) receives per source

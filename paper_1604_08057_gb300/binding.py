@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -69,7 +70,7 @@ EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", 
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
            "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_overlap_apply", "ov_overlap_solve", "ov_u1_current",
-           "ov_kk_gemm", "ov_strerror"]
+           "ov_kk_gemm", "ov_tsl_sign_deflated", "ov_tsl_sign_jvp_deflated", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -114,6 +115,9 @@ def load(path: str = LIB_PATH):
     lib.ov_u1_current.argtypes = [P, dims_t, P, D, D, I32, P, I32, D, I32, P, ctypes.POINTER(D), ctypes.POINTER(Info)]
     lib.ov_debug_inject.argtypes = [P, I32, I32]
     lib.ov_kk_gemm.argtypes = [P, P, I32, P, I32, P, I32, I32]
+    lib.ov_tsl_sign_deflated.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, P, P, P, P, ctypes.POINTER(Info)]
+    lib.ov_tsl_sign_jvp_deflated.argtypes = [P, dims_t, P, D, D, I32, P, I32, P, D, I32, P, P, P, P, P, P, P,
+                                             ctypes.POINTER(Info)]
     lib.ov_launch_count.argtypes = [P]
     lib.ov_launch_count.restype = ctypes.c_int64
     lib.ov_strerror.argtypes = [ctypes.c_int]
@@ -429,6 +433,69 @@ def tsl_sign_jvp(u, mu, m_w, b, k, e=None, m_dir=0.0, precision="fp64", rebiorth
     _check(lib.ov_tsl_sign_jvp(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
                                _ptr(e) if e is not None else None, float(m_dir), _ptr(dx), _ptr(x),
                                ctypes.byref(info)), "ov_tsl_sign_jvp")
+    if single:
+        dx, x = dx[0], x[0]
+    return (dx, x, info.as_dict()) if return_info else (dx, x)
+
+
+def _eigen_args(u, lam, fields):
+    """Host complex eigenvalues -> interleaved doubles; eigenvector fields -> contiguous
+    complex128 CUDA tensors shaped (l, Nt, Nz, Ny, Nx, 4, 3)."""
+    lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128).reshape(-1))
+    l = lam.size
+    out = []
+    for f in fields:
+        if f is None:
+            out.append(None)
+            continue
+        if f.dtype != torch.complex128 or not f.is_cuda or tuple(f.shape) != (l,) + tuple(u.shape[:4]) + (4, 3):
+            raise ValueError("eigenvector fields must be complex128 CUDA, shaped (l, Nt, Nz, Ny, Nx, 4, 3)")
+        out.append(f.contiguous())
+    lam_d = lam.view(np.float64).copy()
+    return l, lam_d, out
+
+
+def tsl_sign_deflated(u, mu, m_w, b, k, lam, R, L, precision="fp64", rebiorth=1, passes=2, return_info=False):
+    """Standard deflation (Sec. 3): x = TSL_k(H, Pbar b) + sum_i sgn(Re lam_i) R_i (L_i^dag b)
+    with the caller's eigen-triples (lam: l complex numbers; R, L: eigenvector fields)."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    l, lam_d, (rr, ll) = _eigen_args(u, lam, (R, L))
+    x = torch.empty_like(bb)
+    info = Info()
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_tsl_sign_deflated(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k), l,
+                                    lam_d.ctypes.data if l else None, _ptr(rr) if l else None,
+                                    _ptr(ll) if l else None, _ptr(x), ctypes.byref(info)), "ov_tsl_sign_deflated")
+    if single:
+        x = x[0]
+    return (x, info.as_dict()) if return_info else x
+
+
+def tsl_sign_jvp_deflated(u, mu, m_w, b, k, lam, R, L, dR, dL, e=None, m_dir=0.0, precision="fp64", rebiorth=1,
+                          passes=2, return_info=False):
+    """Generalised deflation of Theorem 1's block matrix (Sec. 3, Eq. final_res): (dx, x)
+    with dx ~ d/dt sgn(H(U + tE, mu + t m_dir)) b and x ~ sgn(H) b; dR, dL are the
+    eigenvector derivatives along the same direction (App. B)."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    bb, single = _spinors(b, u)
+    if e is not None:
+        _dims(e)
+        e = e.contiguous()
+    l, lam_d, (rr, ll, drr, dll) = _eigen_args(u, lam, (R, L, dR, dL))
+    x = torch.empty_like(bb)
+    dx = torch.empty_like(bb)
+    info = Info()
+    ctx = context(precision, rebiorth, passes)
+    ptr = lambda t: _ptr(t) if (l and t is not None) else None
+    _check(lib.ov_tsl_sign_jvp_deflated(ctx, dims, _ptr(u), float(mu), float(m_w), bb.shape[0], _ptr(bb), int(k),
+                                        _ptr(e) if e is not None else None, float(m_dir), l,
+                                        lam_d.ctypes.data if l else None, ptr(rr), ptr(ll), ptr(drr), ptr(dll),
+                                        _ptr(dx), _ptr(x), ctypes.byref(info)), "ov_tsl_sign_jvp_deflated")
     if single:
         dx, x = dx[0], x[0]
     return (dx, x, info.as_dict()) if return_info else (dx, x)

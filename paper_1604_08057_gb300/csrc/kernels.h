@@ -210,6 +210,8 @@ void vec_dots(const double* basis, int64_t stride, int nvec, const double* w, in
 void vec_update(double* w, const double* basis, int64_t stride, int nvec, const zd* coef, double s, int64_t n,
                 cudaStream_t st);
 void vec_scale(const double* in, double* out, double fr, double fi, int64_t n, cudaStream_t st);
+// out[p * l + i] = sg[i] in[p * l + i] for p < np, i < l (deflation: the exact part's coefficients)
+void coef_sign(const zd* in, const double* sg, zd* out, int l, int np, cudaStream_t st);
 void vec_sub(const double* a, const double* b, double* out, int64_t n, cudaStream_t st);
 // j[l] (+)= scale (-Im sum conj(g_re) U + i (-Im sum conj(g_im) U)) per link l < nlinks (9 entries each)
 void theta_current(const double* u, const double* g_re, const double* g_im, double* j, int64_t nlinks, double scale,

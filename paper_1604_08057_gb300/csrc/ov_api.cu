@@ -22,7 +22,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, NBUF
 };
 
 struct Status {
@@ -950,6 +950,93 @@ void merge_info(ov_tsl_info* acc, const ov_tsl_info& one) {
   if (one.k_reached < acc->k_reached) acc->k_reached = one.k_reached;
   if (one.newton_iters > acc->newton_iters) acc->newton_iters = one.newton_iters;
   for (int i = 0; i < 8; ++i) acc->t_ms[i] += one.t_ms[i];
+}
+
+// Deflation (Sec. 3): the projected start vector(s) from the caller's eigen-triples,
+// the (block) TSL on them, and the exact part added back; every vector operation
+// is a kernel on the user-layout fields (complex128).
+template <typename R>
+int deflated_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
+                  const void* b, int k, const void* E, double m_dir, bool block, int l, const double* lam,
+                  const void* Rf, const void* Lf, const void* dRf, const void* dLf, void* dx, void* x,
+                  ov_tsl_info* info) {
+  check_ptr(b);
+  check_ptr(x);
+  if (block) check_ptr(dx);
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1 || dims[3] < 1 || nsrc < 1) throw Status{OV_ERR_INVALID_ARG};
+  if (l > 0) {
+    if (!lam) throw Status{OV_ERR_INVALID_ARG};
+    check_ptr(Rf);
+    check_ptr(Lf);
+    if (block) {
+      check_ptr(dRf);
+      check_ptr(dLf);
+    }
+  }
+  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+  const int64_t n = 12 * V;          // complex entries per field
+  const int64_t fd = 2 * n;          // doubles per field
+  std::vector<double> sg(std::max(l, 1), 0.0);
+  for (int i = 0; i < l; ++i) {
+    if (!std::isfinite(lam[2 * i]) || !std::isfinite(lam[2 * i + 1])) throw Status{OV_ERR_INVALID_ARG};
+    if (lam[2 * i] == 0.0) throw Status{OV_ERR_SIGN_ILLPOSED};
+    sg[i] = lam[2 * i] > 0.0 ? 1.0 : -1.0;
+  }
+  const int lm = std::max(l, 1);
+  zd* a = wsT<zd>(c, B_DFA, (int64_t)nsrc * lm);
+  zd* cc = wsT<zd>(c, B_DFC, (int64_t)nsrc * lm);
+  zd* sa = wsT<zd>(c, B_DFSA, (int64_t)nsrc * lm);
+  zd* sc = wsT<zd>(c, B_DFSC, (int64_t)nsrc * lm);
+  zd* part = wsT<zd>(c, B_DFPART, 152 * (int64_t)lm);
+  double* sgd = wsT<double>(c, B_DFSG, lm);
+  double* bot = wsT<double>(c, B_DFBOT, nsrc * fd);
+  double* top = block ? wsT<double>(c, B_DFTOP, nsrc * fd) : nullptr;
+  const double* bd = static_cast<const double*>(b);
+  const double* rd = static_cast<const double*>(Rf);
+  const double* ld = static_cast<const double*>(Lf);
+  const double* drd = static_cast<const double*>(dRf);
+  const double* dld = static_cast<const double*>(dLf);
+  CK(cudaMemcpyAsync(sgd, sg.data(), sizeof(double) * lm, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(bot, bd, sizeof(double) * nsrc * fd, cudaMemcpyDeviceToDevice, c->st));
+  if (block) CK(cudaMemsetAsync(top, 0, sizeof(double) * nsrc * fd, c->st));
+  if (l > 0) {
+    for (int p = 0; p < nsrc; ++p) {
+      run(c, OV_KIND_COMBINE, 2, [&] { vec_dots(ld, fd, l, bd + p * fd, n, a + (int64_t)p * l, part, c->st); });
+      if (block)
+        run(c, OV_KIND_COMBINE, 2, [&] { vec_dots(dld, fd, l, bd + p * fd, n, cc + (int64_t)p * l, part, c->st); });
+      // Pbar: bottom' = b - sum R_i a_i;  top' = -sum (R_i c_i + dR_i a_i)
+      run(c, OV_KIND_COMBINE, 1, [&] { vec_update(bot + p * fd, rd, fd, l, a + (int64_t)p * l, -1.0, n, c->st); });
+      if (block)
+        run(c, OV_KIND_COMBINE, 2, [&] {
+          vec_update(top + p * fd, rd, fd, l, cc + (int64_t)p * l, -1.0, n, c->st);
+          vec_update(top + p * fd, drd, fd, l, a + (int64_t)p * l, -1.0, n, c->st);
+        });
+    }
+    run(c, OV_KIND_COMBINE, 2, [&] {
+      coef_sign(a, sgd, sa, l, nsrc, c->st);
+      if (block) coef_sign(cc, sgd, sc, l, nsrc, c->st);
+    });
+  }
+  launch_check();
+  const int st = block ? block_impl<R>(c, dims, U, mu, m_w, nsrc, top, bot, k, E, m_dir, dx, x, info)
+                       : tsl_sign_impl<R>(c, dims, U, mu, m_w, nsrc, bot, k, x, info);
+  if (st != OV_OK) return st;
+  if (l > 0) {
+    double* xd = static_cast<double*>(x);
+    double* dxd = static_cast<double*>(dx);
+    for (int p = 0; p < nsrc; ++p) {
+      // the exact part: sum_i sgn(lambda_i) (R_i c_i + dR_i a_i, R_i a_i)
+      run(c, OV_KIND_COMBINE, 1, [&] { vec_update(xd + p * fd, rd, fd, l, sa + (int64_t)p * l, 1.0, n, c->st); });
+      if (block)
+        run(c, OV_KIND_COMBINE, 2, [&] {
+          vec_update(dxd + p * fd, rd, fd, l, sc + (int64_t)p * l, 1.0, n, c->st);
+          vec_update(dxd + p * fd, drd, fd, l, sa + (int64_t)p * l, 1.0, n, c->st);
+        });
+    }
+  }
+  launch_check();
+  CK(cudaStreamSynchronize(c->st));
+  return OV_OK;
 }
 
 template <typename R>
@@ -1971,6 +2058,35 @@ int ov_block_tsl_sign(ov_context* c, const int32_t dims[4], const void* U, doubl
 int ov_tsl_sign_jvp(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
                     const void* b, int32_t k, const void* E, double m_dir, void* dx, void* x, ov_tsl_info* info) {
   return ov_block_tsl_sign(c, dims, U, mu, m_w, nsrc, nullptr, b, k, E, m_dir, dx, x, info);
+}
+
+int ov_tsl_sign_deflated(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
+                         const void* b, int32_t k, int32_t l, const double* lam, const void* R, const void* L,
+                         void* x, ov_tsl_info* info) {
+  if (!c || !dims || k < 2 || k > 4096 || l < 0 || l > 4096) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? deflated_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, nullptr, 0.0, false, l, lam, R, L, nullptr,
+                                      nullptr, nullptr, x, info)
+               : deflated_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, nullptr, 0.0, false, l, lam, R, L, nullptr,
+                                       nullptr, nullptr, x, info);
+  });
+}
+
+int ov_tsl_sign_jvp_deflated(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w,
+                             int32_t nsrc, const void* b, int32_t k, const void* E, double m_dir, int32_t l,
+                             const double* lam, const void* R, const void* L, const void* dR, const void* dL,
+                             void* dx, void* x, ov_tsl_info* info) {
+  if (!c || !dims || k < 2 || k > 4096 || l < 0 || l > 4096) return OV_ERR_INVALID_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? deflated_impl<float>(c, dims, U, mu, m_w, nsrc, b, k, E, m_dir, true, l, lam, R, L, dR, dL, dx, x,
+                                      info)
+               : deflated_impl<double>(c, dims, U, mu, m_w, nsrc, b, k, E, m_dir, true, l, lam, R, L, dR, dL, dx,
+                                       x, info);
+  });
 }
 
 int ov_tsl_eps(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,

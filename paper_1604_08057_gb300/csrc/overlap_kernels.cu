@@ -97,6 +97,18 @@ void vec_update(double* w, const double* basis, int64_t stride, int nvec, const 
                                                 n);
 }
 
+__global__ void k_coef_sign(const zd* __restrict__ in, const double* __restrict__ sg, zd* __restrict__ out, int l,
+                            int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double s = sg[t % l];
+  out[t] = mk(s * in[t].re, s * in[t].im);
+}
+void coef_sign(const zd* in, const double* sg, zd* out, int l, int np, cudaStream_t st) {
+  const int n = l * np;
+  if (n > 0) k_coef_sign<<<ov_nblk(n, 128), 128, 0, st>>>(in, sg, out, l, n);
+}
+
 // out = f in  (f complex, in and out may coincide)
 __global__ void k_vec_scale(const double2* in, double2* out, double fr, double fi, int64_t n) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
