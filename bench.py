@@ -63,7 +63,7 @@ def parse_args():
                     help="two-pass TSL with checkpoints every S steps (needs --rebiorth 0)")
     ap.add_argument("--m-w", type=float, default=None, help="override the workload's Wilson mass")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
-    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch", "kk"],
+    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch", "kk", "deflation"],
                     help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling); "
                          "batch: the uneven batch of 32 problems (forward + VJP) through ov_tsl_batch; "
                          "kk: one k x k complex product (ov_kk_gemm), FP64 and split, at the workload's k")
@@ -350,6 +350,10 @@ def run_ours(args, rank, world, local_rank):
         out["schedule_compare"] = schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x)
         out["diagnostics"] = diagnostics_leg(args, ut, bt, xt, wl, k, ms_total / args.steps)
         out["kk_products"] = kk_products_leg(args, ut, bt, xt, wl, k, du, dmu, x, ms_total / args.steps)
+        try:
+            out["deflation"] = deflation_leg(ut.device.index)
+        except Exception as exc:   # reported, not fatal: the leg is beside the headline
+            out["deflation"] = {"error": str(exc)}
         out["basis_in_host_memory"] = host_basis_leg(args, ut, bt, xt, wl, k, du, dmu, x)
         out["other_workloads"] = other_workloads_leg(args)
         if world == 1:
@@ -487,6 +491,49 @@ def host_basis_leg(args, ut, bt, xt, wl, k, du, dmu, x):
         return {"error": str(exc)}
     finally:
         binding.basis_memory("device", *opts, segment=args.segment)
+
+
+def deflation_leg(dev_index, dims=(3, 3, 3, 3), mu=0.3, m_w=-2.0, l=40, ks=(40, 80, 120)):
+    """Deflation (Sec. 3) on a lattice small enough for a dense eigendecomposition
+    (3^4, n = 972): H is assembled on the GPU (ov_apply_H on the 972 unit vectors),
+    its eigen-triples come from scipy (LAPACK zgeev), and sgn(H) b from them is the
+    exact reference.  Reported per k: the error of the plain and of the deflated TSL
+    (l eigenvalues smallest in |lambda|) and the seconds per call of each."""
+    import numpy as np
+    import scipy.linalg as sla
+    import torch
+    from paper_1604_08057_gb300 import binding
+    dev = torch.device("cuda", dev_index)
+    rng = np.random.default_rng(31)
+    u = torch.tensor(inputs.su3_links(dims, 0.3, rng), device=dev)
+    b = torch.tensor(inputs.gaussian_spinors(dims, 1, rng), device=dev)
+    n = 12 * int(np.prod(dims))
+    unit = torch.eye(n, dtype=torch.complex128, device=dev).reshape((n,) + tuple(dims) + (4, 3))
+    h = binding.apply_H(u, mu, m_w, unit).reshape(n, n).T.cpu().numpy()    # column j = H e_j
+    lam, vl, vr = sla.eig(h, left=True, right=True)
+    order = np.argsort(np.abs(lam), kind="stable")
+    lam, vl, vr = lam[order], vl[:, order], vr[:, order]
+    vr = vr / np.linalg.norm(vr, axis=0, keepdims=True)
+    vl = vl / np.einsum("ij,ij->j", vl.conj(), vr).conj()[None, :]
+    exact = (vr * np.sign(lam.real)) @ (vl.conj().T @ b.cpu().numpy().ravel())
+    shape = (l,) + tuple(dims) + (4, 3)
+    rf = torch.tensor(np.ascontiguousarray(vr[:, :l].T).reshape(shape), device=dev)
+    lf = torch.tensor(np.ascontiguousarray(vl[:, :l].T).reshape(shape), device=dev)
+    out = {"lattice": "x".join(map(str, dims)), "n": n, "deflated": l, "min_abs_re_lambda": float(np.min(np.abs(lam.real))),
+           "lambda_l_abs": float(abs(lam[l - 1])), "per_k": {}}
+    rel = lambda a: float(np.linalg.norm(a.cpu().numpy().ravel() - exact) / np.linalg.norm(exact))
+    for k in ks:
+        row = {}
+        for name, call in (("plain", lambda: binding.tsl_sign(u, mu, m_w, b, k)),
+                           ("deflated", lambda: binding.tsl_sign_deflated(u, mu, m_w, b, k, lam[:l], rf, lf))):
+            x = call()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x = call()
+            torch.cuda.synchronize()
+            row[name] = {"rel_err": rel(x), "s_per_call": round(time.perf_counter() - t0, 5)}
+        out["per_k"][str(k)] = row
+    return out
 
 
 def kk_leg(args, dev_index, reps=5):
@@ -877,6 +924,11 @@ def main():
         print(json.dumps({"leg": "uneven_batch", "precision": args.precision, "rebiorth_period": args.rebiorth,
                           "segment": args.segment,
                           "gs_passes": args.passes, **batch_leg(args)}))
+        return
+    if args.leg == "deflation":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"leg": "deflation", **deflation_leg(local_rank)}))
         return
     if args.leg == "kk":
         import torch
