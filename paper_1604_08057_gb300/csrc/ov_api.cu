@@ -130,9 +130,14 @@ void* ws(ov_context* c, int id, size_t bytes, bool zero);
 // C_p = op(A_p) op(B_p), k x k complex, for the problems p < nb with act[p] set (all
 // when act is null; act_dev is the device copy): on the BF16 tensor cores by the exact
 // digit splitting (options.gemm), else FP64 arithmetic
+// whether the k x k products of this context run on the tensor cores (options.gemm)
+bool kk_split(const ov_context* c, int k) {
+  return k <= OZ_MAX_K && (c->opt.gemm == 2 || (c->opt.gemm == 0 && k >= 128));
+}
+
 void kk_gemm(ov_context* c, const zd* A, int64_t sA, int hA, const zd* B, int64_t sB, int hB, zd* C, int64_t sC,
              int k, int nb, const std::vector<int>* act, const int* act_dev) {
-  const bool split = k <= OZ_MAX_K && (c->opt.gemm == 2 || (c->opt.gemm == 0 && k >= 128));
+  const bool split = kk_split(c, k);
   if (!split) {
     run(c, OV_KIND_DENSE_GEMM, 1,
         [&] { dense_gemm_batch(A, sA, hA, B, sB, hB, C, sC, k, nb, act ? act_dev : nullptr, c->st); });
@@ -1247,8 +1252,11 @@ int vjp_reverse(ov_context* c, FwdState<R>& F, const void* xbar, void* x, void* 
     //   A <- [g A / 2 | -Y A / (2 g)],  B <- [B | Y^H B]   (Y = X_i^{-H}),
     // two k x k x r products instead of two k^3 ones; E is formed once the rank
     // would pass rmax.  (Factors beyond a source's own rank stay zero.)
+    // (with the tensor-core products a full k x k product costs about what two FP64
+    // k x k x 16 ones do, so the factored form stops at rank 8 there)
     int rmax = 0;
-    for (int r = 2; r <= 256 && r <= k / 2; r *= 2) rmax = r;
+    const int rcap = kk_split(c, k) ? 8 : 256;
+    for (int r = 2; r <= rcap && r <= k / 2; r *= 2) rmax = r;
     if (rmax < 2) rmax = 1;
     zd* fa = wsT<zd>(c, B_LRA, (int64_t)nsrc * k * rmax);
     zd* fb = wsT<zd>(c, B_LRB, (int64_t)nsrc * k * rmax);
