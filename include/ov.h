@@ -444,6 +444,19 @@ int ov_u1_current(ov_context *ctx, const int32_t dims[4], const void *U, double 
 int ov_tridiag_eigenvalues(int32_t k, const double *alpha, const double *beta, const double *delta,
                            double *eig);
 
+/* One eigenvector of the same T_k, on the host: the right eigenvector
+ * (T_k y = theta y; left = 0) or the left one (z^dag T_k = theta z^dag, i.e.
+ * T_k^dag z = conj(theta) z; left = 1) for the eigenvalue theta (host
+ * double[2]), by three steps of inverse iteration with a pivoted tridiagonal
+ * solve (Wilkinson, The Algebraic Eigenvalue Problem, ch. 9), O(k).  vec
+ * (host double[2k], interleaved complex) receives it with unit 2-norm.  theta
+ * should be an eigenvalue of T_k to working accuracy (e.g. from
+ * ov_tridiag_eigenvalues); a nearby value gives the eigenvector of the nearest
+ * eigenvalue.  Returns OV_OK, OV_ERR_INVALID_ARG, OV_ERR_NONFINITE or
+ * OV_ERR_NOCONV (a solve overflowed). */
+int ov_tridiag_eigenvector(int32_t k, const double *alpha, const double *beta, const double *delta,
+                           const double *theta, int32_t left, double *vec);
+
 /* One complex k x k product of the kind the Frechet adjoint's iteration forms
  * (Theorem 1: X_i^{-H} E X_i^{-H} and sgn(T)^H E sgn(T)^H):
  * C = op(A) op(B), op = identity (flag 0) or conjugate transpose (flag 1).

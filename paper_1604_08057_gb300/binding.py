@@ -70,7 +70,8 @@ EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", 
            "ov_tsl_sign", "ov_tsl_sign_vjp", "ov_tsl_coefficients", "ov_profile_enable", "ov_profile_read",
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
            "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_overlap_apply", "ov_overlap_solve", "ov_u1_current",
-           "ov_kk_gemm", "ov_tsl_sign_deflated", "ov_tsl_sign_jvp_deflated", "ov_strerror"]
+           "ov_kk_gemm", "ov_tsl_sign_deflated", "ov_tsl_sign_jvp_deflated",
+           "ov_tridiag_eigenvector", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -109,6 +110,7 @@ def load(path: str = LIB_PATH):
     lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
     lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
     lib.ov_tridiag_eigenvalues.argtypes = [I32, P, P, P, P]
+    lib.ov_tridiag_eigenvector.argtypes = [I32, P, P, P, P, I32, P]
     lib.ov_overlap_apply.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, P, ctypes.POINTER(Info)]
     lib.ov_overlap_solve.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, D, I32, P, ctypes.POINTER(I32),
                                      ctypes.POINTER(D)]
@@ -289,6 +291,20 @@ def kk_gemm(a, b, ha=False, hb=False, mode="split"):
     _check(load().ov_kk_gemm(ctx, a.data_ptr(), int(bool(ha)), b.data_ptr(), int(bool(hb)), c.data_ptr(),
                              a.shape[0], {"fp64": 1, "split": 2}[mode]), "ov_kk_gemm")
     return c
+
+
+def tridiag_eigenvector(alpha, beta, delta, theta, left=False):
+    """Right (or, with left=True, left: z^dag T = theta z^dag) eigenvector of the TSL
+    tridiagonal for the eigenvalue theta, unit norm, by inverse iteration (host)."""
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128))
+    b = np.ascontiguousarray(np.asarray(beta, dtype=np.complex128))
+    d = np.ascontiguousarray(np.asarray(delta, dtype=np.float64))
+    k = a.size
+    th = np.array([complex(theta)], dtype=np.complex128)
+    out = np.zeros(k, dtype=np.complex128)
+    _check(load().ov_tridiag_eigenvector(k, a.ctypes.data, b.ctypes.data, d.ctypes.data, th.ctypes.data,
+                                         int(bool(left)), out.ctypes.data), "ov_tridiag_eigenvector")
+    return out
 
 
 def _dims(u: torch.Tensor):

@@ -114,3 +114,94 @@ extern "C" int ov_tridiag_eigenvalues(int32_t k, const double* alpha, const doub
   }
   return OV_OK;
 }
+
+// Eigenvectors of T_k for a given (Ritz) eigenvalue theta, by inverse iteration
+// (Wilkinson, "The Algebraic Eigenvalue Problem", ch. 9): three solves of
+// (M - sigma) x = x with M = T_k (right eigenvector) or M = T_k^dag and
+// sigma = conj(theta) (left eigenvector z, z^dag T_k = theta z^dag), each by
+// Gaussian elimination with partial pivoting on the tridiagonal (rows exchanged
+// as needed; the fill-in is one second superdiagonal).  A pivot that vanishes
+// exactly is replaced by eps ||M||, which keeps the solve finite and leaves its
+// direction that of the eigenvector.
+namespace {
+
+bool tridiag_solve(std::vector<cx> dl, std::vector<cx> d, std::vector<cx> du, std::vector<cx>& b, double tiny) {
+  const int n = (int)d.size();
+  std::vector<cx> du2(n > 2 ? n - 2 : 0, cx(0.0, 0.0));
+  std::vector<char> swapped(n > 1 ? n - 1 : 0, 0);
+  for (int i = 0; i + 1 < n; ++i) {
+    if (std::abs(d[i]) >= std::abs(dl[i])) {
+      if (d[i] == cx(0.0, 0.0)) d[i] = tiny;
+      const cx f = dl[i] / d[i];
+      dl[i] = f;
+      d[i + 1] -= f * du[i];
+    } else {
+      const cx f = d[i] / dl[i];
+      d[i] = dl[i];
+      dl[i] = f;
+      const cx t = du[i];
+      du[i] = d[i + 1];
+      d[i + 1] = t - f * d[i + 1];
+      if (i + 2 < n) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du[i + 1];
+      }
+      swapped[i] = 1;
+    }
+  }
+  if (d[n - 1] == cx(0.0, 0.0)) d[n - 1] = tiny;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (swapped[i]) {
+      const cx t = b[i];
+      b[i] = b[i + 1];
+      b[i + 1] = t - dl[i] * b[i];
+    } else {
+      b[i + 1] -= dl[i] * b[i];
+    }
+  }
+  b[n - 1] /= d[n - 1];
+  if (n > 1) b[n - 2] = (b[n - 2] - du[n - 2] * b[n - 1]) / d[n - 2];
+  for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / d[i];
+  for (const cx& v : b)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" int ov_tridiag_eigenvector(int32_t k, const double* alpha, const double* beta, const double* delta,
+                                      const double* theta, int32_t left, double* vec) {
+  if (k < 1 || !alpha || !delta || !theta || !vec || (k > 1 && !beta) || (left != 0 && left != 1))
+    return OV_ERR_INVALID_ARG;
+  const cx th(theta[0], theta[1]);
+  std::vector<cx> d(k), dl(k > 1 ? k - 1 : 0), du(k > 1 ? k - 1 : 0);
+  double nrm = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const cx a(alpha[2 * j], alpha[2 * j + 1]);
+    d[j] = left ? std::conj(a) - std::conj(th) : a - th;
+    nrm = std::max(nrm, std::abs(a));
+  }
+  for (int j = 1; j < k; ++j) {
+    const cx b(beta[2 * j], beta[2 * j + 1]);   // T[j-1][j]
+    const cx s(delta[j], 0.0);                  // T[j][j-1]
+    du[j - 1] = left ? std::conj(s) : b;
+    dl[j - 1] = left ? std::conj(b) : s;
+    nrm = std::max(nrm, std::max(std::abs(b), std::abs(s)));
+  }
+  if (!std::isfinite(nrm) || !std::isfinite(th.real()) || !std::isfinite(th.imag())) return OV_ERR_NONFINITE;
+  const double tiny = 2.220446049250313e-16 * (nrm > 0.0 ? nrm : 1.0);
+  std::vector<cx> x(k, cx(1.0 / std::sqrt((double)k), 0.0));
+  for (int it = 0; it < 3; ++it) {
+    if (!tridiag_solve(dl, d, du, x, tiny)) return OV_ERR_NOCONV;
+    double s = 0.0;
+    for (const cx& v : x) s += std::norm(v);
+    s = std::sqrt(s);
+    if (!(s > 0.0) || !std::isfinite(s)) return OV_ERR_NOCONV;
+    for (cx& v : x) v /= s;
+  }
+  for (int j = 0; j < k; ++j) {
+    vec[2 * j] = x[j].real();
+    vec[2 * j + 1] = x[j].imag();
+  }
+  return OV_OK;
+}

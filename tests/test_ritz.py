@@ -78,3 +78,40 @@ def test_rejects_non_finite_input():
     with pytest.raises(binding.OVError) as exc:
         binding.tridiag_eigenvalues(a, b, d)
     assert exc.value.status == -6
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 40, 300])
+def test_tridiagonal_eigenvectors_right_and_left(k):
+    """ov_tridiag_eigenvector: T y = theta y and z^dag T = theta z^dag for every
+    eigenvalue of random TSL tridiagonals, unit norm, against the residual bound
+    of a backward-stable solve (and numpy's eigenvectors up to phase)."""
+    rng = np.random.default_rng(500 + k)
+    a, b, d = _random_tsl_tridiag(k, rng)
+    t = tsl.tridiag(a, b, d)
+    theta = binding.tridiag_eigenvalues(a, b, d)
+    nt = np.linalg.norm(t, 2)
+    for th in theta[: min(k, 25)]:
+        y = binding.tridiag_eigenvector(a, b, d, th)
+        z = binding.tridiag_eigenvector(a, b, d, th, left=True)
+        assert abs(np.linalg.norm(y) - 1) <= 1e-12 and abs(np.linalg.norm(z) - 1) <= 1e-12
+        assert np.linalg.norm(t @ y - th * y) <= 1e-9 * nt
+        assert np.linalg.norm(z.conj() @ t - th * z.conj()) <= 1e-9 * nt
+
+
+def test_tridiagonal_eigenvectors_match_dense_eig():
+    rng = np.random.default_rng(7)
+    a, b, d = _random_tsl_tridiag(12, rng)
+    t = tsl.tridiag(a, b, d)
+    w, v = np.linalg.eig(t)
+    for i in range(12):
+        y = binding.tridiag_eigenvector(a, b, d, w[i])
+        vi = v[:, i] / np.linalg.norm(v[:, i])
+        phase = np.vdot(vi, y)
+        assert abs(abs(phase) - 1) <= 1e-9
+        assert np.linalg.norm(y - phase * vi) <= 1e-9
+
+
+def test_tridiagonal_eigenvector_rejects_bad_arguments():
+    a, b, d = _random_tsl_tridiag(4, np.random.default_rng(1))
+    with pytest.raises(binding.OVError):
+        binding.tridiag_eigenvector(a, b, d, np.nan)
