@@ -286,6 +286,28 @@ int ov_tsl_sign_deflated(ov_context *ctx, const int32_t dims[4], const void *U, 
                          int32_t nsrc, const void *b, int32_t k, int32_t l, const double *lam,
                          const void *R, const void *L, void *x, ov_tsl_info *info);
 
+/* Eigen-triples for the deflation from the last forward pass on this context
+ * (ov_tsl_sign or ov_tsl_sign_vjp with the same dims, the same k and
+ * precision, no segments; the bases V_k, W_k and T_k are still held): the
+ * Ritz triples of source src.  The eigenvalues theta of T_k
+ * (ov_tridiag_eigenvalues) are taken in order of |theta| (the paper deflates
+ * the eigenvalues smallest in absolute value); for up to 2 lmax + 8 of them the
+ * right and left eigenvectors y, z of T_k (ov_tridiag_eigenvector, scaled to
+ * z^dag y = 1) give R = V_k y and L = W_k z (then L^dag R = 1 while the bases
+ * are biorthogonal), and the residual ||H R - theta R|| / ||R|| is computed
+ * with one application of H.  Those with residual <= tol are written, in
+ * |theta| order: l_out (host) their number (<= lmax), lam (host
+ * double[2 lmax]) their theta, R and L (device arrays of lmax spinor fields,
+ * complex128 user layout) the vectors, resid (host double[lmax], may be NULL)
+ * the residuals.  The paper computes the eigen-triples by Arnoldi (ARPACK);
+ * Ritz triples of the TSL's own Krylov space are this library's source (the
+ * converged ones are eigen-triples to the stated residual).  U, mu, m_w: as
+ * in the forward pass.  Returns OV_OK, OV_ERR_INVALID_ARG (no matching
+ * forward pass, lmax < 1, tol <= 0, src out of range), OV_ERR_NOCONV. */
+int ov_tsl_ritz_triples(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w, int32_t src,
+                        int32_t k, int32_t lmax, double tol, int32_t *l_out, double *lam, void *R, void *L,
+                        double *resid);
+
 /* ov_tsl_sign_jvp_deflated: the generalised deflation of Theorem 1's block
  * matrix B = [[H, dH], [0, H]] (Sec. 3, Eqs. x_final, xinv_final,
  * projector_1, final_res), dH along (E, m_dir) as in ov_block_tsl_sign, for

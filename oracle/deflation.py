@@ -179,3 +179,42 @@ def deflated_block_lattice(u, b, mu, m_w, k, e, m_dir, lam, R, L, dR, dL, rebior
     dx = xt + (r @ (sg * c) + dr @ (sg * a)).reshape(b.shape)
     x = xb + (r @ (sg * a)).reshape(b.shape)
     return dx, x
+
+
+def ritz_triples(fwd, u, mu, m_w, lmax, tol):
+    """Ritz triples of a TSL forward pass (tsl.TSLResult with its bases): the
+    eigenvalues theta of T_k in order of |theta|, right and left eigenvectors of T_k
+    from its dense eigendecomposition (the rows of Y^{-1} are the left ones, so that
+    z_i^dag y_j = delta_ij), R = V_k y, L = W_k z, and the residual
+    ||H R - theta R|| / ||R||; up to lmax with residual <= tol.  A pair is checked
+    only when |y_k| max_j delta_j <= 10 tol (y of unit norm; the Lanczos residual
+    of (theta, V_k y) is delta_{k+1} |y_k| ||v_{k+1}||), at most 2 lmax + 8 pairs.
+    Returns (theta, R, L, residuals) with R, L stacked as fields."""
+    from . import dirac
+    theta, y = np.linalg.eig(fwd.t)
+    zh = np.linalg.inv(y)                      # rows: z_i^dag
+    order = np.argsort(np.abs(theta), kind="stable")
+    vm = np.stack([a.ravel() for a in fwd.v], axis=1)
+    wm = np.stack([a.ravel() for a in fwd.w], axis=1)
+    shape = fwd.v[0].shape
+    out_t, out_r, out_l, out_res = [], [], [], []
+    dmax = float(np.max(np.abs(np.diag(fwd.t, -1)))) if len(theta) > 1 else 0.0
+    checks = 0
+    for i in order:
+        if len(out_t) >= lmax or checks >= 2 * lmax + 8:
+            break
+        yi = y[:, i] / np.linalg.norm(y[:, i])
+        if abs(yi[-1]) * dmax > 10 * tol:
+            continue
+        checks += 1
+        r = (vm @ y[:, i]).reshape(shape)
+        l_ = (wm @ zh[i, :].conj()).reshape(shape)
+        res = np.linalg.norm(dirac.apply_h(u, r, mu, m_w) - theta[i] * r) / np.linalg.norm(r)
+        if res <= tol:
+            out_t.append(theta[i])
+            out_r.append(r)
+            out_l.append(l_)
+            out_res.append(res)
+    if not out_t:
+        return np.zeros(0, complex), np.zeros((0,) + shape, complex), np.zeros((0,) + shape, complex), np.zeros(0)
+    return np.array(out_t), np.stack(out_r), np.stack(out_l), np.array(out_res)

@@ -71,7 +71,7 @@ EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", 
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
            "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_overlap_apply", "ov_overlap_solve", "ov_u1_current",
            "ov_kk_gemm", "ov_tsl_sign_deflated", "ov_tsl_sign_jvp_deflated",
-           "ov_tridiag_eigenvector", "ov_strerror"]
+           "ov_tridiag_eigenvector", "ov_tsl_ritz_triples", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -111,6 +111,7 @@ def load(path: str = LIB_PATH):
     lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
     lib.ov_tridiag_eigenvalues.argtypes = [I32, P, P, P, P]
     lib.ov_tridiag_eigenvector.argtypes = [I32, P, P, P, P, I32, P]
+    lib.ov_tsl_ritz_triples.argtypes = [P, dims_t, P, D, D, I32, I32, I32, D, ctypes.POINTER(I32), P, P, P, P]
     lib.ov_overlap_apply.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, P, ctypes.POINTER(Info)]
     lib.ov_overlap_solve.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, D, I32, P, ctypes.POINTER(I32),
                                      ctypes.POINTER(D)]
@@ -469,6 +470,27 @@ def _eigen_args(u, lam, fields):
         out.append(f.contiguous())
     lam_d = lam.view(np.float64).copy()
     return l, lam_d, out
+
+
+def ritz_triples(u, mu, m_w, k, lmax, tol, src=0, precision="fp64", rebiorth=1, passes=2):
+    """Ritz triples (theta, R, L, residual) of the last forward pass on the cached
+    context for these options (a preceding tsl_sign or tsl_sign_vjp with the same U,
+    k): up to lmax with ||H R - theta R|| / ||R|| <= tol, in order of |theta|."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    shape = (lmax,) + tuple(u.shape[:4]) + (4, 3)
+    R = torch.empty(shape, dtype=torch.complex128, device=u.device)
+    L = torch.empty_like(R)
+    lam = np.zeros(lmax, dtype=np.complex128)
+    res = np.zeros(lmax, dtype=np.float64)
+    nl = ctypes.c_int32(0)
+    ctx = context(precision, rebiorth, passes)
+    _check(lib.ov_tsl_ritz_triples(ctx, dims, _ptr(u), float(mu), float(m_w), int(src), int(k), int(lmax),
+                                   float(tol), ctypes.byref(nl), lam.ctypes.data, _ptr(R), _ptr(L),
+                                   res.ctypes.data), "ov_tsl_ritz_triples")
+    n = nl.value
+    return lam[:n], R[:n], L[:n], res[:n]
 
 
 def tsl_sign_deflated(u, mu, m_w, b, k, lam, R, L, precision="fp64", rebiorth=1, passes=2, return_info=False):

@@ -121,6 +121,9 @@ template <typename R> void basis_dots(const Lat<R>& L, int nvec, const R* x, int
 template <typename R> void basis_dots_range(const Lat<R>& L, int j0, int nvec, const R* x, int64_t x_src_stride,
                                             zd* out, zd* cpart, cudaStream_t st);
 template <typename R> void combine(const Lat<R>& L, int nvec, const zd* y, double* out_aos, cudaStream_t st);
+// out_aos (one field, user layout) = sum_{j < nvec} y_j u_j of source src, u = V (side 0) or W (side 1)
+template <typename R> void ritz_combine(const Lat<R>& L, int src, int side, int nvec, const zd* y, double* out_aos,
+                                       cudaStream_t st);
 // out (+)= sum_{j0 <= j < j0 + nvec} y_j v_j  (accumulate when acc is set)
 template <typename R> void combine_range(const Lat<R>& L, int j0, int nvec, const zd* y, double* out_aos, bool acc,
                                          cudaStream_t st);

@@ -1163,6 +1163,42 @@ __global__ void __launch_bounds__(BS) k_combine(Lat<R> L, int j0, int nvec, cons
     for (int c = 0; c < 12; ++c) o[c] = make_double2(acc[c].re, acc[c].im);
   }
 }
+// out = sum_{j < nvec} y_j u_j for one source, u = V (side 0) or W (side 1): a Ritz
+// vector of the TSL (right V_k y, left W_k z), written in the user layout
+template <typename R>
+__global__ void __launch_bounds__(BS) k_ritz_combine(Lat<R> L, int src, int side, int nvec, const zd* __restrict__ y,
+                                                     double* __restrict__ out) {
+  __shared__ zd ys[32];
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t V = L.g.V;
+  zd acc[12];
+#pragma unroll
+  for (int c = 0; c < 12; ++c) acc[c] = mk(0.0, 0.0);
+  for (int i0 = 0; i0 < nvec; i0 += 32) {
+    const int n = min(32, nvec - i0);
+    __syncthreads();
+    if (threadIdx.x < n) ys[threadIdx.x] = y[i0 + threadIdx.x];
+    __syncthreads();
+    if (x < V) {
+      Spinor<R> e;
+      for (int t = 0; t < n; ++t) {
+        load_spinor(side ? L.basis_w(src, i0 + t) : L.basis_v(src, i0 + t), V, x, e);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) cmac(acc[c], ys[t], mk((double)e.c[c].re, (double)e.c[c].im));
+      }
+    }
+  }
+  if (x < V) {
+    double2* o = reinterpret_cast<double2*>(out) + x * 12;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) o[c] = make_double2(acc[c].re, acc[c].im);
+  }
+}
+template <typename R>
+void ritz_combine(const Lat<R>& L, int src, int side, int nvec, const zd* y, double* out, cudaStream_t st) {
+  k_ritz_combine<R><<<nblocks(L.g.V, BS), BS, 0, st>>>(L, src, side, nvec, y, out);
+}
+
 template <typename R>
 void combine_range(const Lat<R>& L, int j0, int nvec, const zd* y, double* out, bool acc, cudaStream_t st) {
   k_combine<R><<<dim3(nblocks(L.g.V, site_bs(L.g.V)), L.nsrc), site_bs(L.g.V), 0, st>>>(L, j0, nvec, y, out, acc ? 1 : 0);
@@ -1633,6 +1669,7 @@ void eps_norms(const double* a_top, const double* a_bot, const double* b, int ns
 }
 
 #define OV_INST(R)                                                                                        \
+  template void ritz_combine<R>(const Lat<R>&, int, int, int, const zd*, double*, cudaStream_t);        \
   template void pack_spinors<R>(const double*, R*, int, int64_t, int64_t, cudaStream_t);                 \
   template void pack_block_start<R>(const double*, const double*, R*, R*, int, int64_t, int64_t,          \
                                     cudaStream_t);                                                       \

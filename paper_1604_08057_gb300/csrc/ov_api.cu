@@ -22,7 +22,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, NBUF
 };
 
 struct Status {
@@ -70,6 +70,9 @@ struct ov_context {
   bool host_buf[NBUF] = {};     // allocated as mapped pinned host memory (options.basis_memory)
   // coefficients of the last forward pass (for ov_tsl_coefficients)
   int last_k = 0, last_nsrc = 0;
+  // shape of the last forward pass whose bases stay in B_BV / B_BW (for ov_tsl_ritz_triples)
+  int last_block = 0, last_seg = 0, last_prec = -1;
+  int32_t last_dims[4] = {0, 0, 0, 0};
   cudaEvent_t ev[8] = {};
   Prof* prof = nullptr;
   int64_t launches = 0;
@@ -846,6 +849,10 @@ int tsl_sign_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   int st = scalar_status(hsc, &kr, k);
   c->last_k = k;
   c->last_nsrc = nsrc;
+  c->last_block = 0;
+  c->last_seg = S > 0 ? 1 : 0;
+  c->last_prec = c->opt.precision;
+  std::copy(dims, dims + 4, c->last_dims);
   if (info) info->k_reached = kr;
   if (st != OV_OK) return st;
   if (c->opt.diagnostics) {
@@ -914,6 +921,10 @@ int block_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, d
   int st = scalar_status(hsc, &kr, k);
   c->last_k = k;
   c->last_nsrc = nsrc;
+  c->last_block = 1;
+  c->last_seg = 0;
+  c->last_prec = c->opt.precision;
+  std::copy(dims, dims + 4, c->last_dims);
   if (info) info->k_reached = kr;
   if (st != OV_OK) return st;
   if (c->opt.diagnostics) {
@@ -955,6 +966,99 @@ void merge_info(ov_tsl_info* acc, const ov_tsl_info& one) {
   if (one.k_reached < acc->k_reached) acc->k_reached = one.k_reached;
   if (one.newton_iters > acc->newton_iters) acc->newton_iters = one.newton_iters;
   for (int i = 0; i < 8; ++i) acc->t_ms[i] += one.t_ms[i];
+}
+
+// Ritz triples of the last forward pass (eigen-triples for deflation, Sec. 3):
+// eigenvalues theta of T_k on the host, the candidates smallest in |theta|, their
+// right and left eigenvectors y, z of T_k (inverse iteration, z^dag y = 1), the Ritz
+// vectors R = V_k y and L = W_k z on the device, and the true residual
+// ||H R - theta R|| / ||R||; candidates at or below tol are returned in |theta| order.
+template <typename R>
+int ritz_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int src, int k, int lmax,
+              double tol, int32_t* l_out, double* lam, void* Rv, void* Lv, double* resid) {
+  check_ptr(Rv);
+  check_ptr(Lv);
+  Lat<R> L = setup<R>(c, dims, U, mu, m_w, c->last_nsrc, k, true);
+  const int64_t V = L.g.V, n = 12 * V, fd = 24 * V;
+  std::vector<double> al(2 * k), be(2 * k), de(k), th(2 * k);
+  CK(cudaMemcpyAsync(al.data(), L.alpha + (int64_t)src * k, sizeof(zd) * k, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(be.data(), L.beta + (int64_t)src * k, sizeof(zd) * k, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(de.data(), L.delta + (int64_t)src * k, sizeof(double) * k, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  int st = ov_tridiag_eigenvalues(k, al.data(), be.data(), de.data(), th.data());
+  if (st != OV_OK) return st;
+  std::vector<int> order(k);
+  for (int i = 0; i < k; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return std::hypot(th[2 * a], th[2 * a + 1]) < std::hypot(th[2 * b], th[2 * b + 1]);
+  });
+  // a Ritz pair is checked with H only when the bottom entry of its unit eigenvector,
+  // times the largest subdiagonal of T_k, is at most 10 tol (the Lanczos residual of
+  // (theta, V_k y) is delta_{k+1} |y_k| ||v_{k+1}||); at most 2 lmax + 8 such checks
+  const int nchecks = 2 * lmax + 8;
+  double dmax = 0.0;
+  for (int j = 1; j < k; ++j) dmax = std::max(dmax, std::abs(de[j]));
+  zd* yd = wsT<zd>(c, B_RZY, 2 * (int64_t)k);
+  double* hf = wsT<double>(c, B_RZH, fd);      // H R
+  zd* dd = wsT<zd>(c, B_RZD, 160);             // dots and their partials
+  Lat<R> L1 = L;
+  L1.nsrc = 1;
+  std::vector<double> y(2 * k), z(2 * k);
+  double* rout = static_cast<double*>(Rv);
+  double* lout = static_cast<double*>(Lv);
+  int got = 0, checks = 0;
+  for (int ci = 0; ci < k && got < lmax && checks < nchecks; ++ci) {
+    const int i = order[ci];
+    const double t2[2] = {th[2 * i], th[2 * i + 1]};
+    if (ov_tridiag_eigenvector(k, al.data(), be.data(), de.data(), t2, 0, y.data()) != OV_OK) continue;
+    if (std::hypot(y[2 * (k - 1)], y[2 * (k - 1) + 1]) * dmax > 10.0 * tol) continue;
+    ++checks;
+    if (ov_tridiag_eigenvector(k, al.data(), be.data(), de.data(), t2, 1, z.data()) != OV_OK) continue;
+    // z <- z / conj(z^dag y), so that z^dag y = 1
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < k; ++j) {
+      sr += z[2 * j] * y[2 * j] + z[2 * j + 1] * y[2 * j + 1];
+      si += z[2 * j] * y[2 * j + 1] - z[2 * j + 1] * y[2 * j];
+    }
+    const double s2 = sr * sr + si * si;
+    if (!(s2 > 1e-16)) continue;   // a nearly defective Ritz value: left and right nearly orthogonal
+    for (int j = 0; j < k; ++j) {  // z / conj(s) = z s / |s|^2
+      const double a = z[2 * j], b = z[2 * j + 1];
+      z[2 * j] = (a * sr - b * si) / s2;
+      z[2 * j + 1] = (a * si + b * sr) / s2;
+    }
+    double* ro = rout + (int64_t)got * fd;
+    double* lo = lout + (int64_t)got * fd;
+    CK(cudaMemcpyAsync(yd, y.data(), sizeof(zd) * k, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(yd + k, z.data(), sizeof(zd) * k, cudaMemcpyHostToDevice, c->st));
+    run(c, OV_KIND_COMBINE, 2, [&] {
+      ritz_combine(L, src, 0, k, yd, ro, c->st);
+      ritz_combine(L, src, 1, k, yd + k, lo, c->st);
+    });
+    // residual: H R - theta R
+    run(c, OV_KIND_LAYOUT, 1, [&] { pack_spinors<R>(ro, L.r, 1, V, L.vs, c->st); });
+    run(c, OV_KIND_APPLY_H, 1, [&] { apply_h(L1, L.r, L.p, 0, c->st, 0, nullptr); });
+    run(c, OV_KIND_LAYOUT, 1, [&] { unpack_spinors<R>(L.p, hf, 1, V, L.vs, c->st); });
+    const zd mth = mk(-t2[0], -t2[1]);
+    CK(cudaMemcpyAsync(dd, &mth, sizeof(zd), cudaMemcpyHostToDevice, c->st));
+    run(c, OV_KIND_COMBINE, 3, [&] {
+      vec_update(hf, ro, fd, 1, dd, 1.0, n, c->st);
+      vec_dots(hf, fd, 1, hf, n, dd + 1, dd + 4, c->st);
+      vec_dots(ro, fd, 1, ro, n, dd + 2, dd + 4, c->st);
+    });
+    launch_check();
+    zd nrm[2];
+    CK(cudaMemcpyAsync(nrm, dd + 1, 2 * sizeof(zd), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const double res = std::sqrt(nrm[0].re / nrm[1].re);
+    if (!(res <= tol)) continue;
+    lam[2 * got] = t2[0];
+    lam[2 * got + 1] = t2[1];
+    if (resid) resid[got] = res;
+    ++got;
+  }
+  *l_out = got;
+  return OV_OK;
 }
 
 // Deflation (Sec. 3): the projected start vector(s) from the caller's eigen-triples,
@@ -1136,6 +1240,10 @@ int vjp_forward(ov_context* c, const int32_t dims[4], const void* U, double mu, 
   int st = scalar_status(F.hsc, &kr, k);
   c->last_k = k;
   c->last_nsrc = nsrc;
+  c->last_block = 0;
+  c->last_seg = S > 0 ? 1 : 0;
+  c->last_prec = c->opt.precision;
+  std::copy(dims, dims + 4, c->last_dims);
   if (info) info->k_reached = kr;
   if (st != OV_OK) return st;
   if (c->opt.diagnostics) {
@@ -2066,6 +2174,21 @@ int ov_block_tsl_sign(ov_context* c, const int32_t dims[4], const void* U, doubl
 int ov_tsl_sign_jvp(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,
                     const void* b, int32_t k, const void* E, double m_dir, void* dx, void* x, ov_tsl_info* info) {
   return ov_block_tsl_sign(c, dims, U, mu, m_w, nsrc, nullptr, b, k, E, m_dir, dx, x, info);
+}
+
+int ov_tsl_ritz_triples(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t src,
+                        int32_t k, int32_t lmax, double tol, int32_t* l_out, double* lam, void* R, void* L,
+                        double* resid) {
+  if (!c || !dims || !l_out || !lam || lmax < 1 || lmax > 4096 || !(tol > 0.0) || k < 2 || k != c->last_k ||
+      src < 0 || src >= c->last_nsrc || c->last_block || c->last_seg || c->last_prec != c->opt.precision ||
+      !std::equal(dims, dims + 4, c->last_dims))
+    return OV_ERR_INVALID_ARG;
+  *l_out = 0;
+  return guarded([&] {
+    return c->opt.precision == OV_MIXED
+               ? ritz_impl<float>(c, dims, U, mu, m_w, src, k, lmax, tol, l_out, lam, R, L, resid)
+               : ritz_impl<double>(c, dims, U, mu, m_w, src, k, lmax, tol, l_out, lam, R, L, resid);
+  });
 }
 
 int ov_tsl_sign_deflated(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t nsrc,

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import deflation, tsl
+from oracle import deflation, overlap, tsl
 from paper_1604_08057_gb300 import binding, inputs
 
 pytestmark = pytest.mark.gpu
@@ -80,3 +80,45 @@ def test_eigenvalue_on_the_imaginary_axis_is_rejected():
     with pytest.raises(binding.OVError) as ei:
         binding.tsl_sign_deflated(T(u), mu, m_w, T(b), 20, lam, T(d["R"]), T(d["L"]))
     assert ei.value.status == -4   # OV_ERR_SIGN_ILLPOSED: sgn is not defined on Re z = 0
+
+
+def test_ritz_triples_match_the_oracle_and_deflate():
+    """Ritz triples of a k = 170 forward pass on 2^4 (m_w = -1, n = 192; the
+    eigenvalues smallest in |lambda| converge last): the accepted eigenvalues and
+    spectral projectors equal the oracle's Ritz triples of the same pass, the
+    residuals are what they claim (H applied independently), and deflating them
+    makes a k = 40 TSL more accurate against the exact sign."""
+    dims, mu, m_w, k = (2, 2, 2, 2), 0.3, -1.0, 170
+    rng = np.random.default_rng(41)
+    u = inputs.su3_links(dims, 0.3, rng)
+    b = inputs.gaussian_spinors(dims, 1, rng)[0]
+    ut, bt = T(u), T(b)
+    binding.tsl_sign(ut, mu, m_w, bt, k)
+    th, R, L, res = binding.ritz_triples(ut, mu, m_w, k, 8, 1e-4)
+    assert len(th) >= 4 and np.all(res <= 1e-4)
+    th_o, R_o, L_o, res_o = deflation.ritz_triples(tsl.tsl_forward(u, b, mu, m_w, k), u, mu, m_w, 8, 1e-4)
+    probe = rng.standard_normal(192) + 1j * rng.standard_normal(192)
+    Rn, Ln = R.cpu().numpy(), L.cpu().numpy()
+    for i in range(len(th)):
+        j = int(np.argmin(np.abs(th_o - th[i])))
+        assert abs(th_o[j] - th[i]) <= 1e-8
+        p_gpu = Rn[i].ravel() * np.vdot(Ln[i].ravel(), probe)
+        p_or = R_o[j].ravel() * np.vdot(L_o[j].ravel(), probe)
+        assert rel(p_gpu, p_or) <= 1e-6
+        hr = binding.apply_H(ut, mu, m_w, R[i]).cpu().numpy()
+        assert abs(np.linalg.norm(hr - th[i] * Rn[i]) / np.linalg.norm(Rn[i]) - res[i]) <= 1e-3 * res[i] + 1e-14
+    lam, r, l_ = deflation.eigentriples(overlap.dense_h(u, mu, m_w))
+    exact = (r @ np.diag(np.sign(lam.real)) @ l_.conj().T) @ b.ravel()
+    plain = binding.tsl_sign(ut, mu, m_w, bt, 40).cpu().numpy()
+    defl = binding.tsl_sign_deflated(ut, mu, m_w, bt, 40, th, R, L).cpu().numpy()
+    assert rel(defl.ravel(), exact) < rel(plain.ravel(), exact)
+
+
+def test_ritz_triples_need_a_matching_forward_pass():
+    dims, mu, m_w = (2, 2, 2, 2), 0.3, -1.0
+    rng = np.random.default_rng(42)
+    u = inputs.su3_links(dims, 0.3, rng)
+    b = inputs.gaussian_spinors(dims, 1, rng)[0]
+    binding.tsl_sign(T(u), mu, m_w, T(b), 30)
+    with pytest.raises(binding.OVError):
+        binding.ritz_triples(T(u), mu, m_w, 31, 4, 1e-6)      # k differs from the last pass

@@ -145,3 +145,24 @@ def test_lattice_forms_agree_with_the_dense_forms():
                                                     d["lam"], r, l_, dr, dl)
     assert rel(xb_lat.ravel(), xb_den) <= 1e-10
     assert rel(dx_lat.ravel(), dx_den) <= 1e-9
+
+
+def test_ritz_triples_of_a_full_krylov_space_are_the_eigen_triples():
+    """With k = n (the 2^4 lattice, n = 192, m_w = -1 where the TSL reaches k = n),
+    the Ritz triples of the TSL are H's eigen-triples: the same eigenvalues, and
+    the same spectral projectors R_i <L_i| as the dense eigendecomposition."""
+    dims, mu, m_w = (2, 2, 2, 2), 0.3, -1.0
+    rng = np.random.default_rng(21)
+    u = inputs.su3_links(dims, 0.3, rng)
+    b = inputs.gaussian_spinors(dims, 1, rng)[0]
+    fwd = tsl.tsl_forward(u, b, mu, m_w, 192)
+    th, R, L, res = deflation.ritz_triples(fwd, u, mu, m_w, 10, 1e-8)
+    assert len(th) == 10 and np.all(res <= 1e-8)
+    lam, r, l_ = deflation.eigentriples(overlap.dense_h(u, mu, m_w))
+    probe = rng.standard_normal(192) + 1j * rng.standard_normal(192)
+    for i in range(10):
+        j = int(np.argmin(np.abs(lam - th[i])))
+        assert abs(lam[j] - th[i]) <= 1e-9 * abs(lam).max()
+        p_ritz = R[i].ravel() * np.vdot(L[i].ravel(), probe)
+        p_eig = r[:, j] * np.vdot(l_[:, j], probe)
+        assert rel(p_ritz, p_eig) <= 1e-7
