@@ -308,6 +308,29 @@ int ov_tsl_ritz_triples(ov_context *ctx, const int32_t dims[4], const void *U, d
                         int32_t k, int32_t lmax, double tol, int32_t *l_out, double *lam, void *R, void *L,
                         double *resid);
 
+/* Eigenvalue and eigenvector derivatives for the generalised deflation (App.
+ * B; computed, as App. E does, by shifted inversions), FP64 whatever the
+ * context's precision: for the eigen-triples (lam, R, L) of H(U, mu) as in
+ * ov_tsl_sign_deflated and the direction (E, m_dir) of ov_block_tsl_sign,
+ *   dlambda_i = L_i^dag dH R_i,
+ *   (lambda_i - H) dR_i = (1 - R_i L_i^dag)(dH - dlambda_i) R_i,
+ *   (conj lambda_i - H^dag) dL_i = (1 - L_i R_i^dag)(dH^dag - conj dlambda_i) L_i,
+ * each solved by conjugate gradients on the normal equations (CG on
+ * A A^dag with A = lambda_i - H, the paper's App. E choice) to relative
+ * residual tol in at most maxit CG steps (two applications of H each), then
+ * normalised by L_i^dag dR_i = 0, dL_i^dag R_i = 0.
+ * dlam (host double[2l]), dR, dL (device arrays of l spinor fields), resid
+ * (host double[2l], may be NULL: the right and left solves' final relative
+ * residuals).  Accuracy needs the eigen-triples to be accurate and the
+ * eigenvalue separated from the others (the shifted operator's smallest
+ * singular value on the complement is about the gap; CG needs about
+ * ||H|| / gap steps per digit).  Returns OV_OK,
+ * OV_ERR_NOCONV (a solve missed tol; everything is still written),
+ * OV_ERR_INVALID_ARG, OV_ERR_NONFINITE. */
+int ov_eigen_derivatives(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w,
+                         const void *E, double m_dir, int32_t l, const double *lam, const void *R, const void *L,
+                         double tol, int32_t maxit, double *dlam, void *dR, void *dL, double *resid);
+
 /* ov_tsl_sign_jvp_deflated: the generalised deflation of Theorem 1's block
  * matrix B = [[H, dH], [0, H]] (Sec. 3, Eqs. x_final, xinv_final,
  * projector_1, final_res), dH along (E, m_dir) as in ov_block_tsl_sign, for

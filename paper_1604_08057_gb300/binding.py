@@ -71,7 +71,8 @@ EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", 
            "ov_launch_count", "ov_apply_H_noalloc", "ov_autotune", "ov_set_stencil_variants",
            "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_overlap_apply", "ov_overlap_solve", "ov_u1_current",
            "ov_kk_gemm", "ov_tsl_sign_deflated", "ov_tsl_sign_jvp_deflated",
-           "ov_tridiag_eigenvector", "ov_tsl_ritz_triples", "ov_strerror"]
+           "ov_tridiag_eigenvector", "ov_tsl_ritz_triples",
+           "ov_eigen_derivatives", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
     lib.ov_tridiag_eigenvalues.argtypes = [I32, P, P, P, P]
     lib.ov_tridiag_eigenvector.argtypes = [I32, P, P, P, P, I32, P]
     lib.ov_tsl_ritz_triples.argtypes = [P, dims_t, P, D, D, I32, I32, I32, D, ctypes.POINTER(I32), P, P, P, P]
+    lib.ov_eigen_derivatives.argtypes = [P, dims_t, P, D, D, P, D, I32, P, P, P, D, I32, P, P, P, P]
     lib.ov_overlap_apply.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, P, ctypes.POINTER(Info)]
     lib.ov_overlap_solve.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, D, I32, P, ctypes.POINTER(I32),
                                      ctypes.POINTER(D)]
@@ -491,6 +493,30 @@ def ritz_triples(u, mu, m_w, k, lmax, tol, src=0, precision="fp64", rebiorth=1, 
                                    res.ctypes.data), "ov_tsl_ritz_triples")
     n = nl.value
     return lam[:n], R[:n], L[:n], res[:n]
+
+
+def eigen_derivatives(u, mu, m_w, lam, R, L, e=None, m_dir=0.0, tol=1e-11, maxit=20000):
+    """(dlam, dR, dL, residuals): derivatives of the eigen-triples along (E, m_dir) by
+    shifted solves (CG on the normal equations; App. B, E), normalised by
+    <L_i|dR_i> = <dL_i|R_i> = 0."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    if e is not None:
+        _dims(e)
+        e = e.contiguous()
+    l, lam_d, (rr, ll) = _eigen_args(u, lam, (R, L))
+    dR = torch.empty_like(rr)
+    dL = torch.empty_like(ll)
+    dlam = np.zeros(l, dtype=np.complex128)
+    res = np.zeros(2 * l, dtype=np.float64)
+    ctx = context("fp64", 1, 2)
+    st = lib.ov_eigen_derivatives(ctx, dims, _ptr(u), float(mu), float(m_w), _ptr(e) if e is not None else None,
+                                  float(m_dir), l, lam_d.ctypes.data, _ptr(rr), _ptr(ll), float(tol), int(maxit),
+                                  dlam.ctypes.data, _ptr(dR), _ptr(dL), res.ctypes.data)
+    if st not in (0, -9):     # OV_OK, or OV_ERR_NOCONV with everything written
+        _check(st, "ov_eigen_derivatives")
+    return dlam, dR, dL, res.reshape(l, 2)
 
 
 def tsl_sign_deflated(u, mu, m_w, b, k, lam, R, L, precision="fp64", rebiorth=1, passes=2, return_info=False):

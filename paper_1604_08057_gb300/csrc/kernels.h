@@ -100,6 +100,8 @@ template <typename R> void apply_h(const Lat<R>& L, const R* in, R* out, int dag
 // variant 0 for APPLY_IL (its fields are per-source); apply_h_il, pack_spinors_il and
 // unpack_spinors_il are the interleaved form.
 constexpr int APPLY_IL = 13;
+// out = dH in (dagger 0) or dH^dag in (dagger 1), dH along L.ue (may be null) and L.mdir
+template <typename R> void apply_dh(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st);
 void apply_h_il(const Lat<float>& L, const float* in, float* out, int dagger, cudaStream_t st);
 void pack_spinors_il(const double* aos, float* dst, int nsrc, int64_t V, cudaStream_t st);
 void unpack_spinors_il(const float* f, double* aos, int nsrc, int64_t V, cudaStream_t st);

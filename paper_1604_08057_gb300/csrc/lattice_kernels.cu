@@ -172,6 +172,28 @@ __global__ void __launch_bounds__(BSZ) k_apply_h(Lat<R> L, const R* __restrict__
     if (s0 + i < nsrc) store_spinor(out + (int64_t)(s0 + i) * L.vs, L.g.V, x, o[i]);
 }
 
+// out = dH in (dagger = 0) or dH^dag in (dagger = 1) for every source, dH along the
+// links L.ue (may be null) and L.mdir (App. A, Eq. WD_op is affine in the links;
+// the adjoint exchanges the temporal factors and negates m)
+template <typename R>
+__global__ void __launch_bounds__(BS) k_apply_dh(Lat<R> L, const R* __restrict__ in, R* __restrict__ out,
+                                                 int dagger) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int src = blockIdx.y;
+  if (x >= L.g.V) return;
+  const FieldLoad<R> ld{in + src * L.vs, L.g.V};
+  Spinor<R> o;
+  if (dagger)
+    dh_site_ld(ld, L.ue, L.u, L.g, x, L.kappa, L.efinv, L.ef, -L.mdir, o);
+  else
+    dh_site_ld(ld, L.ue, L.u, L.g, x, L.kappa, L.ef, L.efinv, L.mdir, o);
+  store_spinor(out + src * L.vs, L.g.V, x, o);
+}
+template <typename R>
+void apply_dh(const Lat<R>& L, const R* in, R* out, int dagger, cudaStream_t st) {
+  k_apply_dh<R><<<dim3(nblocks(L.g.V, BS), L.nsrc), BS, 0, st>>>(L, in, out, dagger);
+}
+
 // Sources interleaved innermost (variant APPLY_IL, FP32): component pair cp of site x
 // for source src is the float4 at (x * 6 + cp) * nsrc + src.  The per-site arithmetic
 // is h_site_ld's, operation for operation, so the results equal variant 0's.
@@ -1670,6 +1692,7 @@ void eps_norms(const double* a_top, const double* a_bot, const double* b, int ns
 
 #define OV_INST(R)                                                                                        \
   template void ritz_combine<R>(const Lat<R>&, int, int, int, const zd*, double*, cudaStream_t);        \
+  template void apply_dh<R>(const Lat<R>&, const R*, R*, int, cudaStream_t);                             \
   template void pack_spinors<R>(const double*, R*, int, int64_t, int64_t, cudaStream_t);                 \
   template void pack_block_start<R>(const double*, const double*, R*, R*, int, int64_t, int64_t,          \
                                     cudaStream_t);                                                       \

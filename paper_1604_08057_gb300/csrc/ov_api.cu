@@ -22,7 +22,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, B_EDT1, B_EDT2, B_EDX, B_EDC, B_CGY, B_CGR, B_CGP, B_CGQ, B_CGT, B_CGC, NBUF
 };
 
 struct Status {
@@ -1656,21 +1656,19 @@ int overlap_apply_impl(ov_context* c, const int32_t dims[4], const void* U, doub
 // Returns OV_ERR_NOCONV when the relative residual is still above tol after
 // maxit operator applications (*iters, *resid report where it stopped).
 constexpr int GMRES_M = 30;
-template <typename R>
-int overlap_solve_one(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, const double* rhs,
-                      int k, int dagger, double tol, int maxit, double* x, int* iters, double* resid) {
-  const Geom g = make_geom(dims);
-  const int64_t n = 12 * g.V, n2 = 2 * n;
+// Restarted GMRES(m) on vectors of n complex entries (user layout) for the operator
+// `apply(in, out)`; the same algorithm serves the overlap solve and the shifted
+// solves of the eigenvector derivatives.
+template <typename Apply>
+int gmres_solve(ov_context* c, int64_t n, const double* rhs, double* x, double tol, int maxit, Apply&& apply,
+                int* iters, double* resid) {
+  const int64_t n2 = 2 * n;
   const int m = std::max(1, std::min(maxit, GMRES_M));
   double* Vb = wsT<double>(c, B_GMV, (int64_t)(m + 1) * n2);
   double* r = wsT<double>(c, B_GMR, n2);
   double* ax = wsT<double>(c, B_GMW, n2);
   zd* hd = wsT<zd>(c, B_GMH, 2 * (int64_t)(m + 1));
   zd* part = wsT<zd>(c, B_GMP, 152 * (int64_t)(m + 1));
-  auto apply = [&](const double* in, double* out) {
-    const int st = overlap_apply_impl<R>(c, dims, U, mu, m_w, 1, in, k, dagger, out, nullptr);
-    if (st != OV_OK) throw Status{st};
-  };
   auto dots = [&](const double* basis, int nvec, const double* w, std::vector<zd>& out) {
     run(c, OV_KIND_COMBINE, 2, [&] { vec_dots(basis, n2, nvec, w, n, hd, part, c->st); });
     out.resize(nvec);
@@ -1757,6 +1755,180 @@ int overlap_solve_one(ov_context* c, const int32_t dims[4], const void* U, doubl
   *iters = it;
   *resid = rn / bnorm;
   return rn <= tol * bnorm ? OV_OK : OV_ERR_NOCONV;
+}
+
+template <typename R>
+int overlap_solve_one(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, const double* rhs,
+                      int k, int dagger, double tol, int maxit, double* x, int* iters, double* resid) {
+  const Geom g = make_geom(dims);
+  return gmres_solve(
+      c, 12 * g.V, rhs, x, tol, maxit,
+      [&](const double* in, double* out) {
+        const int st = overlap_apply_impl<R>(c, dims, U, mu, m_w, 1, in, k, dagger, out, nullptr);
+        if (st != OV_OK) throw Status{st};
+      },
+      iters, resid);
+}
+
+// A x = rhs by conjugate gradients on the normal equations A A^dag y = rhs, x = A^dag y
+// (the minimum-norm solution for a consistent singular A), on vectors of n complex
+// entries; the residual ||rhs - A x|| is the CG residual.  maxit counts CG steps.
+template <typename ApplyA, typename ApplyAdag>
+int cg_normal_solve(ov_context* c, int64_t n, const double* rhs, double* x, double tol, int maxit, ApplyA&& apply_a,
+                    ApplyAdag&& apply_adag, int* iters, double* resid) {
+  const int64_t n2 = 2 * n;
+  double* y = wsT<double>(c, B_CGY, n2);
+  double* r = wsT<double>(c, B_CGR, n2);
+  double* p = wsT<double>(c, B_CGP, n2);
+  double* q = wsT<double>(c, B_CGQ, n2);
+  double* t = wsT<double>(c, B_CGT, n2);
+  zd* cd = wsT<zd>(c, B_CGC, 160);
+  auto dot = [&](const double* a, const double* b) {
+    run(c, OV_KIND_COMBINE, 2, [&] { vec_dots(a, n2, 1, b, n, cd + 1, cd + 4, c->st); });
+    zd h;
+    CK(cudaMemcpyAsync(&h, cd + 1, sizeof(zd), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return h.re;
+  };
+  auto axpy = [&](double* w, const double* v, double a) {   // w += a v (a real)
+    const zd ca = mk(a, 0.0);
+    CK(cudaMemcpyAsync(cd, &ca, sizeof(zd), cudaMemcpyHostToDevice, c->st));
+    run(c, OV_KIND_COMBINE, 1, [&] { vec_update(w, v, n2, 1, cd, 1.0, n, c->st); });
+  };
+  CK(cudaMemsetAsync(y, 0, sizeof(double) * n2, c->st));
+  CK(cudaMemcpyAsync(r, rhs, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(p, rhs, sizeof(double) * n2, cudaMemcpyDeviceToDevice, c->st));
+  const double bn = std::sqrt(dot(rhs, rhs));
+  double rr = bn * bn;
+  int it = 0;
+  *iters = 0;
+  *resid = 0.0;
+  if (!std::isfinite(bn)) return OV_ERR_NONFINITE;
+  if (bn > 0.0) {
+    while (std::sqrt(rr) > tol * bn && it < maxit) {
+      apply_adag(p, t);
+      apply_a(t, q);
+      const double pq = dot(p, q);
+      if (!(pq > 0.0) || !std::isfinite(pq)) break;
+      const double al = rr / pq;
+      axpy(y, p, al);
+      axpy(r, q, -al);
+      const double rn = dot(r, r);
+      if (!std::isfinite(rn)) return OV_ERR_NONFINITE;
+      const double be = rn / rr;
+      rr = rn;
+      run(c, OV_KIND_COMBINE, 1, [&] { vec_scale(p, p, be, 0.0, n, c->st); });
+      axpy(p, r, 1.0);
+      ++it;
+    }
+  }
+  apply_adag(y, x);
+  *iters = it;
+  *resid = bn > 0.0 ? std::sqrt(rr) / bn : 0.0;
+  return std::sqrt(rr) <= tol * bn ? OV_OK : OV_ERR_NOCONV;
+}
+
+// Eigenvalue and eigenvector derivatives along (E, m_dir) (App. B, computed as App. E
+// does, by shifted inversions with CG on the normal equations), FP64, for the
+// eigen-triples (lambda_i, R_i, L_i):
+//   dlambda_i = <L_i| dH R_i>,
+//   (lambda_i - H) dR_i = Q_i (dH - dlambda_i) R_i,           Q_i = 1 - R_i <L_i|,
+//   (conj lambda_i - H^dag) dL_i = Q_i^dag (dH^dag - conj dlambda_i) L_i,
+// each by cg_normal_solve (restarted GMRES stagnates on these indefinite shifted
+// operators), then <L_i|dR_i> = 0 and <dL_i|R_i> = 0 imposed (the singular shifted
+// operators fix dR_i, dL_i only up to R_i, L_i).
+int eigderiv_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, const void* E,
+                  double m_dir, int l, const double* lam, const void* Rf, const void* Lf, double tol, int maxit,
+                  double* dlam, void* dRf, void* dLf, double* resid) {
+  check_ptr(Rf);
+  check_ptr(Lf);
+  check_ptr(dRf);
+  check_ptr(dLf);
+  if (E) check_ptr(E);
+  if (!(tol > 0.0) || maxit < 1 || !std::isfinite(m_dir)) throw Status{OV_ERR_INVALID_ARG};
+  Lat<double> L1 = setup<double>(c, dims, U, mu, m_w, 1, 2, false);
+  const int64_t V = L1.g.V, n = 12 * V, fd = 24 * V;
+  if (E) {
+    double* ue = wsT<double>(c, B_ELINKS, link_reals<double>() * V);
+    run(c, OV_KIND_LAYOUT, 1, [&] { pack_links<double>(static_cast<const double*>(E), ue, V, c->st); });
+    L1.ue = ue;
+  }
+  L1.mdir = m_dir;
+  double* t1 = wsT<double>(c, B_EDT1, fd);
+  double* t2 = wsT<double>(c, B_EDT2, fd);
+  zd* cd = wsT<zd>(c, B_EDC, 160);    // [0..3] coefficients, [4..] dot partials
+  auto op = [&](const double* in, double* out, int which, int dagger) {   // which: 0 H, 1 dH
+    run(c, OV_KIND_LAYOUT, 1, [&] { pack_spinors<double>(in, L1.r, 1, V, L1.vs, c->st); });
+    run(c, OV_KIND_APPLY_H, 1, [&] {
+      if (which) apply_dh(L1, L1.r, L1.p, dagger, c->st);
+      else apply_h(L1, L1.r, L1.p, dagger, c->st, 0, nullptr);
+    });
+    run(c, OV_KIND_LAYOUT, 1, [&] { unpack_spinors<double>(L1.p, out, 1, V, L1.vs, c->st); });
+  };
+  auto dot = [&](const double* a, const double* b) {   // a^dag b
+    run(c, OV_KIND_COMBINE, 2, [&] { vec_dots(a, fd, 1, b, n, cd + 1, cd + 4, c->st); });
+    zd h;
+    CK(cudaMemcpyAsync(&h, cd + 1, sizeof(zd), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return h;
+  };
+  auto axpy = [&](double* w, const double* v, zd a) {   // w += a v
+    CK(cudaMemcpyAsync(cd, &a, sizeof(zd), cudaMemcpyHostToDevice, c->st));
+    run(c, OV_KIND_COMBINE, 1, [&] { vec_update(w, v, fd, 1, cd, 1.0, n, c->st); });
+  };
+  const double* Rb = static_cast<const double*>(Rf);
+  const double* Lb = static_cast<const double*>(Lf);
+  double* dRb = static_cast<double*>(dRf);
+  double* dLb = static_cast<double*>(dLf);
+  int worst = OV_OK;
+  for (int i = 0; i < l; ++i) {
+    const double* Ri = Rb + (int64_t)i * fd;
+    const double* Li = Lb + (int64_t)i * fd;
+    const zd li = mk(lam[2 * i], lam[2 * i + 1]);
+    // dlambda_i and the right-hand side of the right derivative
+    op(Ri, t1, 1, 0);
+    const zd dl = dot(Li, t1);
+    dlam[2 * i] = dl.re;
+    dlam[2 * i + 1] = dl.im;
+    axpy(t1, Ri, mk(-dl.re, -dl.im));
+    const zd pr = dot(Li, t1);
+    axpy(t1, Ri, mk(-pr.re, -pr.im));
+    double* x = dRb + (int64_t)i * fd;
+    int it = 0;
+    double rr = 0.0;
+    const zd lic = mk(li.re, -li.im);
+    auto a_r = [&](const double* in, double* out) {   // out = lambda_i in - H in
+      op(in, out, 0, 0);
+      run(c, OV_KIND_COMBINE, 1, [&] { vec_scale(out, out, -1.0, 0.0, n, c->st); });
+      axpy(out, in, li);
+    };
+    auto a_rdag = [&](const double* in, double* out) {   // out = conj(lambda_i) in - H^dag in
+      op(in, out, 0, 1);
+      run(c, OV_KIND_COMBINE, 1, [&] { vec_scale(out, out, -1.0, 0.0, n, c->st); });
+      axpy(out, in, lic);
+    };
+    int st = cg_normal_solve(c, n, t1, x, tol, maxit, a_r, a_rdag, &it, &rr);
+    if (st != OV_OK && st != OV_ERR_NOCONV) return st;
+    if (st == OV_ERR_NOCONV) worst = st;
+    const zd cr = dot(Li, x);
+    axpy(x, Ri, mk(-cr.re, -cr.im));
+    if (resid) resid[2 * i] = rr;
+    // the left derivative
+    op(Li, t2, 1, 1);
+    axpy(t2, Li, mk(-dl.re, dl.im));       // - conj(dlambda) L_i
+    const zd pl = dot(Ri, t2);
+    axpy(t2, Li, mk(-pl.re, -pl.im));
+    double* y = dLb + (int64_t)i * fd;
+    st = cg_normal_solve(c, n, t2, y, tol, maxit, a_rdag, a_r, &it, &rr);
+    if (st != OV_OK && st != OV_ERR_NOCONV) return st;
+    if (st == OV_ERR_NOCONV) worst = st;
+    const zd cl = dot(Ri, y);
+    axpy(y, Li, mk(-cl.re, -cl.im));
+    if (resid) resid[2 * i + 1] = rr;
+  }
+  launch_check();
+  CK(cudaStreamSynchronize(c->st));
+  return worst;
 }
 
 template <typename R>
@@ -2188,6 +2360,15 @@ int ov_tsl_ritz_triples(ov_context* c, const int32_t dims[4], const void* U, dou
     return c->opt.precision == OV_MIXED
                ? ritz_impl<float>(c, dims, U, mu, m_w, src, k, lmax, tol, l_out, lam, R, L, resid)
                : ritz_impl<double>(c, dims, U, mu, m_w, src, k, lmax, tol, l_out, lam, R, L, resid);
+  });
+}
+
+int ov_eigen_derivatives(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, const void* E,
+                         double m_dir, int32_t l, const double* lam, const void* R, const void* L, double tol,
+                         int32_t maxit, double* dlam, void* dR, void* dL, double* resid) {
+  if (!c || !dims || l < 1 || l > 4096 || !lam || !dlam) return OV_ERR_INVALID_ARG;
+  return guarded([&] {
+    return eigderiv_impl(c, dims, U, mu, m_w, E, m_dir, l, lam, R, L, tol, maxit, dlam, dR, dL, resid);
   });
 }
 

@@ -122,3 +122,57 @@ def test_ritz_triples_need_a_matching_forward_pass():
     binding.tsl_sign(T(u), mu, m_w, T(b), 30)
     with pytest.raises(binding.OVError):
         binding.ritz_triples(T(u), mu, m_w, 31, 4, 1e-6)      # k differs from the last pass
+
+
+def _separated(lam_all, lam, count, gap=0.01):
+    """Indices of eigenvalues in lam whose distance to every other eigenvalue of H
+    exceeds gap (the shifted solves are conditioned by the gap)."""
+    sel = []
+    for i, x in enumerate(lam):
+        d = np.abs(lam_all - x)
+        d = d[d > 0]
+        if d.min() > gap:
+            sel.append(i)
+        if len(sel) == count:
+            break
+    return sel
+
+
+def test_eigen_derivatives_match_the_oracle():
+    """dlambda_i, dR_i, dL_i by shifted GMRES on the GPU against the oracle's
+    first-order perturbation formulas from the full eigendecomposition (2^4,
+    m_w = -2, random link direction and mu direction), for eigenvalues separated
+    from the rest by more than 0.01."""
+    u, b, e, mu, m_w = lattice_case(12)
+    m_dir = 0.2
+    d = deflation.lattice_eigendata(u, mu, m_w, 16, e, m_dir)
+    lam_all, _, _ = deflation.eigentriples(d["h"])
+    sel = _separated(lam_all, d["lam"], 3)
+    assert len(sel) >= 2
+    dlam, dR, dL, res = binding.eigen_derivatives(T(u), mu, m_w, d["lam"][sel], T(d["R"][sel]), T(d["L"][sel]),
+                                                  e=T(e), m_dir=m_dir)
+    assert np.all(res <= 1e-10)
+    dR, dL = dR.cpu().numpy(), dL.cpu().numpy()
+    for c, i in enumerate(sel):
+        assert abs(dlam[c] - d["dlam"][i]) <= 1e-10 * max(1.0, abs(d["dlam"][i]))
+        assert rel(dR[c], d["dR"][i]) <= 1e-7, (i, rel(dR[c], d["dR"][i]))
+        assert rel(dL[c], d["dL"][i]) <= 1e-7, (i, rel(dL[c], d["dL"][i]))
+
+
+def test_generalised_deflation_with_gpu_eigen_derivatives():
+    """The full GPU route: eigen-derivatives by shifted solves, then the generalised
+    deflation, against the oracle's deflation with its own eigen-data."""
+    u, b, e, mu, m_w = lattice_case(15)
+    m_dir, k = 0.1, 40
+    d = deflation.lattice_eigendata(u, mu, m_w, 16, e, m_dir)
+    lam_all, _, _ = deflation.eigentriples(d["h"])
+    sel = _separated(lam_all, d["lam"], 4)
+    lam, Rs, Ls = d["lam"][sel], d["R"][sel], d["L"][sel]
+    dlam, dR, dL, res = binding.eigen_derivatives(T(u), mu, m_w, lam, T(Rs), T(Ls), e=T(e), m_dir=m_dir)
+    dx, x = binding.tsl_sign_jvp_deflated(T(u), mu, m_w, T(b), k, lam, T(Rs), T(Ls), dR, dL, e=T(e), m_dir=m_dir)
+    dx, x = dx.cpu().numpy(), x.cpu().numpy()
+    for s in range(2):
+        dx_o, x_o = deflation.deflated_block_lattice(u, b[s], mu, m_w, k, e, m_dir, lam, Rs, Ls,
+                                                     d["dR"][sel], d["dL"][sel])
+        assert rel(x[s], x_o) <= 1e-9
+        assert rel(dx[s], dx_o) <= 1e-7
