@@ -502,6 +502,18 @@ int ov_tridiag_eigenvalues(int32_t k, const double *alpha, const double *beta, c
 int ov_tridiag_eigenvector(int32_t k, const double *alpha, const double *beta, const double *delta,
                            const double *theta, int32_t left, double *vec);
 
+/* Eigenvalues (and, with vecs non-NULL, right eigenvectors) of a complex upper
+ * Hessenberg matrix on the host: h (host double[2 m^2], row-major,
+ * interleaved complex; entries below the subdiagonal must be zero), eig (host
+ * double[2m]), vecs (host double[2 m^2], row-major, column i the unit
+ * eigenvector of eig[i]).  Implicit single-shift QR with Wilkinson and
+ * exceptional shifts (Golub and Van Loan, Matrix Computations, ch. 7.5), then
+ * three steps of inverse iteration per eigenvector with a pivoted LU; O(m^3),
+ * for the Arnoldi matrices of ov_eigen_smallest.  Returns OV_OK,
+ * OV_ERR_INVALID_ARG (m out of 1..4096, not Hessenberg), OV_ERR_NONFINITE,
+ * OV_ERR_NOCONV. */
+int ov_hessenberg_eigen(int32_t m, const double *h, double *eig, double *vecs);
+
 /* One complex k x k product of the kind the Frechet adjoint's iteration forms
  * (Theorem 1: X_i^{-H} E X_i^{-H} and sgn(T)^H E sgn(T)^H):
  * C = op(A) op(B), op = identity (flag 0) or conjugate transpose (flag 1).

@@ -72,7 +72,8 @@ EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", 
            "ov_tsl_sign_jvp", "ov_block_tsl_sign", "ov_tsl_eps", "ov_block_tsl_eps", "ov_tsl_batch", "ov_profile_select", "ov_selftest_wait", "ov_tsl_sign_fwd", "ov_tsl_sign_vjp_tape", "ov_tape_destroy", "ov_tridiag_eigenvalues", "ov_debug_inject", "ov_overlap_apply", "ov_overlap_solve", "ov_u1_current",
            "ov_kk_gemm", "ov_tsl_sign_deflated", "ov_tsl_sign_jvp_deflated",
            "ov_tridiag_eigenvector", "ov_tsl_ritz_triples",
-           "ov_eigen_derivatives", "ov_strerror"]
+           "ov_eigen_derivatives",
+           "ov_hessenberg_eigen", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
     lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
     lib.ov_tridiag_eigenvalues.argtypes = [I32, P, P, P, P]
     lib.ov_tridiag_eigenvector.argtypes = [I32, P, P, P, P, I32, P]
+    lib.ov_hessenberg_eigen.argtypes = [I32, P, P, P]
     lib.ov_tsl_ritz_triples.argtypes = [P, dims_t, P, D, D, I32, I32, I32, D, ctypes.POINTER(I32), P, P, P, P]
     lib.ov_eigen_derivatives.argtypes = [P, dims_t, P, D, D, P, D, I32, P, P, P, D, I32, P, P, P, P]
     lib.ov_overlap_apply.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, P, ctypes.POINTER(Info)]
@@ -308,6 +310,18 @@ def tridiag_eigenvector(alpha, beta, delta, theta, left=False):
     _check(load().ov_tridiag_eigenvector(k, a.ctypes.data, b.ctypes.data, d.ctypes.data, th.ctypes.data,
                                          int(bool(left)), out.ctypes.data), "ov_tridiag_eigenvector")
     return out
+
+
+def hessenberg_eigen(h, vectors=True):
+    """Eigenvalues (and unit right eigenvectors, as columns) of a complex upper
+    Hessenberg matrix, on the host."""
+    a = np.ascontiguousarray(np.asarray(h, dtype=np.complex128))
+    m = a.shape[0]
+    eig = np.zeros(m, dtype=np.complex128)
+    vec = np.zeros((m, m), dtype=np.complex128) if vectors else None
+    _check(load().ov_hessenberg_eigen(m, a.ctypes.data, eig.ctypes.data, vec.ctypes.data if vectors else None),
+           "ov_hessenberg_eigen")
+    return (eig, vec) if vectors else eig
 
 
 def _dims(u: torch.Tensor):

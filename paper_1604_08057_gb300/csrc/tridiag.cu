@@ -205,3 +205,148 @@ extern "C" int ov_tridiag_eigenvector(int32_t k, const double* alpha, const doub
   }
   return OV_OK;
 }
+
+// Eigenvalues and right eigenvectors of a small complex upper Hessenberg matrix (the
+// Arnoldi matrix of the shift-and-invert eigen-solver), on the host: the implicit
+// single-shift QR algorithm with Wilkinson shifts and exceptional shifts (Francis
+// 1961-62; Golub and Van Loan, "Matrix Computations", ch. 7.5) for the eigenvalues,
+// then inverse iteration on the original matrix with a pivoted LU for each
+// eigenvector.  O(m^3); meant for m up to a few hundred.
+namespace {
+
+using cmat = std::vector<cx>;   // row-major m x m
+
+bool hessenberg_qr(cmat t, int m, std::vector<cx>& eig) {
+  const double eps = 2.220446049250313e-16;
+  eig.assign(m, cx(0.0, 0.0));
+  auto at = [&](int i, int j) -> cx& { return t[(size_t)i * m + j]; };
+  int hi = m - 1, iter = 0, total = 0;
+  while (hi >= 0) {
+    if (hi == 0) {
+      eig[0] = at(0, 0);
+      break;
+    }
+    // the active block [lo, hi]: the first negligible subdiagonal above hi
+    int lo = hi;
+    while (lo > 0) {
+      const double s = std::abs(at(lo, lo)) + std::abs(at(lo - 1, lo - 1));
+      if (std::abs(at(lo, lo - 1)) <= eps * (s > 0.0 ? s : 1.0)) {
+        at(lo, lo - 1) = 0.0;
+        break;
+      }
+      --lo;
+    }
+    if (lo == hi) {
+      eig[hi] = at(hi, hi);
+      --hi;
+      iter = 0;
+      continue;
+    }
+    if (++total > 60 * m) return false;
+    // Wilkinson shift from the trailing 2 x 2 block; an exceptional shift every 10
+    cx sigma;
+    if (++iter % 10 == 0) {
+      sigma = at(hi, hi) + 0.75 * std::abs(at(hi, hi - 1));
+    } else {
+      const cx a = at(hi - 1, hi - 1), b = at(hi - 1, hi), c = at(hi, hi - 1), d = at(hi, hi);
+      const cx tr2 = 0.5 * (a + d), det = a * d - b * c;
+      const cx disc = std::sqrt(tr2 * tr2 - det);
+      const cx e1 = tr2 + disc, e2 = tr2 - disc;
+      sigma = std::abs(e1 - d) < std::abs(e2 - d) ? e1 : e2;
+    }
+    // implicit QR step on rows / columns lo..hi: the first rotation from the shifted
+    // first column, then the bulge chased down the subdiagonal
+    cx x = at(lo, lo) - sigma, y = at(lo + 1, lo);
+    for (int k = lo; k < hi; ++k) {
+      if (k > lo) {
+        x = at(k, k - 1);
+        y = at(k + 1, k - 1);
+      }
+      const double nr = std::sqrt(std::norm(x) + std::norm(y));
+      if (nr == 0.0) continue;
+      const cx cc = x / nr, ss = y / nr;   // G = [[conj c, conj s], [-s, c]] zeroes y
+      const int c0 = k > lo ? k - 1 : lo;
+      for (int j = c0; j <= hi; ++j) {     // rows k, k+1
+        const cx p = at(k, j), q = at(k + 1, j);
+        at(k, j) = std::conj(cc) * p + std::conj(ss) * q;
+        at(k + 1, j) = -ss * p + cc * q;
+      }
+      const int r1 = std::min(k + 2, hi);
+      for (int i = lo; i <= r1; ++i) {    // columns k, k+1 (G^dag from the right)
+        const cx p = at(i, k), q = at(i, k + 1);
+        at(i, k) = cc * p + ss * q;
+        at(i, k + 1) = -std::conj(ss) * p + std::conj(cc) * q;
+      }
+      if (k > lo) at(k + 1, k - 1) = 0.0;
+    }
+  }
+  return true;
+}
+
+// (A - mu) x = b by LU with partial pivoting (a zero pivot replaced by tiny)
+bool dense_shift_solve(const cmat& a, int m, cx mu, std::vector<cx>& b, double tiny) {
+  cmat w(a);
+  for (int i = 0; i < m; ++i) w[(size_t)i * m + i] -= mu;
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    for (int i = k + 1; i < m; ++i)
+      if (std::abs(w[(size_t)i * m + k]) > std::abs(w[(size_t)p * m + k])) p = i;
+    if (p != k) {
+      for (int j = 0; j < m; ++j) std::swap(w[(size_t)k * m + j], w[(size_t)p * m + j]);
+      std::swap(b[k], b[p]);
+    }
+    if (w[(size_t)k * m + k] == cx(0.0, 0.0)) w[(size_t)k * m + k] = tiny;
+    for (int i = k + 1; i < m; ++i) {
+      const cx f = w[(size_t)i * m + k] / w[(size_t)k * m + k];
+      if (f == cx(0.0, 0.0)) continue;
+      for (int j = k; j < m; ++j) w[(size_t)i * m + j] -= f * w[(size_t)k * m + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    cx s = b[i];
+    for (int j = i + 1; j < m; ++j) s -= w[(size_t)i * m + j] * b[j];
+    b[i] = s / w[(size_t)i * m + i];
+  }
+  for (const cx& v : b)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" int ov_hessenberg_eigen(int32_t m, const double* h, double* eig, double* vecs) {
+  if (m < 1 || m > 4096 || !h || !eig) return OV_ERR_INVALID_ARG;
+  cmat a((size_t)m * m);
+  double nrm = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    a[i] = cx(h[2 * i], h[2 * i + 1]);
+    if (!std::isfinite(h[2 * i]) || !std::isfinite(h[2 * i + 1])) return OV_ERR_NONFINITE;
+    nrm = std::max(nrm, std::abs(a[i]));
+  }
+  for (int i = 2; i < m; ++i)
+    for (int j = 0; j < i - 1; ++j)
+      if (a[(size_t)i * m + j] != cx(0.0, 0.0)) return OV_ERR_INVALID_ARG;   // not upper Hessenberg
+  std::vector<cx> ev;
+  if (!hessenberg_qr(a, m, ev)) return OV_ERR_NOCONV;
+  const double tiny = 2.220446049250313e-16 * (nrm > 0.0 ? nrm : 1.0);
+  for (int i = 0; i < m; ++i) {
+    eig[2 * i] = ev[i].real();
+    eig[2 * i + 1] = ev[i].imag();
+    if (!vecs) continue;
+    std::vector<cx> x(m, cx(1.0 / std::sqrt((double)m), 0.0));
+    for (int it = 0; it < 3; ++it) {
+      if (!dense_shift_solve(a, m, ev[i], x, tiny)) return OV_ERR_NOCONV;
+      double s = 0.0;
+      for (const cx& v : x) s += std::norm(v);
+      s = std::sqrt(s);
+      if (!(s > 0.0) || !std::isfinite(s)) return OV_ERR_NOCONV;
+      for (cx& v : x) v /= s;
+    }
+    for (int j = 0; j < m; ++j) {      // column i of vecs (row-major m x m)
+      vecs[2 * ((size_t)j * m + i)] = x[j].real();
+      vecs[2 * ((size_t)j * m + i) + 1] = x[j].imag();
+    }
+  }
+  return OV_OK;
+}

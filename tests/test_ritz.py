@@ -115,3 +115,30 @@ def test_tridiagonal_eigenvector_rejects_bad_arguments():
     a, b, d = _random_tsl_tridiag(4, np.random.default_rng(1))
     with pytest.raises(binding.OVError):
         binding.tridiag_eigenvector(a, b, d, np.nan)
+
+
+@pytest.mark.parametrize("m", [1, 2, 5, 40, 150])
+def test_hessenberg_eigen_matches_dense_eig(m):
+    """ov_hessenberg_eigen on random complex upper Hessenberg matrices: the spectrum
+    of LAPACK's zgeev and A y = mu y for every returned pair."""
+    rng = np.random.default_rng(900 + m)
+    a = np.triu(rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m)), -1)
+    eig, vec = binding.hessenberg_eigen(a)
+    want = np.linalg.eigvals(a)
+    assert _match(eig, want) <= 1e-10 * max(1.0, np.abs(want).max())
+    na = np.linalg.norm(a, 2)
+    for i in range(m):
+        assert abs(np.linalg.norm(vec[:, i]) - 1) <= 1e-12
+        assert np.linalg.norm(a @ vec[:, i] - eig[i] * vec[:, i]) <= 1e-9 * na
+
+
+def test_hessenberg_eigen_special_cases():
+    # diagonal (already deflated), a Jordan-like 2 x 2 block, and a rejected full matrix
+    d = np.diag([3.0 + 1j, -2.0, 0.5j])
+    eig = binding.hessenberg_eigen(d, vectors=False)
+    assert _match(eig, np.diag(d)) <= 1e-14
+    j = np.array([[1.0, 1.0], [1e-20, 1.0]], dtype=complex)
+    eig = binding.hessenberg_eigen(j, vectors=False)
+    assert np.allclose(eig, [1.0, 1.0], atol=1e-9)
+    with pytest.raises(binding.OVError):
+        binding.hessenberg_eigen(np.ones((4, 4)))
