@@ -308,6 +308,25 @@ int ov_tsl_ritz_triples(ov_context *ctx, const int32_t dims[4], const void *U, d
                         int32_t k, int32_t lmax, double tol, int32_t *l_out, double *lam, void *R, void *L,
                         double *resid);
 
+/* Eigen-triples of H(U, mu) smallest in |lambda|, for the deflation (the
+ * paper obtains them by ARPACK's Arnoldi): shift-and-invert Arnoldi, m steps on
+ * H^{-1} and m steps on H^{-dag} from the caller's start vector (device, one
+ * spinor field), each inversion by conjugate gradients on the normal
+ * equations to relative residual tol in at most maxit steps, classical
+ * Gram-Schmidt twice per step; the eigenpairs of each m x m Hessenberg matrix
+ * (ov_hessenberg_eigen) with the largest |mu| give lambda = 1/mu and the Ritz
+ * vectors.  Right and left are paired by eigenvalue (within 1e-6 |lambda|) and
+ * L scaled to L^dag R = 1.  Outputs up to l triples in order of |lambda|:
+ * l_out (host), lam (host double[2l]), R, L (device arrays of l spinor fields,
+ * complex128 user layout), resid (host double[l], may be NULL: ||H R -
+ * lambda R|| / ||R||).  FP64 whatever the context's precision.  Needs
+ * m >= l (m = 4l to 8l is typical), m <= 1024.  Returns OV_OK, OV_ERR_NOCONV
+ * (an inner solve missed tol; results still written), OV_ERR_INVALID_ARG,
+ * OV_ERR_NONFINITE. */
+int ov_eigen_smallest(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w, int32_t l,
+                      int32_t m, const void *start, double tol, int32_t maxit, int32_t *l_out, double *lam,
+                      void *R, void *L, double *resid);
+
 /* Eigenvalue and eigenvector derivatives for the generalised deflation (App.
  * B; computed, as App. E does, by shifted inversions), FP64 whatever the
  * context's precision: for the eigen-triples (lam, R, L) of H(U, mu) as in

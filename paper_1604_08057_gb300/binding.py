@@ -73,7 +73,7 @@ EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", 
            "ov_kk_gemm", "ov_tsl_sign_deflated", "ov_tsl_sign_jvp_deflated",
            "ov_tridiag_eigenvector", "ov_tsl_ritz_triples",
            "ov_eigen_derivatives",
-           "ov_hessenberg_eigen", "ov_strerror"]
+           "ov_hessenberg_eigen", "ov_eigen_smallest", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
     lib.ov_tridiag_eigenvalues.argtypes = [I32, P, P, P, P]
     lib.ov_tridiag_eigenvector.argtypes = [I32, P, P, P, P, I32, P]
     lib.ov_hessenberg_eigen.argtypes = [I32, P, P, P]
+    lib.ov_eigen_smallest.argtypes = [P, dims_t, P, D, D, I32, I32, P, D, I32, ctypes.POINTER(I32), P, P, P, P]
     lib.ov_tsl_ritz_triples.argtypes = [P, dims_t, P, D, D, I32, I32, I32, D, ctypes.POINTER(I32), P, P, P, P]
     lib.ov_eigen_derivatives.argtypes = [P, dims_t, P, D, D, P, D, I32, P, P, P, D, I32, P, P, P, P]
     lib.ov_overlap_apply.argtypes = [P, dims_t, P, D, D, I32, P, I32, I32, P, ctypes.POINTER(Info)]
@@ -505,6 +506,30 @@ def ritz_triples(u, mu, m_w, k, lmax, tol, src=0, precision="fp64", rebiorth=1, 
     _check(lib.ov_tsl_ritz_triples(ctx, dims, _ptr(u), float(mu), float(m_w), int(src), int(k), int(lmax),
                                    float(tol), ctypes.byref(nl), lam.ctypes.data, _ptr(R), _ptr(L),
                                    res.ctypes.data), "ov_tsl_ritz_triples")
+    n = nl.value
+    return lam[:n], R[:n], L[:n], res[:n]
+
+
+def eigen_smallest(u, mu, m_w, l, m, start, tol=1e-12, maxit=20000):
+    """(lam, R, L, residuals): up to l eigen-triples of H smallest in |lambda| by
+    shift-and-invert Arnoldi with m steps per side from the start field."""
+    lib = load()
+    dims = _dims(u)
+    u = u.contiguous()
+    st, single = _spinors(start, u)
+    if st.shape[0] != 1:
+        raise ValueError("one start field")
+    shape = (l,) + tuple(u.shape[:4]) + (4, 3)
+    R = torch.empty(shape, dtype=torch.complex128, device=u.device)
+    L = torch.empty_like(R)
+    lam = np.zeros(l, dtype=np.complex128)
+    res = np.zeros(l, dtype=np.float64)
+    nl = ctypes.c_int32(0)
+    ctx = context("fp64", 1, 2)
+    code = lib.ov_eigen_smallest(ctx, dims, _ptr(u), float(mu), float(m_w), int(l), int(m), _ptr(st), float(tol),
+                                 int(maxit), ctypes.byref(nl), lam.ctypes.data, _ptr(R), _ptr(L), res.ctypes.data)
+    if code not in (0, -9):
+        _check(code, "ov_eigen_smallest")
     n = nl.value
     return lam[:n], R[:n], L[:n], res[:n]
 

@@ -22,7 +22,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, B_EDT1, B_EDT2, B_EDX, B_EDC, B_CGY, B_CGR, B_CGP, B_CGQ, B_CGT, B_CGC, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, B_EDT1, B_EDT2, B_EDX, B_EDC, B_CGY, B_CGR, B_CGP, B_CGQ, B_CGT, B_CGC, B_SIQ, B_SILT, B_SIT1, B_SIC, B_SIP, NBUF
 };
 
 struct Status {
@@ -1931,6 +1931,152 @@ int eigderiv_impl(ov_context* c, const int32_t dims[4], const void* U, double mu
   return worst;
 }
 
+// Eigen-triples of H(U, mu) smallest in |lambda| by shift-and-invert Arnoldi (the
+// role ARPACK plays in the paper, Sec. 3, 4.1): m Arnoldi steps on H^{-1} (right) and
+// on H^{-dag} (left) from the caller's start vector, each inversion by
+// cg_normal_solve, classical Gram-Schmidt twice; the m x m Hessenberg matrices'
+// eigenpairs (ov_hessenberg_eigen) with the largest |mu| give lambda = 1/mu and the
+// Ritz vectors; left and right are paired by eigenvalue, scaled to L^dag R = 1, and
+// the residual ||H R - lambda R|| / ||R|| is reported.  FP64.
+int eigsmall_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int l, int m,
+                  const void* start, double tol, int maxit, int32_t* l_out, double* lam, void* Rf, void* Lf,
+                  double* resid) {
+  check_ptr(start);
+  check_ptr(Rf);
+  check_ptr(Lf);
+  if (!(tol > 0.0) || maxit < 1 || m < l || m > 1024) throw Status{OV_ERR_INVALID_ARG};
+  Lat<double> L1 = setup<double>(c, dims, U, mu, m_w, 1, 2, false);
+  const int64_t V = L1.g.V, n = 12 * V, fd = 24 * V;
+  double* Q = wsT<double>(c, B_SIQ, (int64_t)(m + 1) * fd);
+  double* lt = wsT<double>(c, B_SILT, (int64_t)l * fd);
+  double* t1 = wsT<double>(c, B_SIT1, fd);
+  zd* cd = wsT<zd>(c, B_SIC, (int64_t)m + 8);          // [0, m) coefficients, [m] a dot
+  zd* dots = cd + m;
+  zd* part = wsT<zd>(c, B_SIP, 152 * (int64_t)(m + 1)); // partial sums of vec_dots (152 per vector)
+  auto opH = [&](const double* in, double* out, int dagger) {
+    run(c, OV_KIND_LAYOUT, 1, [&] { pack_spinors<double>(in, L1.r, 1, V, L1.vs, c->st); });
+    run(c, OV_KIND_APPLY_H, 1, [&] { apply_h(L1, L1.r, L1.p, dagger, c->st, 0, nullptr); });
+    run(c, OV_KIND_LAYOUT, 1, [&] { unpack_spinors<double>(L1.p, out, 1, V, L1.vs, c->st); });
+  };
+  auto dot = [&](const double* a, const double* b) {
+    run(c, OV_KIND_COMBINE, 2, [&] { vec_dots(a, fd, 1, b, n, dots, part, c->st); });
+    zd h;
+    CK(cudaMemcpyAsync(&h, dots, sizeof(zd), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return std::complex<double>(h.re, h.im);
+  };
+  std::vector<std::complex<double>> lamr, laml;
+  std::vector<int> keep_r;
+  double* Rb = static_cast<double*>(Rf);
+  double* Lb = static_cast<double*>(Lf);
+  int worst = OV_OK;
+  for (int side = 0; side < 2; ++side) {
+    const int dg = side;   // A = H (right) or H^dag (left)
+    const double s0 = std::sqrt(dot(static_cast<const double*>(start), static_cast<const double*>(start)).real());
+    if (!(s0 > 0.0) || !std::isfinite(s0)) throw Status{OV_ERR_INVALID_ARG};
+    run(c, OV_KIND_COMBINE, 1,
+        [&] { vec_scale(static_cast<const double*>(start), Q, 1.0 / s0, 0.0, n, c->st); });
+    std::vector<std::complex<double>> hm((size_t)(m + 1) * m, 0.0);
+    int mm = m;
+    for (int j = 0; j < m; ++j) {
+      double* w = Q + (int64_t)(j + 1) * fd;
+      int it = 0;
+      double rr = 0.0;
+      const int st = cg_normal_solve(
+          c, n, Q + (int64_t)j * fd, w, tol, maxit, [&](const double* in, double* out) { opH(in, out, dg); },
+          [&](const double* in, double* out) { opH(in, out, 1 - dg); }, &it, &rr);
+      if (st != OV_OK && st != OV_ERR_NOCONV) return st;
+      if (st == OV_ERR_NOCONV) worst = st;
+      for (int pass = 0; pass < 2; ++pass) {
+        run(c, OV_KIND_COMBINE, 3, [&] {
+          vec_dots(Q, fd, j + 1, w, n, cd, part, c->st);
+          vec_update(w, Q, fd, j + 1, cd, -1.0, n, c->st);
+        });
+        std::vector<zd> hh(j + 1);
+        CK(cudaMemcpyAsync(hh.data(), cd, sizeof(zd) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int i = 0; i <= j; ++i) hm[(size_t)i * m + j] += std::complex<double>(hh[i].re, hh[i].im);
+      }
+      const double hn = std::sqrt(dot(w, w).real());
+      if (!std::isfinite(hn)) return OV_ERR_NONFINITE;
+      hm[(size_t)(j + 1) * m + j] = hn;
+      if (!(hn > 1e-14 * std::abs(hm[(size_t)j * m + j]))) {   // an invariant subspace: stop here
+        mm = j + 1;
+        break;
+      }
+      run(c, OV_KIND_COMBINE, 1, [&] { vec_scale(w, w, 1.0 / hn, 0.0, n, c->st); });
+    }
+    // eigenpairs of the leading mm x mm Hessenberg block
+    std::vector<double> hv(2 * (size_t)mm * mm), ev(2 * (size_t)mm), vv(2 * (size_t)mm * mm);
+    for (int i = 0; i < mm; ++i)
+      for (int jj = 0; jj < mm; ++jj) {
+        hv[2 * ((size_t)i * mm + jj)] = hm[(size_t)i * m + jj].real();
+        hv[2 * ((size_t)i * mm + jj) + 1] = hm[(size_t)i * m + jj].imag();
+      }
+    const int st = ov_hessenberg_eigen(mm, hv.data(), ev.data(), vv.data());
+    if (st != OV_OK) return st;
+    std::vector<int> order(mm);
+    for (int i = 0; i < mm; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return std::hypot(ev[2 * a], ev[2 * a + 1]) > std::hypot(ev[2 * b], ev[2 * b + 1]);
+    });
+    const int take = std::min(l, mm);
+    std::vector<std::complex<double>>& lamv = side ? laml : lamr;
+    for (int q = 0; q < take; ++q) {
+      const int i = order[q];
+      const std::complex<double> muv(ev[2 * i], ev[2 * i + 1]);
+      if (std::abs(muv) == 0.0) break;
+      lamv.push_back(side ? std::conj(1.0 / muv) : 1.0 / muv);   // an eigenvalue of H either way
+      std::vector<zd> y(mm);
+      for (int jj = 0; jj < mm; ++jj) y[jj] = mk(vv[2 * ((size_t)jj * mm + i)], vv[2 * ((size_t)jj * mm + i) + 1]);
+      CK(cudaMemcpyAsync(cd, y.data(), sizeof(zd) * mm, cudaMemcpyHostToDevice, c->st));
+      double* out = (side ? lt : Rb) + (int64_t)q * fd;
+      CK(cudaMemsetAsync(out, 0, sizeof(double) * fd, c->st));
+      run(c, OV_KIND_COMBINE, 1, [&] { vec_update(out, Q, fd, mm, cd, 1.0, n, c->st); });
+    }
+  }
+  // pair every right eigenvalue with the nearest left one; scale L to L^dag R = 1
+  int got = 0;
+  std::vector<char> used(laml.size(), 0);
+  for (size_t i = 0; i < lamr.size(); ++i) {
+    int best = -1;
+    double bd = INFINITY;
+    for (size_t j = 0; j < laml.size(); ++j) {
+      if (used[j]) continue;
+      const double d = std::abs(laml[j] - lamr[i]);
+      if (d < bd) {
+        bd = d;
+        best = (int)j;
+      }
+    }
+    if (best < 0 || !(bd <= 1e-6 * std::abs(lamr[i]) + 1e-12)) continue;
+    used[best] = 1;
+    double* ro = Rb + (int64_t)got * fd;
+    double* lo = Lb + (int64_t)got * fd;
+    if ((int64_t)got != (int64_t)i)
+      CK(cudaMemcpyAsync(ro, Rb + (int64_t)i * fd, sizeof(double) * fd, cudaMemcpyDeviceToDevice, c->st));
+    const std::complex<double> sdot = dot(lt + (int64_t)best * fd, ro);   // L^dag R
+    if (std::abs(sdot) < 1e-12) continue;
+    const std::complex<double> f = 1.0 / std::conj(sdot);
+    run(c, OV_KIND_COMBINE, 1,
+        [&] { vec_scale(lt + (int64_t)best * fd, lo, f.real(), f.imag(), n, c->st); });
+    // residual ||H R - lambda R|| / ||R||
+    opH(ro, t1, 0);
+    const zd ml = mk(-lamr[i].real(), -lamr[i].imag());
+    CK(cudaMemcpyAsync(cd, &ml, sizeof(zd), cudaMemcpyHostToDevice, c->st));
+    run(c, OV_KIND_COMBINE, 1, [&] { vec_update(t1, ro, fd, 1, cd, 1.0, n, c->st); });
+    const double rn = std::sqrt(dot(t1, t1).real() / dot(ro, ro).real());
+    lam[2 * got] = lamr[i].real();
+    lam[2 * got + 1] = lamr[i].imag();
+    if (resid) resid[got] = rn;
+    ++got;
+  }
+  *l_out = got;
+  launch_check();
+  CK(cudaStreamSynchronize(c->st));
+  return worst;
+}
+
 template <typename R>
 int overlap_solve_impl(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
                        const void* rhs, int k, int dagger, double tol, int maxit, void* x, int32_t* iters,
@@ -2369,6 +2515,16 @@ int ov_eigen_derivatives(ov_context* c, const int32_t dims[4], const void* U, do
   if (!c || !dims || l < 1 || l > 4096 || !lam || !dlam) return OV_ERR_INVALID_ARG;
   return guarded([&] {
     return eigderiv_impl(c, dims, U, mu, m_w, E, m_dir, l, lam, R, L, tol, maxit, dlam, dR, dL, resid);
+  });
+}
+
+int ov_eigen_smallest(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int32_t l,
+                      int32_t m, const void* start, double tol, int32_t maxit, int32_t* l_out, double* lam, void* R,
+                      void* L, double* resid) {
+  if (!c || !dims || !l_out || !lam || l < 1 || l > 1024 || m < l || m > 1024) return OV_ERR_INVALID_ARG;
+  *l_out = 0;
+  return guarded([&] {
+    return eigsmall_impl(c, dims, U, mu, m_w, l, m, start, tol, maxit, l_out, lam, R, L, resid);
   });
 }
 

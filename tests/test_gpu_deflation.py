@@ -176,3 +176,28 @@ def test_generalised_deflation_with_gpu_eigen_derivatives():
                                                      d["dR"][sel], d["dL"][sel])
         assert rel(x[s], x_o) <= 1e-9
         assert rel(dx[s], dx_o) <= 1e-7
+
+
+def test_shift_invert_arnoldi_finds_the_smallest_eigen_triples():
+    """ov_eigen_smallest on 2^4 at m_w = -2 (n = 192): the 8 eigenvalues smallest in
+    |lambda| of the dense eigendecomposition, their spectral projectors, small
+    residuals, and a deflated TSL with them equal to one with the exact triples."""
+    u, b, e, mu, m_w = lattice_case(16)
+    rng = np.random.default_rng(61)
+    start = inputs.gaussian_spinors((2, 2, 2, 2), 1, rng)[0]
+    lam, R, L, res = binding.eigen_smallest(T(u), mu, m_w, 8, 64, T(start))
+    assert len(lam) == 8 and np.all(res <= 1e-8), res
+    lam_all, r, l_ = deflation.eigentriples(overlap.dense_h(u, mu, m_w))
+    assert np.allclose(np.sort(np.abs(lam)), np.abs(lam_all[:8]), rtol=1e-9)
+    probe = rng.standard_normal(192) + 1j * rng.standard_normal(192)
+    Rn, Ln = R.cpu().numpy(), L.cpu().numpy()
+    for i in range(8):
+        j = int(np.argmin(np.abs(lam_all - lam[i])))
+        assert abs(lam_all[j] - lam[i]) <= 1e-9 * abs(lam_all[j])
+        p_gpu = Rn[i].ravel() * np.vdot(Ln[i].ravel(), probe)
+        p_ex = r[:, j] * np.vdot(l_[:, j], probe)
+        assert rel(p_gpu, p_ex) <= 1e-6
+    d = deflation.lattice_eigendata(u, mu, m_w, 8)
+    x_gpu_triples = binding.tsl_sign_deflated(T(u), mu, m_w, T(b), 40, lam, R, L).cpu().numpy()
+    x_exact_triples = binding.tsl_sign_deflated(T(u), mu, m_w, T(b), 40, d["lam"], T(d["R"]), T(d["L"])).cpu().numpy()
+    assert rel(x_gpu_triples, x_exact_triples) <= 1e-7
