@@ -63,7 +63,7 @@ def parse_args():
                     help="two-pass TSL with checkpoints every S steps (needs --rebiorth 0)")
     ap.add_argument("--m-w", type=float, default=None, help="override the workload's Wilson mass")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
-    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch", "kk", "deflation"],
+    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch", "kk", "deflation", "deflation8"],
                     help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling); "
                          "batch: the uneven batch of 32 problems (forward + VJP) through ov_tsl_batch; "
                          "kk: one k x k complex product (ov_kk_gemm), FP64 and split, at the workload's k")
@@ -536,6 +536,49 @@ def deflation_leg(dev_index, dims=(3, 3, 3, 3), mu=0.3, m_w=-2.0, l=40, ks=(40, 
     return out
 
 
+def deflation_scale_leg(dev_index, l=30, m=90, ks=(100, 200, 400)):
+    """Deflation at the 8x8^3 workload (n = 49152, the lattice size of the paper's
+    Sec. 4 test, 30 deflated eigenvalues there too), where no dense reference
+    exists: the 30 eigen-triples smallest in |lambda| by shift-and-invert Arnoldi
+    (ov_eigen_smallest, m steps per side), then per k the a-posteriori error
+    eps = ||sgn(H)^2 b - b|| / (2 ||b||) (Eq. error_est) of the plain and of the
+    deflated TSL, and the seconds per sgn(H) b of each."""
+    import numpy as np
+    import torch
+    from paper_1604_08057_gb300 import binding
+    dev = torch.device("cuda", dev_index)
+    wl = inputs.WORKLOADS["8x8^3"]
+    u, b, _ = inputs.make_inputs(wl, nsrc=1)
+    ut, bt = torch.tensor(u, device=dev), torch.tensor(b[0], device=dev)
+    start = torch.tensor(inputs.gaussian_spinors(wl.dims, 1, np.random.default_rng(71))[0], device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, R, L, res = binding.eigen_smallest(ut, wl.mu, wl.m_w, l, m, start, tol=1e-10)
+    torch.cuda.synchronize()
+    out = {"lattice": "8x8^3", "n": 12 * wl.volume, "requested": l, "arnoldi_steps_per_side": m,
+           "found": int(len(lam)), "eigen_s": round(time.perf_counter() - t0, 2),
+           "max_residual": float(res.max()) if len(res) else None,
+           "abs_lambda_range": [float(np.abs(lam).min()), float(np.abs(lam).max())] if len(lam) else None,
+           "per_k": {}}
+    bn = float(torch.linalg.vector_norm(bt))
+    for k in ks:
+        row = {}
+        for name in ("plain", "deflated"):
+            def sgn(v):
+                if name == "plain":
+                    return binding.tsl_sign(ut, wl.mu, wl.m_w, v, k)
+                return binding.tsl_sign_deflated(ut, wl.mu, wl.m_w, v, k, lam, R, L)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            x = sgn(bt)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t1
+            x2 = sgn(x)
+            row[name] = {"eps": float(torch.linalg.vector_norm(x2 - bt)) / (2 * bn), "s_per_call": round(dt, 4)}
+        out["per_k"][str(k)] = row
+    return out
+
+
 def kk_leg(args, dev_index, reps=5):
     """One complex k x k product C = A^H B of the Frechet adjoint's kind through
     ov_kk_gemm, in FP64 arithmetic and by the tensor-core digit splitting: ms per
@@ -924,6 +967,11 @@ def main():
         print(json.dumps({"leg": "uneven_batch", "precision": args.precision, "rebiorth_period": args.rebiorth,
                           "segment": args.segment,
                           "gs_passes": args.passes, **batch_leg(args)}))
+        return
+    if args.leg == "deflation8":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"leg": "deflation_8x8^3", **deflation_scale_leg(local_rank)}))
         return
     if args.leg == "deflation":
         import torch
