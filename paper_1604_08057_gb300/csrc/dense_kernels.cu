@@ -901,11 +901,16 @@ __global__ void __launch_bounds__(256) k_newton_combine(const zd* __restrict__ x
   block_sum<1>(v, scratch);
   if (threadIdx.x == 0) part[blockIdx.x] = v[0];
   if (arrive_last(cnt, gridDim.x)) {
+    // the last block sums the partials: thread t takes blocks t, t + 256, ... in
+    // order, then the fixed tree of block_sum (the same order on every run; one
+    // thread alone would be a chain of k^2 / 256 dependent FP64 additions)
     zd t = mk(0.0, 0.0);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) t = t + ld_cg(part + b);
+    zd tv[1] = {t};
+    block_sum<1>(tv, scratch);
     if (threadIdx.x == 0) {
-      for (unsigned b = 0; b < gridDim.x; ++b) t = t + ld_cg(part + b);
-      stats[0] += w * t.re;
-      stats[1] += w * t.im;
+      stats[0] += w * tv[0].re;
+      stats[1] += w * tv[0].im;
     }
   }
 }
