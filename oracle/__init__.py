@@ -20,6 +20,8 @@ ksign   k x k matrix sign by scaled Newton iteration and its Frechet adjoint by
 tsl     Two-sided Lanczos approximation x ~ sgn(H) b (Sec. 1 and 2, the TSL of
         Bloch et al.), with optional re-biorthogonalisation.
 vjp     Reverse-mode derivative of the TSL map with respect to all links and mu.
+nested  Nested Krylov approximation of the k x k sign, one nesting level
+        (Sec. 4.1): Arnoldi on S = (T_k + T_k^{-1})/2 from e_1.
 
 Pins: every function is checked in ``tests/test_oracle_*.py`` against facts
 that do not come from the oracle itself (closed forms in momentum space,
@@ -27,4 +29,4 @@ eigendecomposition sign, sgn^2 = 1, gamma5-hermiticity, gauge covariance,
 Daleckii-Krein, central finite differences, autograd through a dense
 restatement).
 """
-from . import dirac, ksign, tsl, vjp  # noqa: F401
+from . import dirac, ksign, nested, tsl, vjp  # noqa: F401
