@@ -63,10 +63,13 @@ def parse_args():
                     help="two-pass TSL with checkpoints every S steps (needs --rebiorth 0)")
     ap.add_argument("--m-w", type=float, default=None, help="override the workload's Wilson mass")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, stencil, FP64 and CPU legs")
-    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch", "kk", "deflation", "deflation8"],
+    ap.add_argument("--leg", default="all", choices=["all", "stencil", "batch", "kk", "deflation", "deflation8",
+                                                     "nested", "nested_stage"],
                     help="stencil: only the multi-source Wilson-Dirac leg (for kernel profiling); "
                          "batch: the uneven batch of 32 problems (forward + VJP) through ov_tsl_batch; "
-                         "kk: one k x k complex product (ov_kk_gemm), FP64 and split, at the workload's k")
+                         "kk: one k x k complex product (ov_kk_gemm), FP64 and split, at the workload's k; "
+                         "nested: the nested TSL's k x k stage against the full sign at the workload; "
+                         "nested_stage: that stage alone on a synthetic tridiagonal of the workload's k")
     args = ap.parse_args()
     # P = 60 at 14x14^3, k = 800: x within 1e-9 and dU within 1e-4 of the P = 1 result
     # (P = 20: 2e-10 and 4e-4), the same eps_A; the uneven batch keeps P = 20
@@ -351,6 +354,10 @@ def run_ours(args, rank, world, local_rank):
         out["diagnostics"] = diagnostics_leg(args, ut, bt, xt, wl, k, ms_total / args.steps)
         out["kk_products"] = kk_products_leg(args, ut, bt, xt, wl, k, du, dmu, x, ms_total / args.steps)
         try:
+            out["nested_tsl"] = nested_leg(args, ut, bt, wl, k)
+        except Exception as exc:   # reported, not fatal: the leg is beside the headline
+            out["nested_tsl"] = {"error": str(exc)}
+        try:
             out["deflation"] = deflation_leg(ut.device.index)
         except Exception as exc:   # reported, not fatal: the leg is beside the headline
             out["deflation"] = {"error": str(exc)}
@@ -409,6 +416,74 @@ def forward_leg(args, ut, bt, wl, k, reps=2):
     torch.cuda.synchronize()
     return {"value": round(e0.elapsed_time(e1) / 1e3 / reps, 6), "unit": "s per sgn(H)b", "steps": reps,
             "newton_iters": info["newton_iters"]}
+
+
+def nested_leg(args, ut, bt, wl, k, inner=(60, 100, 150), reps=2):
+    """The k x k stage of sgn(H) b by the nested TSL (Sec. 4.1: one nesting level,
+    inner Krylov size m) against the full Newton sign of T_k, at this workload and
+    schedule: seconds per ov_tsl_sign call and its k x k phase (device events), the
+    relative difference of x from the full-sign x, eps_A (Eq. error_est) with and
+    without nesting, and the k x k stage alone on the call's own T_k
+    (ov_tridiag_sign_nested; host-timed, including the T_k upload and y download)."""
+    import time
+    import torch
+    from paper_1604_08057_gb300 import binding
+    opts = (args.precision, args.rebiorth, args.passes)
+
+    def call(m):
+        binding.nested_sign(m, *opts)
+        binding.tsl_sign(ut, wl.mu, wl.m_w, bt, k, *opts)        # warm-up: capture, workspace
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            x, info = binding.tsl_sign(ut, wl.mu, wl.m_w, bt, k, *opts, return_info=True)
+        e1.record()
+        torch.cuda.synchronize()
+        return x, {"s_per_call": round(e0.elapsed_time(e1) / 1e3 / reps, 4), "kk_ms": round(info["t_ms"][1], 3),
+                   "newton_iters": info["newton_iters"]}
+
+    def stage(a, b, d, m, n=3):
+        binding.tridiag_sign_nested(a, b, d, m)
+        t0 = time.perf_counter()
+        for _ in range(n):
+            y, _ = binding.tridiag_sign_nested(a, b, d, m)
+        return y, round((time.perf_counter() - t0) / n * 1e3, 3)
+
+    out = {"inner_sizes": list(inner), "reps": reps}
+    try:
+        x0, out["full"] = call(0)
+        a, b, d = binding.tsl_coefficients(k, 0, *opts)
+        y0, out["full"]["stage_ms"] = stage(a, b, d, 0)
+        out["full"]["eps_a"] = float(binding.tsl_eps(ut, wl.mu, wl.m_w, bt, k, *opts)[0])
+        for m in inner:
+            x, r = call(m)
+            r["rel_diff_x_vs_full"] = float((x - x0).norm() / x0.norm())
+            y, r["stage_ms"] = stage(a, b, d, m)
+            r["stage_rel_diff_y_vs_full"] = float(abs(y - y0).max() / abs(y0).max())
+            if m == 100:
+                r["eps_a"] = float(binding.tsl_eps(ut, wl.mu, wl.m_w, bt, k, *opts)[0])
+            out[f"m{m}"] = r
+    finally:
+        binding.nested_sign(0, *opts)
+    return out
+
+
+def nested_stage_leg(k, inner=(60, 100, 150), reps=5, seed=11):
+    """The k x k stage alone on a seeded synthetic tridiagonal of size k (no lattice):
+    ms per ov_tridiag_sign_nested call for the full Newton sign (m = 0) and the nested
+    form (host-timed, including the upload of T and the download of y)."""
+    import time
+    from paper_1604_08057_gb300 import binding
+    a, b, d = inputs.tridiagonal_coefficients(k, np.random.default_rng(seed))
+    out = {"k": k, "reps": reps}
+    for m in (0,) + tuple(inner):
+        binding.tridiag_sign_nested(a, b, d, m)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            _, it = binding.tridiag_sign_nested(a, b, d, m)
+        out[f"m{m}"] = {"ms": round((time.perf_counter() - t0) / reps * 1e3, 3), "newton_iters": it}
+    return out
 
 
 def schedule_leg(args, ut, bt, xt, wl, k, du, dmu, x, periods=(20,)):
@@ -982,6 +1057,22 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         print(json.dumps(kk_leg(args, local_rank)))
+        return
+    if args.leg == "nested_stage":
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"leg": "nested_stage", **nested_stage_leg(args.k or workload_of(args).k)}))
+        return
+    if args.leg == "nested":
+        import torch
+        torch.cuda.set_device(local_rank)
+        wl = workload_of(args)
+        k = args.k or wl.k
+        u, b, _ = inputs.make_inputs(wl)
+        dev = f"cuda:{local_rank}"
+        print(json.dumps({"leg": "nested_tsl", "workload": f"{args.workload}, k={k}, mu={wl.mu}, m_w={wl.m_w}",
+                          "rebiorth_period": args.rebiorth, "gs_passes": args.passes,
+                          **nested_leg(args, torch.tensor(u, device=dev), torch.tensor(b, device=dev), wl, k)}))
         return
     if args.leg == "stencil":
         import torch

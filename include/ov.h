@@ -120,7 +120,23 @@ typedef struct {
                         * else FP64 arithmetic; 1: FP64 arithmetic always; 2: the tensor-core
                         * form wherever k <= 1024.  Needs ~930 k^2 bytes of device workspace
                         * (0.6 GB at k = 800). */
+  int32_t nested;      /* k x k sign of the forward passes (ov_tsl_sign and everything built on it:
+                        * ov_tsl_eps, ov_overlap_apply, ov_overlap_solve, the deflated forms; the
+                        * block TSL of ov_block_tsl_sign / ov_tsl_sign_jvp / ov_block_tsl_eps):
+                        * 0 (default) sgn(T_k) e_1 by the scaled Newton iteration on T_k;
+                        * m in 1..OV_NESTED_MAX: the nested TSL with one nesting level and inner
+                        * Krylov size m (Sec. 4.1, inner size 100 there), sgn(T_k) e_1 ~
+                        * Q_m sgn(H_m) e_1 from m Arnoldi steps on S = (T_k + T_k^{-1})/2 started
+                        * at e_1 (sgn(S) = sgn(T_k): z -> (z + 1/z)/2 keeps the sign of Re z), see
+                        * ov_tridiag_sign_nested.  O(k^2 m) work instead of O(k^3) per Newton
+                        * iteration; an approximation of the full result whose error falls with m.
+                        * The reverse mode (ov_tsl_sign_vjp, ov_tsl_sign_fwd, ov_tsl_batch,
+                        * ov_u1_current) differentiates the full k x k sign and returns
+                        * OV_ERR_INVALID_ARG while nested > 0.  Needs 16 k^2 bytes of device
+                        * workspace per source for S. */
 } ov_options;
+
+#define OV_NESTED_MAX 1024   /* largest inner Krylov size of options.nested */
 
 typedef struct {
   int32_t k_reached;        /* Lanczos steps completed */
@@ -494,6 +510,27 @@ int ov_overlap_solve(ov_context *ctx, const int32_t dims[4], const void *U, doub
 int ov_u1_current(ov_context *ctx, const int32_t dims[4], const void *U, double mu, double m_w, int32_t nnoise,
                   const void *eta, int32_t k, double tol, int32_t maxit, void *j, double *trace_mu,
                   ov_tsl_info *info);
+
+/* The k x k stage of the TSL on one tridiagonal T, on the device: y = beta0 f,
+ * with f = sgn(T) e_1 by the scaled Newton iteration on T when m = 0 (the
+ * stage of ov_tsl_sign without nesting), or, for m > 0, the nested
+ * approximation of Sec. 4.1 (one nesting level, inner Krylov size m):
+ *   S = (T + T^{-1})/2 (dense; T^{-1} from an LU of T with partial pivoting),
+ *   m steps of Arnoldi on S from e_1 (classical Gram-Schmidt twice),
+ *   S Q_m = Q_m H_m + h q e_m^T,  f = Q_m sgn(H_m) e_1,
+ * sgn(H_m) by the same Newton iteration; m >= k, or a Krylov space of S that
+ * closes early (a residual <= 1e-14 ||S q_j||), gives f = sgn(T) e_1 up to
+ * rounding.  Host arrays as ov_tsl_coefficients writes them: alpha[2k],
+ * beta[2k] interleaved complex (alpha_j = T[j][j], beta_j = T[j-1][j],
+ * beta_0 unused), delta[k] (delta_j = T[j][j-1], delta_0 unused); y (host
+ * double[2k], interleaved complex); newton_iters (may be NULL) receives the
+ * Newton iteration count.  Uses the context's workspace and stream (options
+ * other than newton and dense do not apply).  2 <= k <= 4096,
+ * 0 <= m <= OV_NESTED_MAX.  Returns OV_OK, OV_ERR_INVALID_ARG,
+ * OV_ERR_SIGN_ILLPOSED (T singular, a non-finite entry, or the Newton
+ * iteration failed), OV_ERR_OOM, OV_ERR_CUDA. */
+int ov_tridiag_sign_nested(ov_context *ctx, int32_t k, const double *alpha, const double *beta,
+                           const double *delta, int32_t m, double beta0, double *y, int32_t *newton_iters);
 
 /* Eigenvalues of one TSL tridiagonal T_k (the Ritz values), on the host: no
  * GPU and no context needed.  Host arrays as ov_tsl_coefficients writes them:

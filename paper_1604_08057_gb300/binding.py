@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rebiorth", ctypes.c_int32),
                 ("passes", ctypes.c_int32), ("segment", ctypes.c_int32), ("dense", ctypes.c_int32),
                 ("diagnostics", ctypes.c_int32), ("newton", ctypes.c_int32),
-                ("basis_memory", ctypes.c_int32), ("graphs", ctypes.c_int32), ("gemm", ctypes.c_int32)]
+                ("basis_memory", ctypes.c_int32), ("graphs", ctypes.c_int32), ("gemm", ctypes.c_int32),
+                ("nested", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -73,7 +74,7 @@ EXPORTS = ["ov_context_create", "ov_context_destroy", "ov_context_set_options", 
            "ov_kk_gemm", "ov_tsl_sign_deflated", "ov_tsl_sign_jvp_deflated",
            "ov_tridiag_eigenvector", "ov_tsl_ritz_triples",
            "ov_eigen_derivatives",
-           "ov_hessenberg_eigen", "ov_eigen_smallest", "ov_strerror"]
+           "ov_hessenberg_eigen", "ov_eigen_smallest", "ov_tridiag_sign_nested", "ov_strerror"]
 
 KINDS = ["stencil_pair", "update", "proj_dots", "proj_update", "combine", "dense", "rev_scalar",
          "rev_stencil", "force", "apply_h", "layout", "dense_gemm"]
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
     lib.ov_autotune.argtypes = [P, dims_t, P, D, D, I32, ctypes.POINTER(TuneReport)]
     lib.ov_set_stencil_variants.argtypes = [P, I32, I32]
     lib.ov_tridiag_eigenvalues.argtypes = [I32, P, P, P, P]
+    lib.ov_tridiag_sign_nested.argtypes = [P, I32, P, P, P, I32, D, P, ctypes.POINTER(I32)]
     lib.ov_tridiag_eigenvector.argtypes = [I32, P, P, P, P, I32, P]
     lib.ov_hessenberg_eigen.argtypes = [I32, P, P, P]
     lib.ov_eigen_smallest.argtypes = [P, dims_t, P, D, D, I32, I32, P, D, I32, ctypes.POINTER(I32), P, P, P, P]
@@ -164,10 +166,10 @@ def _set_extra(precision, rebiorth, passes, segment, **kw):
     ctx = context(precision, rebiorth, passes, segment=segment)
     key = (precision, rebiorth, passes, segment, ctx.value)
     ex = _extra.setdefault(key, {"dense": 0, "diagnostics": 0, "newton": 0, "basis_memory": 0, "graphs": 1,
-                                 "gemm": 0})
+                                 "gemm": 0, "nested": 0})
     ex.update({k: int(v) for k, v in kw.items()})
     opt = Options(_PREC[precision], rebiorth, passes, segment, ex["dense"], ex["diagnostics"], ex["newton"],
-                  ex["basis_memory"], ex["graphs"], ex["gemm"])
+                  ex["basis_memory"], ex["graphs"], ex["gemm"], ex["nested"])
     _check(load().ov_context_set_options(ctx, ctypes.byref(opt)), "ov_context_set_options")
     return ctx
 
@@ -208,6 +210,13 @@ def kk_products(mode: str, precision: str = "fp64", rebiorth: int = 1, passes: i
     "auto" (default: BF16 tensor cores by exact digit splitting for 128 <= k <= 1024,
     else FP64), "fp64", or "split" (the tensor-core form wherever k <= 1024)."""
     _set_extra(precision, rebiorth, passes, segment, gemm={"auto": 0, "fp64": 1, "split": 2}[mode])
+
+
+def nested_sign(m: int, precision: str = "fp64", rebiorth: int = 1, passes: int = 2, segment: int = 0):
+    """k x k sign of the forward passes on the cached context: 0 (default) the full
+    Newton sign of T_k, m > 0 the nested TSL with inner Krylov size m (one nesting level:
+    Arnoldi on (T_k + T_k^-1)/2 from e_1).  The reverse mode refuses nested > 0."""
+    _set_extra(precision, rebiorth, passes, segment, nested=int(m))
 
 
 def debug_inject(kind: str, step: int = 0, precision: str = "fp64", rebiorth: int = 1, passes: int = 2,
@@ -280,6 +289,25 @@ def tridiag_eigenvalues(alpha, beta, delta):
     _check(load().ov_tridiag_eigenvalues(k, a.ctypes.data, b.ctypes.data, d.ctypes.data, out.ctypes.data),
            "ov_tridiag_eigenvalues")
     return out
+
+
+def tridiag_sign_nested(alpha, beta, delta, m, beta0=1.0, device=None):
+    """beta0 sgn(T) e_1 for the TSL tridiagonal (host numpy arrays as tsl_coefficients
+    returns them) on the device: m = 0 the full Newton sign, m > 0 the nested
+    approximation with inner Krylov size m.  Returns (y, newton_iters)."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(alpha, dtype=np.complex128))
+    b = np.ascontiguousarray(np.asarray(beta, dtype=np.complex128))
+    d = np.ascontiguousarray(np.asarray(delta, dtype=np.float64))
+    k = a.shape[0]
+    if b.shape != (k,) or d.shape != (k,):
+        raise ValueError("alpha, beta, delta must have length k")
+    y = np.empty(k, dtype=np.complex128)
+    it = ctypes.c_int32(0)
+    ctx = context("fp64", 1, 2, device=device)
+    _check(load().ov_tridiag_sign_nested(ctx, k, a.ctypes.data, b.ctypes.data, d.ctypes.data, int(m), float(beta0),
+                                         y.ctypes.data, ctypes.byref(it)), "ov_tridiag_sign_nested")
+    return y, int(it.value)
 
 
 def kk_gemm(a, b, ha=False, hb=False, mode="split"):

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libov.so")
 SOURCES = ["lattice_kernels.cu", "dense_kernels.cu", "ov_api.cu", "noalloc.cu", "tridiag.cu", "overlap_kernels.cu",
-           "ozaki.cu"]
+           "ozaki.cu", "nested.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]

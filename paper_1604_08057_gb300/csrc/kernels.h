@@ -231,4 +231,25 @@ void dense_set_column0(zd* E, const zd* gy, int64_t gy_stride, double beta0, int
 void dense_extract_y(const zd* F, double beta0, int k, zd* y, cudaStream_t st);
 void dense_extract_tri(const zd* E, int k, zd* ga, zd* gb, double* gd, cudaStream_t st);
 
+// ---- nested Krylov sign of T_k (Sec. 4.1, one nesting level; nested.cu) ----
+// Workspace for nb problems: lu [nb][4k], piv [nb][k], s [nb][k][k] (S = (T + T^{-1})/2),
+// q [nb][m][k] (inner basis), w [nb][k], h [nb][m][m] (Hessenberg H_m), meff [nb].
+struct NestWs {
+  zd* lu;
+  int* piv;
+  zd* s;
+  zd* q;
+  zd* w;
+  zd* h;
+  int* meff;
+};
+// LU of every T, S, q_0 = e_1, h = 0, meff = m; sets *err on a singular T.  Returns launches.
+int nested_prepare(const zd* alpha, const zd* beta, const double* delta, int k, int nb, int m, const NestWs& W,
+                   int* err, cudaStream_t st);
+// m Arnoldi steps on S from e_1 (two launches per step); meff[p] drops below m when
+// problem p's Krylov space closes.  Returns launches.
+int nested_arnoldi(int k, int nb, int m, const NestWs& W, int* err, cudaStream_t st);
+// y = beta0 sum_{c < me} q_c F[c][0]; q one problem's basis, F its sign (leading dimension ld)
+void nested_combine(const zd* q, const zd* F, int ld, int k, int me, double beta0, zd* y, cudaStream_t st);
+
 }  // namespace ov

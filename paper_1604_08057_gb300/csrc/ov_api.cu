@@ -22,7 +22,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, B_EDT1, B_EDT2, B_EDX, B_EDC, B_CGY, B_CGR, B_CGP, B_CGQ, B_CGT, B_CGC, B_SIQ, B_SILT, B_SIT1, B_SIC, B_SIP, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, B_EDT1, B_EDT2, B_EDX, B_EDC, B_CGY, B_CGR, B_CGP, B_CGQ, B_CGT, B_CGC, B_SIQ, B_SILT, B_SIT1, B_SIC, B_SIP, B_NLU, B_NPIV, B_NS, B_NQ, B_NW, B_NH, B_NHN, B_NMEFF, B_NHC, B_NHCN, B_NTA, B_NTB, B_NTD, B_NTY, NBUF
 };
 
 struct Status {
@@ -789,31 +789,109 @@ int newton_batch(ov_context* c, zd* a[2], int k, int nb, int* err_dev, std::vect
   return itmax;
 }
 
-// y_src = beta0 sgn(T_k) e_1 for every source
-template <typename R>
-int sign_all(ov_context* c, Lat<R>& L, const std::vector<SrcScal>& hsc, zd* y, int* iters) {
-  const int k = L.k, nsrc = L.nsrc;
-  const int64_t n = (int64_t)k * k;
+// y_p = beta0_p Q_p sgn(H_p) e_1 for nb tridiagonals T_p (alpha, beta, delta at
+// stride k): the nested Krylov sign with inner size m_in (Sec. 4.1,
+// one nesting level; nested.cu).  The Hessenberg matrices go through the same
+// scaled Newton iteration as the full k x k sign, all problems in one batch when
+// their inner spaces have the same size.
+int nested_sign(ov_context* c, int m_in, const zd* alpha, const zd* beta, const double* delta, int k, int nb,
+                const std::vector<double>& beta0, zd* y, int* iters) {
+  const int m = std::min(m_in, k);
+  const int64_t mm = (int64_t)m * m;
+  NestWs W{wsT<zd>(c, B_NLU, (int64_t)nb * 4 * k), wsT<int>(c, B_NPIV, (int64_t)nb * k),
+           wsT<zd>(c, B_NS, (int64_t)nb * k * k),  wsT<zd>(c, B_NQ, (int64_t)nb * m * k),
+           wsT<zd>(c, B_NW, (int64_t)nb * k),      wsT<zd>(c, B_NH, nb * mm),
+           wsT<int>(c, B_NMEFF, nb)};
   int* derr = wsT<int>(c, B_DERR, 1, true);
-  zd* a[2] = {wsT<zd>(c, B_X, nsrc * n), wsT<zd>(c, B_XN, nsrc * n)};
-  for (int src = 0; src < nsrc; ++src)
-    run(c, OV_KIND_DENSE, 2, [&] {
-      dense_build_t(L.alpha + (int64_t)src * k, L.beta + (int64_t)src * k, L.delta + (int64_t)src * k, k,
-                    a[0] + src * n, c->st);
-    });
-  std::vector<int> which, its;
-  const int itmax = newton_batch(c, a, k, nsrc, derr, which, its);
-  if (itmax < 0) return sign_failed(c, derr);
-  for (int src = 0; src < nsrc; ++src)
-    run(c, OV_KIND_DENSE, 1, [&] {
-      dense_extract_y(a[which[src]] + src * n, hsc[src].beta0, k, y + (int64_t)src * k, c->st);
-    });
+  run(c, OV_KIND_DENSE, 0, [&] { c->launches += nested_prepare(alpha, beta, delta, k, nb, m, W, derr, c->st); });
+  run(c, OV_KIND_DENSE, 0, [&] { c->launches += nested_arnoldi(k, nb, m, W, derr, c->st); });
+  launch_check();
+  std::vector<int> meff(nb);
+  CK(cudaMemcpyAsync(meff.data(), W.meff, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->st));
+  {
+    const int ss = sign_status(c, derr);
+    if (ss != OV_OK) return ss;
+  }
+  int itmax = 0;
+  if (m >= 2 && std::all_of(meff.begin(), meff.end(), [&](int v) { return v == m; })) {
+    zd* a[2] = {W.h, wsT<zd>(c, B_NHN, nb * mm)};
+    std::vector<int> which, its;
+    itmax = newton_batch(c, a, m, nb, derr, which, its);
+    if (itmax < 0) return sign_failed(c, derr);
+    for (int p = 0; p < nb; ++p)
+      run(c, OV_KIND_DENSE, 1, [&] {
+        nested_combine(W.q + (int64_t)p * m * k, a[which[p]] + p * mm, m, k, m, beta0[p], y + (int64_t)p * k, c->st);
+      });
+  } else {
+    // a closed inner space: each problem on its own m_eff x m_eff leading block
+    for (int p = 0; p < nb; ++p) {
+      const int me = meff[p];
+      zd* a[2] = {wsT<zd>(c, B_NHC, (int64_t)me * me), wsT<zd>(c, B_NHCN, (int64_t)me * me)};
+      if (me == 1) {
+        // a 1 x 1 Hessenberg matrix: sgn(h) = sgn(Re h), on the host
+        zd h{};
+        CK(cudaMemcpyAsync(&h, W.h + p * mm, sizeof(zd), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (!std::isfinite(h.re) || !std::isfinite(h.im) || h.re == 0.0) return OV_ERR_SIGN_ILLPOSED;
+        const zd f{h.re > 0.0 ? 1.0 : -1.0, 0.0};
+        CK(cudaMemcpyAsync(a[0], &f, sizeof(zd), cudaMemcpyHostToDevice, c->st));
+        run(c, OV_KIND_DENSE, 1,
+            [&] { nested_combine(W.q + (int64_t)p * m * k, a[0], 1, k, 1, beta0[p], y + (int64_t)p * k, c->st); });
+        CK(cudaStreamSynchronize(c->st));   // f lives on this stack frame
+        itmax = std::max(itmax, 1);
+        continue;
+      }
+      CK(cudaMemcpy2DAsync(a[0], sizeof(zd) * me, W.h + p * mm, sizeof(zd) * m, sizeof(zd) * me, me,
+                           cudaMemcpyDeviceToDevice, c->st));
+      std::vector<int> which, its;
+      const int it = newton_batch(c, a, me, 1, derr, which, its);
+      if (it < 0) return sign_failed(c, derr);
+      itmax = std::max(itmax, it);
+      run(c, OV_KIND_DENSE, 1, [&] {
+        nested_combine(W.q + (int64_t)p * m * k, a[which[0]], me, k, me, beta0[p], y + (int64_t)p * k, c->st);
+      });
+    }
+  }
+  launch_check();
   {
     const int ss = sign_status(c, derr);
     if (ss != OV_OK) return ss;
   }
   if (iters) *iters = itmax;
   return OV_OK;
+}
+
+// y_p = beta0_p sgn(T_p) e_1 for nb tridiagonals (alpha, beta, delta at stride k):
+// the full k x k sign by the scaled Newton iteration, all problems in one batch
+int full_sign(ov_context* c, const zd* alpha, const zd* beta, const double* delta, int k, int nb,
+              const std::vector<double>& beta0, zd* y, int* iters) {
+  const int64_t n = (int64_t)k * k;
+  int* derr = wsT<int>(c, B_DERR, 1, true);
+  zd* a[2] = {wsT<zd>(c, B_X, nb * n), wsT<zd>(c, B_XN, nb * n)};
+  for (int p = 0; p < nb; ++p)
+    run(c, OV_KIND_DENSE, 2, [&] {
+      dense_build_t(alpha + (int64_t)p * k, beta + (int64_t)p * k, delta + (int64_t)p * k, k, a[0] + p * n, c->st);
+    });
+  std::vector<int> which, its;
+  const int itmax = newton_batch(c, a, k, nb, derr, which, its);
+  if (itmax < 0) return sign_failed(c, derr);
+  for (int p = 0; p < nb; ++p)
+    run(c, OV_KIND_DENSE, 1, [&] { dense_extract_y(a[which[p]] + p * n, beta0[p], k, y + (int64_t)p * k, c->st); });
+  {
+    const int ss = sign_status(c, derr);
+    if (ss != OV_OK) return ss;
+  }
+  if (iters) *iters = itmax;
+  return OV_OK;
+}
+
+// y_src = beta0 sgn(T_k) e_1 for every source (nested when options.nested > 0)
+template <typename R>
+int sign_all(ov_context* c, Lat<R>& L, const std::vector<SrcScal>& hsc, zd* y, int* iters) {
+  std::vector<double> b0(L.nsrc);
+  for (int src = 0; src < L.nsrc; ++src) b0[src] = hsc[src].beta0;
+  if (c->opt.nested > 0) return nested_sign(c, c->opt.nested, L.alpha, L.beta, L.delta, L.k, L.nsrc, b0, y, iters);
+  return full_sign(c, L.alpha, L.beta, L.delta, L.k, L.nsrc, b0, y, iters);
 }
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
@@ -1215,6 +1293,8 @@ template <typename R>
 int vjp_forward(ov_context* c, const int32_t dims[4], const void* U, double mu, double m_w, int nsrc,
                 const void* b, int k, FwdState<R>& F, ov_tsl_info* info) {
   check_ptr(b);
+  // the reverse mode differentiates the full k x k sign (Theorem 1 by Newton), not the nested one
+  if (c->opt.nested > 0) throw Status{OV_ERR_INVALID_ARG};
   const int S = c->opt.segment > 0 && c->opt.segment < k ? c->opt.segment : 0;
   F.S = S;
   F.k = k;
@@ -2254,7 +2334,7 @@ bool valid_options(const ov_options* o) {
          o->segment >= 0 && (o->segment == 0 || o->rebiorth == 0) && (o->dense == 0 || o->dense == 1) &&
          (o->diagnostics == 0 || o->diagnostics == 1) && (o->newton == 0 || o->newton == 1) &&
          (o->basis_memory == 0 || o->basis_memory == 1) && (o->graphs == 0 || o->graphs == 1) &&
-         o->gemm >= 0 && o->gemm <= 2;
+         o->gemm >= 0 && o->gemm <= 2 && o->nested >= 0 && o->nested <= OV_NESTED_MAX;
 }
 
 // x = V_k y from a forward state (a second pass over the segments if there are any)
@@ -2741,6 +2821,30 @@ int ov_tsl_coefficients(ov_context* c, int32_t src, int32_t k, double* alpha, do
     CK(cudaMemcpyAsync(delta, static_cast<double*>(c->buf[B_DELTA]) + (int64_t)src * k, sizeof(double) * k,
                        cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
+    return OV_OK;
+  });
+}
+
+int ov_tridiag_sign_nested(ov_context* c, int32_t k, const double* alpha, const double* beta, const double* delta,
+                           int32_t m, double beta0, double* y, int32_t* newton_iters) {
+  if (!c || k < 2 || k > 4096 || m < 0 || m > OV_NESTED_MAX || !alpha || !beta || !delta || !y ||
+      !std::isfinite(beta0))
+    return OV_ERR_INVALID_ARG;
+  return guarded([&] {
+    zd* da = wsT<zd>(c, B_NTA, k);
+    zd* db = wsT<zd>(c, B_NTB, k);
+    double* dd = wsT<double>(c, B_NTD, k);
+    zd* dy = wsT<zd>(c, B_NTY, k);
+    CK(cudaMemcpyAsync(da, alpha, sizeof(zd) * k, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(db, beta, sizeof(zd) * k, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(dd, delta, sizeof(double) * k, cudaMemcpyHostToDevice, c->st));
+    const std::vector<double> b0{beta0};
+    int it = 0;
+    const int st = m > 0 ? nested_sign(c, m, da, db, dd, k, 1, b0, dy, &it) : full_sign(c, da, db, dd, k, 1, b0, dy, &it);
+    if (st != OV_OK) return st;
+    CK(cudaMemcpyAsync(y, dy, sizeof(zd) * k, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (newton_iters) *newton_iters = it;
     return OV_OK;
   });
 }

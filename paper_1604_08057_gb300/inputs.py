@@ -96,6 +96,21 @@ def z2_noise(dims, n: int, rng: np.random.Generator) -> np.ndarray:
     return (2.0 * rng.integers(0, 2, size=shape) - 1.0).astype(np.complex128)
 
 
+def tridiagonal_coefficients(k: int, rng: np.random.Generator, shift: float = 1.5):
+    """Random coefficients in the layout of a TSL tridiagonal: alpha_j complex Gaussian
+    plus +-shift (sign drawn at random), an off-diagonal product omega_j complex
+    Gaussian stored as delta_j = sqrt|omega_j| (below the diagonal) and
+    beta_j = omega_j / delta_j (above); beta_0 = delta_0 = 0.  For sizing and timing the
+    k x k stage without a lattice run."""
+    alpha = rng.standard_normal(k) + 1j * rng.standard_normal(k) + shift * np.sign(rng.standard_normal(k))
+    omega = rng.standard_normal(k) + 1j * rng.standard_normal(k)
+    delta = np.sqrt(np.abs(omega))
+    beta = omega / delta
+    beta[0] = 0.0
+    delta[0] = 0.0
+    return alpha, beta, delta
+
+
 @dataclasses.dataclass(frozen=True)
 class Workload:
     """One of the five synthetic workloads (lattice shapes from Sec. 4)."""
