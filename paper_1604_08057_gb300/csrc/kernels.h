@@ -233,7 +233,8 @@ void dense_extract_tri(const zd* E, int k, zd* ga, zd* gb, double* gd, cudaStrea
 
 // ---- nested Krylov sign of T_k (Sec. 4.1, one nesting level; nested.cu) ----
 // Workspace for nb problems: lu [nb][4k], piv [nb][k], s [nb][k][k] (S = (T + T^{-1})/2),
-// q [nb][m][k] (inner basis), w [nb][k], h [nb][m][m] (Hessenberg H_m), meff [nb].
+// q [nb][m][k] (inner basis), w [nb][k], h [nb][m][m] (Hessenberg H_m), meff [nb],
+// hb [nb][m] (one step's Gram-Schmidt coefficients), wn [nb] (||S q_j||^2).
 struct NestWs {
   zd* lu;
   int* piv;
@@ -242,6 +243,8 @@ struct NestWs {
   zd* w;
   zd* h;
   int* meff;
+  zd* hb;
+  double* wn;
 };
 // LU of every T, S, q_0 = e_1, h = 0, meff = m; sets *err on a singular T.  Returns launches.
 int nested_prepare(const zd* alpha, const zd* beta, const double* delta, int k, int nb, int m, const NestWs& W,

@@ -22,7 +22,7 @@ enum BufId {
   B_LINKS, B_BV, B_BW, B_P, B_Q, B_R, B_S, B_SC, B_ALPHA, B_BETA, B_DELTA, B_PART, B_CNT, B_COEF, B_CPART,
   B_T, B_X, B_XI, B_XN, B_E, B_EN, B_TMP1, B_TMP2, B_IPIV, B_PROW, B_COL, B_DSTAT, B_DPART, B_DCNT, B_DERR,
   B_Y, B_GY, B_GA, B_GB, B_GD, B_XBAR, B_GV, B_GW, B_GV2, B_GW2, B_GR, B_GS, B_GP, B_EV, B_EW, B_REB,
-  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, B_EDT1, B_EDT2, B_EDX, B_EDC, B_CGY, B_CGR, B_CGP, B_CGQ, B_CGT, B_CGC, B_SIQ, B_SILT, B_SIT1, B_SIC, B_SIP, B_NLU, B_NPIV, B_NS, B_NQ, B_NW, B_NH, B_NHN, B_NMEFF, B_NHC, B_NHCN, B_NTA, B_NTB, B_NTD, B_NTY, NBUF
+  B_FORCE, B_DMU, B_DMUPART, B_DMUCNT, B_W0, B_W1, B_REC, B_RECLD, B_ELINKS, B_BLOCKOUT, B_HIN, B_CKR, B_CKS, B_CKV, B_CKW, B_CKSC, B_FSIGN, B_ACT, B_SCAL, B_RSCAL, B_FPARTS, B_LRA, B_LRB, B_BETA0, B_EPS1T, B_EPS1B, B_EPS2T, B_EPS2B, B_EPSN, B_NSPART, B_NSCNT, B_OVX, B_OVB, B_GMV, B_GMW, B_GMR, B_GMH, B_GMP, B_CHI, B_CURX1, B_CURX2, B_CURG1, B_CURG2, B_AERR, B_OZ, B_DFA, B_DFC, B_DFSA, B_DFSC, B_DFPART, B_DFTOP, B_DFBOT, B_DFSG, B_RZY, B_RZF, B_RZH, B_RZD, B_EDT1, B_EDT2, B_EDX, B_EDC, B_CGY, B_CGR, B_CGP, B_CGQ, B_CGT, B_CGC, B_SIQ, B_SILT, B_SIT1, B_SIC, B_SIP, B_NLU, B_NPIV, B_NS, B_NQ, B_NW, B_NH, B_NHN, B_NMEFF, B_NHC, B_NHCN, B_NTA, B_NTB, B_NTD, B_NTY, B_NHB, B_NWN, NBUF
 };
 
 struct Status {
@@ -87,7 +87,7 @@ struct ov_context {
     std::vector<unsigned char> seen;   // shape of the last call launched directly
     cudaGraphExec_t exec = nullptr;
     int64_t nlaunch = 0;
-  } gfwd, grev;
+  } gfwd, grev, gnest;   // forward sweep, reverse sweep, nested k x k stage
   cudaStream_t cap_st = nullptr;
   cudaEvent_t cap_ev[2] = {nullptr, nullptr};
   // one-shot host-side fault injection (ov_debug_inject)
@@ -801,10 +801,22 @@ int nested_sign(ov_context* c, int m_in, const zd* alpha, const zd* beta, const 
   NestWs W{wsT<zd>(c, B_NLU, (int64_t)nb * 4 * k), wsT<int>(c, B_NPIV, (int64_t)nb * k),
            wsT<zd>(c, B_NS, (int64_t)nb * k * k),  wsT<zd>(c, B_NQ, (int64_t)nb * m * k),
            wsT<zd>(c, B_NW, (int64_t)nb * k),      wsT<zd>(c, B_NH, nb * mm),
-           wsT<int>(c, B_NMEFF, nb)};
+           wsT<int>(c, B_NMEFF, nb),               wsT<zd>(c, B_NHB, (int64_t)nb * m),
+           wsT<double>(c, B_NWN, nb)};
   int* derr = wsT<int>(c, B_DERR, 1, true);
-  run(c, OV_KIND_DENSE, 0, [&] { c->launches += nested_prepare(alpha, beta, delta, k, nb, m, W, derr, c->st); });
-  run(c, OV_KIND_DENSE, 0, [&] { c->launches += nested_arnoldi(k, nb, m, W, derr, c->st); });
+  // the set-up and the m Arnoldi steps (~6 m launches) replay as one graph when the shape repeats
+  std::vector<unsigned char> key;
+  key_add(key, k);
+  key_add(key, nb);
+  key_add(key, m);
+  for (const void* ptr : {(const void*)alpha, (const void*)beta, (const void*)delta, (const void*)W.lu,
+                          (const void*)W.piv, (const void*)W.s, (const void*)W.q, (const void*)W.w, (const void*)W.h,
+                          (const void*)W.meff, (const void*)W.hb, (const void*)W.wn, (const void*)derr})
+    key_add(key, ptr);
+  captured(c, c->gnest, key, [&] {
+    run(c, OV_KIND_DENSE, 0, [&] { c->launches += nested_prepare(alpha, beta, delta, k, nb, m, W, derr, c->st); });
+    run(c, OV_KIND_DENSE, 0, [&] { c->launches += nested_arnoldi(k, nb, m, W, derr, c->st); });
+  });
   launch_check();
   std::vector<int> meff(nb);
   CK(cudaMemcpyAsync(meff.data(), W.meff, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->st));
@@ -2404,6 +2416,7 @@ int ov_context_destroy(ov_context* c) {
   if (c->cap_st) cudaStreamSynchronize(c->cap_st);
   if (c->gfwd.exec) cudaGraphExecDestroy(c->gfwd.exec);
   if (c->grev.exec) cudaGraphExecDestroy(c->grev.exec);
+  if (c->gnest.exec) cudaGraphExecDestroy(c->gnest.exec);
   for (auto& e : c->cap_ev)
     if (e) cudaEventDestroy(e);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
