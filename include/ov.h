@@ -77,7 +77,8 @@ typedef struct {
                         * in shared memory (rows stay on chip for all k elimination steps; the
                         * steps are separated by bounded inter-block waits), else 1;
                         * 1: one launch per elimination step, replayed as a CUDA graph.
-                        * Both give bitwise identical results. */
+                        * Both give bitwise identical results.  The m x m matrices of the nested
+                        * stage (options.nested) always use form 1. */
   int32_t diagnostics; /* 0: none.  1: after the forward recurrence of ov_tsl_sign, ov_tsl_sign_vjp,
                         * ov_tsl_sign_fwd and ov_tsl_batch, measure (a) the loss of
                         * biorthogonality of the stored bases, sampled on the last pair of basis
@@ -524,8 +525,10 @@ int ov_u1_current(ov_context *ctx, const int32_t dims[4], const void *U, double 
  * beta[2k] interleaved complex (alpha_j = T[j][j], beta_j = T[j-1][j],
  * beta_0 unused), delta[k] (delta_j = T[j][j-1], delta_0 unused); y (host
  * double[2k], interleaved complex); newton_iters (may be NULL) receives the
- * Newton iteration count.  Uses the context's workspace and stream (options
- * other than newton and dense do not apply).  2 <= k <= 4096,
+ * Newton iteration count.  Uses the context's workspace and stream; of the
+ * options only newton applies, and dense for m = 0 (the nested form inverts
+ * its m x m matrices in the step form, which is faster at these sizes and
+ * gives the same bits).  2 <= k <= 4096,
  * 0 <= m <= OV_NESTED_MAX.  Returns OV_OK, OV_ERR_INVALID_ARG,
  * OV_ERR_SIGN_ILLPOSED (T singular, a non-finite entry, or the Newton
  * iteration failed), OV_ERR_OOM, OV_ERR_CUDA. */

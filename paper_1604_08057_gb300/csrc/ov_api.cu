@@ -824,6 +824,17 @@ int nested_sign(ov_context* c, int m_in, const zd* alpha, const zd* beta, const 
     const int ss = sign_status(c, derr);
     if (ss != OV_OK) return ss;
   }
+  // The Hessenberg matrices' inversions in the step form (one launch per elimination
+  // column, graph-replayed): at m = 60 .. 150 it is faster than the cooperative form,
+  // whose per-step inter-block handshake dominates at these sizes (k = 800: 6.7 / 10.3 /
+  // 14.9 ms per stage against 8.1 / 14.4 / 20.5 at m = 60 / 100 / 150); both forms give
+  // the same bits.
+  struct DenseForm {
+    ov_context* c;
+    int saved;
+    ~DenseForm() { c->opt.dense = saved; }
+  } form{c, c->opt.dense};
+  c->opt.dense = GJ_STEPS;
   int itmax = 0;
   if (m >= 2 && std::all_of(meff.begin(), meff.end(), [&](int v) { return v == m; })) {
     zd* a[2] = {W.h, wsT<zd>(c, B_NHN, nb * mm)};

@@ -174,3 +174,25 @@ def test_reverse_mode_refuses_nested():
     # the context computes normally afterwards
     du, dmu, x = binding.tsl_sign_vjp(T(u), 0.3, -1.0, T(b), 40, T(xbar))
     assert np.isfinite(dmu) and torch.isfinite(du).all()
+
+
+def test_nested_at_the_benchmark_workload():
+    """14x14^3, k = 800, P = 60, one Gram-Schmidt pass (the benchmark's launch
+    configuration), inner size 100: the GPU stage against the oracle's nested sign on
+    the call's own T_k (1e-10, identical input), and x from the nested stage against x
+    from the full k x k sign (bench: 5e-12; required 1e-9, 10x the map's floor)."""
+    wl = inputs.WORKLOADS["14x14^3"]
+    u, b, _ = inputs.make_inputs(wl)
+    ut, bt = T(u), T(b)
+    k, m, period, passes = wl.k, 100, 60, 1
+    full = binding.tsl_sign(ut, wl.mu, wl.m_w, bt, k, "fp64", period, passes)
+    a, bb, d = binding.tsl_coefficients(k, 0, "fp64", period, passes)
+    y, _ = binding.tridiag_sign_nested(a, bb, d, m)
+    want = nested.nested_sign_e1(tsl.tridiag(a, bb, d), m)
+    assert rel(y, want) <= 1e-10, rel(y, want)
+    binding.nested_sign(m, "fp64", period, passes)
+    try:
+        x = binding.tsl_sign(ut, wl.mu, wl.m_w, bt, k, "fp64", period, passes)
+    finally:
+        binding.nested_sign(0, "fp64", period, passes)
+    assert rel(x.cpu().numpy(), full.cpu().numpy()) <= 1e-9
