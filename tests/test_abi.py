@@ -72,3 +72,32 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_nested_option_and_stage_reject_bad_arguments_without_gpu():
+    """options.nested outside 0..OV_NESTED_MAX and ov_tridiag_sign_nested's size and
+    pointer checks are decided on the host, before any CUDA call."""
+    import numpy as np
+    lib = binding.load(build.build())
+    h = ctypes.c_void_p()
+    for bad in (-1, 1025):
+        opt = binding.Options(0, 1, 2, 0)
+        opt.nested = bad
+        assert lib.ov_context_create(ctypes.byref(h), ctypes.byref(opt), None) == -1
+    k = 8
+    a = np.ones(k, dtype=np.complex128)
+    d = np.zeros(k)
+    y = np.zeros(k, dtype=np.complex128)
+    it = ctypes.c_int32(0)
+
+    def call(ctx, kk, m, beta0=1.0, yp=y.ctypes.data):
+        return lib.ov_tridiag_sign_nested(ctx, kk, a.ctypes.data, a.ctypes.data, d.ctypes.data, m, beta0, yp,
+                                          ctypes.byref(it))
+    assert call(None, k, 4) == -1                       # no context
+    fake = ctypes.c_void_p(1)                           # never dereferenced: the sizes fail first
+    assert call(fake, 1, 4) == -1                       # k < 2
+    assert call(fake, 4097, 4) == -1                    # k > 4096
+    assert call(fake, k, -1) == -1                      # m < 0
+    assert call(fake, k, 1025) == -1                    # m > OV_NESTED_MAX
+    assert call(fake, k, 4, float("nan")) == -1         # non-finite beta0
+    assert call(fake, k, 4, 1.0, None) == -1            # no output
