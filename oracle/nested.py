@@ -1,12 +1,12 @@
-"""Nested Krylov approximation of the k x k sign: one level of nesting (Sec. 4.1).
+"""Nested Krylov approximation of the k x k sign: one nesting level (Sec. 4.1).
 
 TEST INFRASTRUCTURE ONLY (see the package header): nothing on the library's
 product path imports this module.
 
-Sec. 4.1 computes its results with a nested version of the TSL, one level of
-nesting, and two Krylov sizes to choose (outer and inner; the inner one is 100
-in its runs).  It defers the algorithm to Bloch and Heybrock (cited there as
-Bloch:11:2) and does not state it.  The reading taken here:
+Sec. 4.1 runs its TSL computations nested once, with an outer and an inner
+Krylov size to choose (the inner one is 100 in its runs).  It leaves the
+algorithm to Bloch and Heybrock (cited there as Bloch:11:2) and does not state
+it.  The reading taken here:
 
 * outer stage: the TSL of size k (``oracle.tsl``) gives T_k and the bases, and
   x = beta_0 V_k sgn(T_k) e_1 as before;

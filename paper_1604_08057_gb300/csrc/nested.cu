@@ -1,4 +1,4 @@
-// Nested Krylov approximation of the k x k sign, one level of nesting (Sec. 4.1,
+// Nested Krylov approximation of the k x k sign, one nesting level (Sec. 4.1,
 // which runs the TSL nested once with an inner Krylov size of 100):
 //
 //   S = (T_k + T_k^{-1}) / 2,   sgn(S) = sgn(T_k)
