@@ -6,7 +6,6 @@ Frechet derivative (Daleckii-Krein in the eigenbasis) when the Krylov space
 exhausts the deflated complement, and deflation's gain in accuracy at fixed k
 on a lattice operator."""
 import numpy as np
-import pytest
 
 from oracle import deflation, overlap, tsl
 from paper_1604_08057_gb300 import inputs
