@@ -89,3 +89,13 @@ def nested_tsl(u, b, mu, m_w, k, m, **kw):
     y = res.beta0 * nested_sign_e1(res.t, m)
     x = sum(y[j] * res.v[j] for j in range(k))
     return x, y, res
+
+
+def nested_block_tsl(u, b, mu, m_w, k, m, e=None, m_dir=0.0, **kw):
+    """Theorem 1's block TSL (``oracle.tsl.block_tsl``: B = [[H, dH], [0, H]] from
+    (0, b)) with the nested k x k stage: the paper's route to the derivative with
+    nesting.  Returns (dx, x, TSLResult of the block run)."""
+    _, _, res = tsl.block_tsl(u, b, mu, m_w, k, e, m_dir, **kw)
+    y = res.beta0 * nested_sign_e1(res.t, m)
+    z = sum(y[j] * res.v[j] for j in range(k))
+    return z[0], z[1], res

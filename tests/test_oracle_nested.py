@@ -9,6 +9,8 @@ What fixes the nested result independently of the oracle's own code:
   for any orthonormal basis of the Krylov space (here: QR of the Krylov matrix);
 * exactness when the Krylov space is complete (m = k, or an invariant subspace);
 * the nested TSL equal to sgn(H) b from the dense eigendecomposition at k = m = n.
+* Theorem 1's block TSL with the nested stage equal to the Daleckii-Krein Frechet
+  derivative and sgn(H) b at k = 2n (also at inner size 80 of 384).
 """
 import numpy as np
 
@@ -123,3 +125,25 @@ def test_nested_tsl_reaches_the_exact_sign():
     x40, _, _ = nested.nested_tsl(u, b, mu, m_w, 120, 40, rebiorth=1)
     full = tsl.tsl_forward(u, b, mu, m_w, 120, rebiorth=1).x
     assert np.linalg.norm(x40 - full) / np.linalg.norm(full) < 1e-8
+
+
+def test_nested_block_tsl_reaches_the_exact_derivative():
+    """Theorem 1 with the nested k x k stage (the paper's derivative route): at k = 2n
+    the upper half equals the Daleckii-Krein Frechet derivative L_sgn(H, dH) b and the
+    lower half sgn(H) b, already at an inner size well below k."""
+    from tests.dense_util import frechet_sign_daleckii_krein
+    dims = (2, 2, 2, 2)
+    rng = np.random.default_rng(62)
+    u = inputs.su3_links(dims, 0.4, rng)
+    b = inputs.gaussian_spinors(dims, 1, rng)[0]
+    e = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape)
+    mu, m_w, m_dir = 0.3, -1.0, 0.7
+    hm = dense_from_apply(lambda p: dirac.apply_h(u, p, mu, m_w), b.shape)
+    dhm = dense_from_apply(lambda p: dirac.apply_dh(u, e, p, mu, m_w, m_dir), b.shape)
+    exact_d = frechet_sign_daleckii_krein(hm, dhm) @ b.ravel()
+    exact_x = sign_eig(hm) @ b.ravel()
+    k = 2 * b.size
+    for m in (80, k):
+        dx, x, _ = nested.nested_block_tsl(u, b, mu, m_w, k, m, e, m_dir)
+        assert np.linalg.norm(dx.ravel() - exact_d) <= 1e-10 * np.linalg.norm(exact_d), m
+        assert np.linalg.norm(x.ravel() - exact_x) <= 1e-10 * np.linalg.norm(exact_x), m
